@@ -1,0 +1,140 @@
+/*
+ * phe.h -- C ABI of libphe, a B300 (sm_103a) engine for the server side of
+ * private LoRA fine-tuning under homomorphic encryption (arXiv 2505.07329).
+ *
+ * The server holds a public int8 weight matrix W (d_out x d_in) in the clear
+ * and receives the client's activations x as RLWE ciphertexts, one per block
+ * of N coefficients (Sec. 4.3.1: L = ceil(d_in/N) blocks, last one zero
+ * padded).  For every token and every output row j it returns the LWE
+ * ciphertext of Eq. (LWEdot),
+ *
+ *     LWE(x . w_j) = sum_{i<L} SampleExtract(RLWE(x_hat_i) . w_hat_ij, N-1),
+ *     w_hat_ij[k]  = w_j[iN + N-1-k]                    (reversed weights),
+ *
+ * followed by the ModulusSwitch to q' = 2^k (Sec. 3.2, Sec. 4.3.1) before the
+ * result goes back to the client.  The backward pass computes W^T . [g] with
+ * the same primitive (Sec. 6.2: encrypted vector-matrix products in both
+ * passes).  The server never sees the secret key (Sec. 5).
+ *
+ * Conventions
+ *   - Every call returns a phe_status; on failure phe_last_error() gives a
+ *     message for the calling thread.  Invalid arguments return PHE_EINVAL
+ *     and launch nothing.
+ *   - Handles (phe_ctx, phe_weights) are opaque, library-owned, and freed
+ *     with the matching *_destroy / *_free call.
+ *   - Data buffers are caller-owned.  Pointers named d_* are device pointers
+ *     on the context's device; h_* are host pointers.
+ *   - `stream` is a cudaStream_t (NULL = legacy default stream).  Calls that
+ *     take a stream are asynchronous on it unless stated otherwise.
+ *   - Ciphertext layout (SoA):
+ *       input  mask  A   [T][L][N] uint64, words in [0, q) (larger words are
+ *                        reduced mod q on load)
+ *       input  body  B   [T][L][N] uint64
+ *       output mask  a'  [T][rows][N]  uint32 (switched) or uint64 (raw)
+ *       output body  b'  [T][rows]     uint32 (switched) or uint64 (raw)
+ *     where rows = d_out for PHE_FWD and d_in for PHE_BWD, and L is formed
+ *     from d_in (PHE_FWD) or d_out (PHE_BWD).
+ */
+#ifndef PHE_H
+#define PHE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum phe_status {
+    PHE_OK = 0,
+    PHE_EINVAL = 1,        /* bad argument, shape or parameter set */
+    PHE_ENOMEM = 2,        /* device or host allocation failed */
+    PHE_EBUSY = 3,         /* admission refused: capacity in use */
+    PHE_ETIMEOUT = 4,      /* a bounded wait ran out */
+    PHE_ECUDA = 5,         /* a CUDA runtime call failed */
+    PHE_EUNSUPPORTED = 6   /* valid request the build does not support */
+} phe_status;
+
+typedef struct phe_ctx phe_ctx;
+typedef struct phe_weights phe_weights;
+
+/* Ring and switch parameters (Sec. 3.1 RLWE ciphertexts over
+ * R_q = Z_q[X]/(X^N+1); Sec. 3.2 ModulusSwitch q -> q_out).
+ *   N          ring degree, a power of two in [256, 8192]
+ *   q          ciphertext modulus: a prime with q = 1 (mod 2N) and
+ *              2^53 < q < 2^61 (e.g. 2^60 - 2^14 + 1)
+ *   log2_qout  k of the output modulus q' = 2^k, 1 <= k <= 32 */
+typedef struct phe_params {
+    uint32_t N;
+    uint32_t log2_qout;
+    uint64_t q;
+} phe_params;
+
+#define PHE_FWD 0              /* W   . [x] : rows = d_out, contraction over d_in */
+#define PHE_BWD 1              /* W^T . [g] : rows = d_in,  contraction over d_out */
+#define PHE_DIR_FWD_BIT 1u
+#define PHE_DIR_BWD_BIT 2u
+
+#define PHE_OUT_SWITCHED 0u    /* outputs mod q' = 2^k as uint32 (the protocol's result) */
+#define PHE_OUT_RAW 1u         /* outputs mod q as uint64, no switch (testing, unfused use) */
+
+/* Name of a status code.  Never fails. */
+const char* phe_status_string(phe_status s);
+
+/* Message of the last failed call made by this thread ("" if none). */
+const char* phe_last_error(void);
+
+/* Create a context on CUDA device `device`: validates the parameters
+ * (primality, q = 1 mod 2N, bounds), finds a primitive 2N-th root of unity
+ * and uploads the twiddle tables.  Blocking.  Errors: PHE_EINVAL for a bad
+ * parameter set, PHE_ECUDA if the device is unusable. */
+phe_status phe_ctx_create(const phe_params* params, int device, phe_ctx** out);
+void phe_ctx_destroy(phe_ctx* ctx);
+
+/* Copy the public weights W (host, int8, row-major [d_out][d_in], caller
+ * keeps ownership) to the device and encode them for the directions in
+ * `dirs` (PHE_DIR_FWD_BIT | PHE_DIR_BWD_BIT): the reversed blocks w_hat_ij
+ * of Sec. 4.3.1, transformed to the NTT domain (and scaled by N^-1), plus a
+ * packed int8 copy for the body product.  1 <= d_out, d_in <= 16384.
+ * Blocking on `stream`.  Errors: PHE_EINVAL, PHE_ENOMEM, PHE_ECUDA. */
+phe_status phe_weights_upload(phe_ctx* ctx, const int8_t* h_W, uint32_t d_out, uint32_t d_in, uint32_t dirs,
+                              void* stream, phe_weights** out);
+void phe_weights_free(phe_weights* w);
+
+/* Output rows, contraction length and input blocks L for a direction;
+ * device bytes held by the handle.  Errors: PHE_EINVAL (direction not
+ * uploaded). */
+phe_status phe_weights_shape(const phe_weights* w, int dir, uint32_t* rows, uint32_t* cols, uint32_t* L);
+uint64_t phe_weights_device_bytes(const phe_weights* w);
+
+/* The hot path, one projection (Eq. (LWEdot) + ModulusSwitch): for T tokens
+ * of input ciphertexts (d_in_mask, d_in_body: [T][L][N] uint64) write the T x
+ * rows LWE ciphertexts: masks to d_out_mask [T][rows][N] and bodies to
+ * d_out_body [T][rows], as uint32 mod 2^k (flags = PHE_OUT_SWITCHED) or as
+ * uint64 mod q (flags = PHE_OUT_RAW).  T = 0 is a no-op.  Uses stream-ordered
+ * scratch of T*L*N*8 bytes (allocated and freed on `stream`).  Errors:
+ * PHE_EINVAL (shapes, null pointers, direction not uploaded), PHE_ENOMEM,
+ * PHE_ECUDA. */
+phe_status phe_matmul(phe_ctx* ctx, const phe_weights* w, int dir, uint32_t T, const uint64_t* d_in_mask,
+                      const uint64_t* d_in_body, void* d_out_mask, void* d_out_body, uint32_t flags, void* stream);
+
+/* Unfused ModulusSwitch (Sec. 3.2): out[i] = round(in[i] * 2^k / q) mod 2^k,
+ * ties rounded up, for n words (device buffers).  Input words are reduced
+ * mod q first.  Errors: PHE_EINVAL, PHE_ECUDA. */
+phe_status phe_modswitch(phe_ctx* ctx, const uint64_t* d_in, uint32_t* d_out, size_t n, void* stream);
+
+/* Client-side helper for tests and benchmarks (not part of the server
+ * path, which never holds the key): RLWE encryption of T int8 vectors of
+ * length d (Sec. 3.1, blocks of Sec. 4.3.1):
+ *     B_ti = A_ti * S + E_ti + delta * x_hat_ti  (mod q)
+ * d_A [T][L][N] masks in [0, q), d_S [N] int8 key (binary or ternary),
+ * d_E [T][L][N] int32 noise, d_x [T][d] int8 messages; writes d_B [T][L][N].
+ * Errors: PHE_EINVAL, PHE_ENOMEM, PHE_ECUDA. */
+phe_status phe_client_encrypt(phe_ctx* ctx, uint32_t T, uint32_t d, const uint64_t* d_A, const int8_t* d_S,
+                              const int32_t* d_E, const int8_t* d_x, uint64_t delta, uint64_t* d_B, void* stream);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PHE_H */

@@ -1,0 +1,422 @@
+// C ABI of libphe (include/phe.h): parameter validation, twiddle tables,
+// weight upload and the per-call hot path.
+#include <cstdarg>
+#include <cstdio>
+#include <cstring>
+#include <new>
+#include <string>
+#include <vector>
+
+#include "phe_host.hpp"
+
+using phe::u32;
+using phe::u64;
+typedef unsigned __int128 u128;
+
+namespace {
+
+thread_local std::string g_err;
+
+phe_status fail(phe_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+phe_status cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) return fail(PHE_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(PHE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+// Makes the context's device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(int dev) {
+    err = cudaGetDevice(&prev);
+    if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
+
+// --- host modular arithmetic (parameter set-up only) ---------------------
+u64 mulmod(u64 a, u64 b, u64 q) { return (u64)(((u128)a * b) % q); }
+u64 powmod(u64 b, u64 e, u64 q) {
+  u64 r = 1 % q;
+  b %= q;
+  for (; e; e >>= 1) {
+    if (e & 1) r = mulmod(r, b, q);
+    b = mulmod(b, b, q);
+  }
+  return r;
+}
+// Miller-Rabin with the first twelve prime bases: exact for n < 3.3e24.
+bool is_prime(u64 n) {
+  const u64 bases[] = {2, 3, 5, 7, 11, 13, 17, 19, 23, 29, 31, 37};
+  if (n < 2) return false;
+  for (u64 p : bases) {
+    if (n % p == 0) return n == p;
+  }
+  u64 d = n - 1;
+  int r = 0;
+  while (!(d & 1)) { d >>= 1; ++r; }
+  for (u64 a : bases) {
+    u64 x = powmod(a, d, n);
+    if (x == 1 || x == n - 1) continue;
+    bool witness = true;
+    for (int i = 1; i < r && witness; ++i) {
+      x = mulmod(x, x, n);
+      if (x == n - 1) witness = false;
+    }
+    if (witness) return false;
+  }
+  return true;
+}
+u64 shoup(u64 w, u64 q) { return (u64)(((u128)w << 64) / q); }
+u32 bitrev(u32 x, int bits) {
+  u32 r = 0;
+  for (int i = 0; i < bits; ++i) r |= ((x >> i) & 1u) << (bits - 1 - i);
+  return r;
+}
+int floor_log2(u64 x) { return 63 - __builtin_clzll(x); }
+
+// Primitive 2N-th root of unity: the smallest g^((q-1)/2N) with order 2N,
+// trying odd g from 3 upward.
+u64 primitive_root_2n(u64 q, u32 N) {
+  const u64 e = (q - 1) / (2ull * N);
+  for (u64 g = 3; g < (1u << 20); g += 2) {
+    const u64 psi = powmod(g, e, q);
+    if (powmod(psi, N, q) == q - 1) return psi;
+  }
+  return 0;
+}
+
+phe_status upload(void** dptr, const void* host, size_t bytes) {
+  cudaError_t e = cudaMalloc(dptr, bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMalloc(tables)");
+  e = cudaMemcpy(*dptr, host, bytes, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy(tables)");
+  return PHE_OK;
+}
+
+void free_tables(phe::Tables& t) {
+  cudaFree(t.fwd_c);
+  cudaFree(t.inv_c);
+  cudaFree(t.fwd_0);
+  cudaFree(t.inv_0);
+  t = phe::Tables{};
+}
+
+phe_status check_dir(const phe_weights* w, int dir) {
+  if (dir != PHE_FWD && dir != PHE_BWD) return fail(PHE_EINVAL, "direction %d is not PHE_FWD or PHE_BWD", dir);
+  if (!(w->dirs & (1u << dir)))
+    return fail(PHE_EINVAL, "direction %s was not uploaded", dir == PHE_FWD ? "PHE_FWD" : "PHE_BWD");
+  return PHE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+const char* phe_status_string(phe_status s) {
+  switch (s) {
+    case PHE_OK: return "PHE_OK";
+    case PHE_EINVAL: return "PHE_EINVAL";
+    case PHE_ENOMEM: return "PHE_ENOMEM";
+    case PHE_EBUSY: return "PHE_EBUSY";
+    case PHE_ETIMEOUT: return "PHE_ETIMEOUT";
+    case PHE_ECUDA: return "PHE_ECUDA";
+    case PHE_EUNSUPPORTED: return "PHE_EUNSUPPORTED";
+  }
+  return "PHE_UNKNOWN";
+}
+
+const char* phe_last_error(void) { return g_err.c_str(); }
+
+phe_status phe_ctx_create(const phe_params* prm, int device, phe_ctx** out) {
+  if (!prm || !out) return fail(PHE_EINVAL, "phe_ctx_create: null argument");
+  *out = nullptr;
+  const u32 N = prm->N;
+  if (N < (1u << phe::kMinLogN) || N > (1u << phe::kMaxLogN) || (N & (N - 1)))
+    return fail(PHE_EINVAL, "N=%u must be a power of two in [256, 8192]", N);
+  const u64 q = prm->q;
+  if (q <= (1ull << 53) || q >= (1ull << 61))
+    return fail(PHE_EINVAL, "q=%llu must satisfy 2^53 < q < 2^61", (unsigned long long)q);
+  if ((q - 1) % (2ull * N) != 0)
+    return fail(PHE_EINVAL, "q=%llu is not 1 mod 2N=%u", (unsigned long long)q, 2 * N);
+  if (!is_prime(q)) return fail(PHE_EINVAL, "q=%llu is not prime", (unsigned long long)q);
+  if (prm->log2_qout < 1 || prm->log2_qout > 32) return fail(PHE_EINVAL, "log2_qout=%u not in [1, 32]", prm->log2_qout);
+
+  int ndev = 0;
+  cudaError_t e = cudaGetDeviceCount(&ndev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDeviceCount");
+  if (device < 0 || device >= ndev) return fail(PHE_EINVAL, "device %d out of range (%d devices)", device, ndev);
+  DeviceGuard g(device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+
+  phe_ctx* c = new (std::nothrow) phe_ctx();
+  if (!c) return fail(PHE_ENOMEM, "phe_ctx_create: host allocation");
+  c->prm = *prm;
+  c->device = device;
+  c->logn = floor_log2(N);
+  e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
+  if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaDeviceGetAttribute"); }
+
+  phe::RingConst& rc = c->rc;
+  rc.q = q;
+  rc.q2 = 2 * q;
+  rc.half_q = q / 2;
+  rc.ms_s = (u32)floor_log2(q);
+  rc.ms_mu = (u64)(((u128)1 << (64 + rc.ms_s)) / q);
+  rc.red_mu = (u64)(((u128)1 << 64) / q);
+  rc.c30 = (1ull << 30) % q;
+  rc.c30p = shoup(rc.c30, q);
+  rc.log2_qout = prm->log2_qout;
+  c->n_inv = powmod(N, q - 2, q);
+  c->n_inv_p = shoup(c->n_inv, q);
+
+  const u64 psi = primitive_root_2n(q, N);
+  if (!psi) { delete c; return fail(PHE_EINVAL, "no primitive 2N-th root of unity found for q"); }
+  const u64 psi_inv = powmod(psi, q - 2, q);
+  const int logn = c->logn;
+  std::vector<ulonglong2> fwd(N), inv(N);
+  for (u32 k = 0; k < N; ++k) {
+    const u32 br = bitrev(k, logn);
+    const u64 a = powmod(psi, br, q), b = powmod(psi_inv, br, q);
+    fwd[k] = make_ulonglong2(a, shoup(a, q));
+    inv[k] = make_ulonglong2(b, shoup(b, q));
+  }
+  // Pass-0 twiddles in thread-major order: slot (st, b) of thread p is the
+  // twiddle of stage st for butterfly group b of positions [16p, 16p+16).
+  const u32 P = N / 16;
+  std::vector<ulonglong2> fwd0(15 * P), inv0(15 * P);
+  for (int st = 0; st < 4; ++st) {
+    for (int b = 0; b < (8 >> st); ++b) {
+      for (u32 p = 0; p < P; ++p) {
+        const u32 idx = (N >> (st + 1)) + ((16 * p) >> (st + 1)) + b;
+        fwd0[phe::pass0_slot(st, b) * P + p] = fwd[idx];
+        inv0[phe::pass0_slot(st, b) * P + p] = inv[idx];
+      }
+    }
+  }
+  phe_status st;
+  if ((st = upload((void**)&c->tab.fwd_c, fwd.data(), N * sizeof(ulonglong2))) != PHE_OK ||
+      (st = upload((void**)&c->tab.inv_c, inv.data(), N * sizeof(ulonglong2))) != PHE_OK ||
+      (st = upload((void**)&c->tab.fwd_0, fwd0.data(), fwd0.size() * sizeof(ulonglong2))) != PHE_OK ||
+      (st = upload((void**)&c->tab.inv_0, inv0.data(), inv0.size() * sizeof(ulonglong2))) != PHE_OK) {
+    free_tables(c->tab);
+    delete c;
+    return st;
+  }
+  *out = c;
+  return PHE_OK;
+}
+
+void phe_ctx_destroy(phe_ctx* c) {
+  if (!c) return;
+  DeviceGuard g(c->device);
+  free_tables(c->tab);
+  delete c;
+}
+
+phe_status phe_weights_upload(phe_ctx* c, const int8_t* h_W, uint32_t d_out, uint32_t d_in, uint32_t dirs,
+                              void* stream, phe_weights** out) {
+  if (!c || !h_W || !out) return fail(PHE_EINVAL, "phe_weights_upload: null argument");
+  *out = nullptr;
+  if (d_out < 1 || d_in < 1 || d_out > 16384 || d_in > 16384)
+    return fail(PHE_EINVAL, "weights %ux%u: dimensions must be in [1, 16384]", d_out, d_in);
+  if (dirs == 0 || (dirs & ~3u)) return fail(PHE_EINVAL, "dirs=%u must be a non-empty subset of {FWD, BWD}", dirs);
+  DeviceGuard g(c->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+
+  phe_weights* w = new (std::nothrow) phe_weights();
+  if (!w) return fail(PHE_ENOMEM, "phe_weights_upload: host allocation");
+  w->ctx = c;
+  w->d_out = d_out;
+  w->d_in = d_in;
+  w->dirs = dirs;
+  const u32 N = c->prm.N;
+  int8_t* dW = nullptr;
+  const size_t wbytes = (size_t)d_out * d_in;
+  cudaError_t e = cudaMalloc(&dW, wbytes);
+  if (e != cudaSuccess) { delete w; return cuda_fail(e, "cudaMalloc(W)"); }
+  e = cudaMemcpyAsync(dW, h_W, wbytes, cudaMemcpyHostToDevice, s);
+  for (int dir = 0; dir < 2 && e == cudaSuccess; ++dir) {
+    if (!(dirs & (1u << dir))) continue;
+    phe_weights::Dir& D = w->dir[dir];
+    D.rows = dir == PHE_FWD ? d_out : d_in;
+    D.cols = dir == PHE_FWD ? d_in : d_out;
+    D.L = (D.cols + N - 1) / N;
+    const u32 rs = dir == PHE_FWD ? d_in : 1, cs = dir == PHE_FWD ? 1 : d_in;
+    const size_t what_bytes = (size_t)D.rows * D.L * N * sizeof(ulonglong2);
+    const size_t wb_bytes = (size_t)((D.cols + 3) / 4) * D.rows * sizeof(uint32_t);
+    if ((e = cudaMalloc(&D.what, what_bytes)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&D.wb, wb_bytes)) != cudaSuccess) break;
+    w->bytes += what_bytes + wb_bytes;
+    if ((e = phe::launch_weight_ntt(c, dW, D.rows, D.cols, rs, cs, D.L, 1, D.what, s)) != cudaSuccess) break;
+    if ((e = phe::launch_pack_body_weights(dW, D.rows, D.cols, rs, cs, D.wb, s)) != cudaSuccess) break;
+  }
+  if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+  cudaFree(dW);
+  if (e != cudaSuccess) {
+    phe_weights_free(w);
+    return cuda_fail(e, "phe_weights_upload");
+  }
+  *out = w;
+  return PHE_OK;
+}
+
+void phe_weights_free(phe_weights* w) {
+  if (!w) return;
+  DeviceGuard g(w->ctx->device);
+  for (auto& D : w->dir) {
+    cudaFree(D.what);
+    cudaFree(D.wb);
+  }
+  delete w;
+}
+
+phe_status phe_weights_shape(const phe_weights* w, int dir, uint32_t* rows, uint32_t* cols, uint32_t* L) {
+  if (!w) return fail(PHE_EINVAL, "phe_weights_shape: null handle");
+  phe_status st = check_dir(w, dir);
+  if (st != PHE_OK) return st;
+  if (rows) *rows = w->dir[dir].rows;
+  if (cols) *cols = w->dir[dir].cols;
+  if (L) *L = w->dir[dir].L;
+  return PHE_OK;
+}
+
+uint64_t phe_weights_device_bytes(const phe_weights* w) { return w ? w->bytes : 0; }
+
+phe_status phe_matmul(phe_ctx* c, const phe_weights* w, int dir, uint32_t T, const uint64_t* d_in_mask,
+                      const uint64_t* d_in_body, void* d_out_mask, void* d_out_body, uint32_t flags, void* stream) {
+  if (!c || !w) return fail(PHE_EINVAL, "phe_matmul: null handle");
+  if (w->ctx != c) return fail(PHE_EINVAL, "phe_matmul: weights belong to another context");
+  phe_status st = check_dir(w, dir);
+  if (st != PHE_OK) return st;
+  if (flags != PHE_OUT_SWITCHED && flags != PHE_OUT_RAW) return fail(PHE_EINVAL, "phe_matmul: flags=%u", flags);
+  if (T == 0) return PHE_OK;
+  if (!d_in_mask || !d_in_body || !d_out_mask || !d_out_body) return fail(PHE_EINVAL, "phe_matmul: null buffer");
+  if (T > (1u << 24)) return fail(PHE_EINVAL, "phe_matmul: T=%u exceeds 2^24", T);
+  DeviceGuard g(c->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  const phe_weights::Dir& D = w->dir[dir];
+  const u32 N = c->prm.N;
+  const int mode = flags == PHE_OUT_RAW ? phe::kOutRaw : phe::kOutSwitched;
+
+  u64* ahat = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&ahat, (size_t)T * D.L * N * sizeof(u64), s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(A_hat)");
+
+  phe::NttJob nj{reinterpret_cast<const u64*>(d_in_mask), ahat, T * D.L};
+  e = phe::launch_input_ntt(c, &nj, 1, s);
+
+  if (e == cudaSuccess) {
+    phe::LweJobTable jt{};
+    jt.n = 1;
+    phe::LweJob& J = jt.j[0];
+    J.what = D.what;
+    J.ahat = ahat;
+    J.out = d_out_mask;
+    J.rows = D.rows;
+    J.T = T;
+    J.L = D.L;
+    J.tok_chunk = 16;
+    J.tiles = D.rows * ((T + J.tok_chunk - 1) / J.tok_chunk);
+    jt.prefix[0] = 0;
+    jt.prefix[1] = J.tiles;
+    e = phe::launch_lwedot(c, jt, mode, 0, s);
+  }
+  if (e == cudaSuccess) {
+    phe::BodyJobTable bt{};
+    bt.n = 1;
+    phe::BodyJob& B = bt.j[0];
+    B.wb = D.wb;
+    B.B = reinterpret_cast<const u64*>(d_in_body);
+    B.out = d_out_body;
+    B.R = D.rows;
+    B.K = D.cols;
+    B.T = T;
+    B.ldB = D.L * N;
+    B.tiles_r = (D.rows + 127) / 128;
+    B.tiles = B.tiles_r * ((T + 15) / 16);
+    bt.prefix[0] = 0;
+    bt.prefix[1] = B.tiles;
+    e = phe::launch_body(c, bt, mode, s);
+  }
+  cudaError_t ef = cudaFreeAsync(ahat, s);
+  if (e != cudaSuccess) return cuda_fail(e, "phe_matmul launch");
+  if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync(A_hat)");
+  return PHE_OK;
+}
+
+phe_status phe_modswitch(phe_ctx* c, const uint64_t* d_in, uint32_t* d_out, size_t n, void* stream) {
+  if (!c) return fail(PHE_EINVAL, "phe_modswitch: null context");
+  if (n == 0) return PHE_OK;
+  if (!d_in || !d_out) return fail(PHE_EINVAL, "phe_modswitch: null buffer");
+  DeviceGuard g(c->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  cudaError_t e = phe::launch_modswitch(c, reinterpret_cast<const u64*>(d_in), d_out, n, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "phe_modswitch launch");
+  return PHE_OK;
+}
+
+phe_status phe_client_encrypt(phe_ctx* c, uint32_t T, uint32_t d, const uint64_t* d_A, const int8_t* d_S,
+                              const int32_t* d_E, const int8_t* d_x, uint64_t delta, uint64_t* d_B, void* stream) {
+  if (!c) return fail(PHE_EINVAL, "phe_client_encrypt: null context");
+  if (T == 0) return PHE_OK;
+  if (d < 1 || d > 16384) return fail(PHE_EINVAL, "phe_client_encrypt: d=%u not in [1, 16384]", d);
+  if (!d_A || !d_S || !d_E || !d_x || !d_B) return fail(PHE_EINVAL, "phe_client_encrypt: null buffer");
+  if (delta >= c->prm.q) return fail(PHE_EINVAL, "phe_client_encrypt: delta must be < q");
+  DeviceGuard g(c->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  const u32 N = c->prm.N;
+  const u32 L = (d + N - 1) / N;
+  const u32 blocks = T * L;
+  u64* ahat = nullptr;
+  ulonglong2* shat = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&ahat, (size_t)blocks * N * sizeof(u64), s);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(A_hat)");
+  e = cudaMallocAsync((void**)&shat, (size_t)N * sizeof(ulonglong2), s);
+  if (e == cudaSuccess) {
+    phe::NttJob nj{reinterpret_cast<const u64*>(d_A), ahat, blocks};
+    e = phe::launch_input_ntt(c, &nj, 1, s);
+  }
+  if (e == cudaSuccess) e = phe::launch_weight_ntt(c, d_S, 1, N, 0, 1, 1, 0, shat, s);
+  if (e == cudaSuccess) {
+    phe::LweJobTable jt{};
+    jt.n = 1;
+    phe::LweJob& J = jt.j[0];
+    J.what = shat;
+    J.ahat = ahat;
+    J.out = d_B;
+    J.err = d_E;
+    J.msg = d_x;
+    J.delta = delta;
+    J.delta_p = shoup(delta, c->prm.q);
+    J.rows = 1;
+    J.T = blocks;
+    J.L = 1;
+    J.tok_chunk = 16;
+    J.msg_d = d;
+    J.tiles = (blocks + 15) / 16;
+    jt.prefix[1] = J.tiles;
+    e = phe::launch_lwedot(c, jt, phe::kOutRing, 0, s);
+  }
+  if (shat) cudaFreeAsync(shat, s);
+  cudaFreeAsync(ahat, s);
+  if (e != cudaSuccess) return cuda_fail(e, "phe_client_encrypt launch");
+  return PHE_OK;
+}
+
+}  // extern "C"

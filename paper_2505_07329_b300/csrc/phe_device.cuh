@@ -1,0 +1,268 @@
+// Device-side modular arithmetic and register-blocked negacyclic NTT passes.
+//
+// Arithmetic follows published methods:
+//   * Shoup's precomputed-quotient multiplication and Harvey's lazy
+//     butterflies (D. Harvey, "Faster arithmetic for number-theoretic
+//     transforms", J. Symb. Comp. 2014): values are kept in [0, 2q) or
+//     [0, 4q) and only reduced where a bound requires it (q < 2^61).
+//   * Negacyclic transforms with the psi-twist merged into the twiddles,
+//     Cooley-Tukey forward (natural in, bit-reversed out) and
+//     Gentleman-Sande inverse (bit-reversed in, natural out) (P. Longa,
+//     M. Naehrig, "Speeding up the number theoretic transform for faster
+//     ideal lattice-based cryptography", CANS 2016).
+//   * Barrett's estimated quotient (P. Barrett, CRYPTO 1986) for the exact
+//     rounding division of the modulus switch.
+#pragma once
+
+#include <cstdint>
+#include <type_traits>
+
+#include <cuda_runtime.h>
+
+namespace phe {
+
+using u64 = unsigned long long;
+using u32 = unsigned int;
+
+// Constants of one ring R_q = Z_q[X]/(X^N+1) and of the switch q -> 2^k.
+struct RingConst {
+  u64 q;          // ciphertext modulus, prime, 2^53 < q < 2^61, q = 1 mod 2N
+  u64 q2;         // 2q
+  u64 half_q;     // floor(q/2)
+  u64 ms_mu;      // floor(2^(64+s) / q), s = floor(log2 q): Barrett constant of the switch
+  u64 red_mu;     // floor(2^64 / q): Barrett constant for reducing a 64-bit word
+  u64 c30;        // 2^30 mod q (recombines the split body accumulators)
+  u64 c30p;       // Shoup quotient of c30
+  u32 ms_s;       // s = floor(log2 q)
+  u32 log2_qout;  // k: output modulus 2^k, 1 <= k <= 32
+};
+
+// x*w mod q in [0, 2q) for any 64-bit x, with w < q and wp = floor(w 2^64 / q).
+__device__ __forceinline__ u64 mul_shoup(u64 x, u64 w, u64 wp, u64 q) {
+  const u64 quo = __umul64hi(wp, x);
+  return x * w - quo * q;
+}
+
+// Gentleman-Sande butterfly, Harvey's lazy form.  In: X, Y in [0, 2q).
+// Out: X <- X + Y, Y <- (X - Y) w, both in [0, 2q).
+__device__ __forceinline__ void gs_bfly(u64& X, u64& Y, u64 w, u64 wp, u64 q, u64 q2) {
+  u64 s = X + Y;
+  s = (s >= q2) ? s - q2 : s;
+  const u64 d = X - Y + q2;
+  Y = mul_shoup(d, w, wp, q);
+  X = s;
+}
+
+// Cooley-Tukey butterfly, Harvey's lazy form.  In: X, Y in [0, 4q).
+// Out: X <- X + Y w, Y <- X - Y w, both in [0, 4q).
+__device__ __forceinline__ void ct_bfly(u64& X, u64& Y, u64 w, u64 wp, u64 q, u64 q2) {
+  const u64 x = (X >= q2) ? X - q2 : X;
+  const u64 t = mul_shoup(Y, w, wp, q);
+  X = x + t;
+  Y = x - t + q2;
+}
+
+__device__ __forceinline__ u64 reduce_2q(u64 x, u64 q) { return (x >= q) ? x - q : x; }
+__device__ __forceinline__ u64 reduce_4q(u64 x, u64 q, u64 q2) {
+  x = (x >= q2) ? x - q2 : x;
+  return (x >= q) ? x - q : x;
+}
+
+// Any 64-bit word to [0, q): quotient estimate floor(c floor(2^64/q) / 2^64)
+// is at most one below floor(c/q) (Barrett), so one correction suffices.
+__device__ __forceinline__ u64 reduce_word(u64 c, const RingConst& rc) {
+  const u64 quo = __umul64hi(c, rc.red_mu);
+  const u64 r = c - quo * rc.q;
+  return (r >= rc.q) ? r - rc.q : r;
+}
+
+// ModulusSwitch q -> 2^k of c in [0, q):
+//   floor((c 2^k + floor(q/2)) / q) mod 2^k   (round half up).
+// X = c 2^k + floor(q/2) < 2^(s+1+k).  With x' = floor(X / 2^s) < 2^(k+1) and
+// mu = floor(2^(64+s)/q), Qt = floor(x' mu / 2^64) satisfies
+// floor(X/q) - 2 <= Qt <= floor(X/q); the remainder X - Qt q < 3q < 2^63 is
+// formed in 64-bit arithmetic and corrected at most twice.
+__device__ __forceinline__ u32 modswitch_word(u64 c, const RingConst& rc) {
+  const u32 k = rc.log2_qout;
+  const u64 lo0 = c << k;
+  const u64 lo = lo0 + rc.half_q;
+  const u64 hi = (c >> (64 - k)) + (lo < lo0 ? 1ull : 0ull);
+  const u64 xs = (lo >> rc.ms_s) | (hi << (64 - rc.ms_s));
+  u64 quo = __umul64hi(xs, rc.ms_mu);
+  u64 r = lo - quo * rc.q;
+  if (r >= rc.q) { r -= rc.q; ++quo; }
+  if (r >= rc.q) { ++quo; }
+  return (u32)(quo & ((k == 32) ? 0xffffffffull : ((1ull << k) - 1)));
+}
+
+// ---------------------------------------------------------------------------
+// Register-blocked NTT of size N = 2^LOGN: P = N/16 threads hold 16 words
+// each.  Stages are grouped into passes of up to four; within a pass every
+// thread owns complete butterfly groups and works in registers; between
+// passes the words move through shared memory.
+//
+// Stage s (0 <= s < LOGN) pairs positions (j, j + 2^s) with bit s of j clear;
+// both transforms use the twiddle at table index (N >> (s+1)) + (j >> (s+1)).
+// ---------------------------------------------------------------------------
+template <int LOGN>
+struct Shape {
+  static constexpr int N = 1 << LOGN;
+  static constexpr int E = 16;                       // words per thread
+  static constexpr int P = N / E;                    // threads per transform
+  static constexpr int NPASS = (LOGN + 3) / 4;
+  static constexpr int TPB = (P < 256) ? 256 : P;    // threads per block
+  static constexpr int SLOTS = TPB / P;              // transforms in flight per block
+  static constexpr int PADN = N + N / 16;            // one pad word per 16: conflict-free exchanges
+};
+
+template <int LOGN, int PASS>
+struct PassShape {
+  static constexpr int S0 = 4 * PASS;                               // first stage of the pass
+  static constexpr int K = (LOGN - S0) < 4 ? (LOGN - S0) : 4;       // stages in the pass
+  static constexpr int G = 1 << K;                                  // words per butterfly group
+  static constexpr int U = 16 / G;                                  // groups per thread
+};
+
+// Position of local word e (= u*G + r) of thread p in pass PASS.
+template <int LOGN, int PASS>
+__device__ __forceinline__ int pass_pos(int p, int e) {
+  using PS = PassShape<LOGN, PASS>;
+  constexpr int P = Shape<LOGN>::P;
+  const int u = e / PS::G, r = e % PS::G;
+  const int g = u * P + p;
+  const int base = ((g >> PS::S0) << (PS::S0 + PS::K)) | (g & ((1 << PS::S0) - 1));
+  return base + (r << PS::S0);
+}
+
+__device__ __forceinline__ int pad_idx(int pos) { return pos + (pos >> 4); }
+
+// Slot of the pass-0 twiddle used by stage st (0..3), twiddle b of the group.
+__host__ __device__ constexpr int pass0_slot(int st, int b) { return (16 - (16 >> st)) + b; }
+
+// Compile-time loop: f(std::integral_constant<int, I>) for I in [B, E).
+template <int B, int E, typename F>
+__device__ __forceinline__ void static_for(F&& f) {
+  if constexpr (B < E) {
+    f(std::integral_constant<int, B>{});
+    static_for<B + 1, E>(f);
+  }
+}
+
+// One stage of a pass: stage ST of pass PASS (ST counted inside the pass).
+// Every twiddle is loaded once and applied to the 2^ST butterflies sharing it.
+template <int LOGN, int PASS, int ST, bool INVERSE>
+__device__ __forceinline__ void pass_stage(u64 (&x)[16], int p, const ulonglong2* __restrict__ tw0,
+                                           const ulonglong2* __restrict__ twc, u64 q, u64 q2) {
+  using PS = PassShape<LOGN, PASS>;
+  constexpr int N = Shape<LOGN>::N;
+  constexpr int P = Shape<LOGN>::P;
+  constexpr int s = PS::S0 + ST;
+  constexpr int h = 1 << ST;
+  constexpr int NB = PS::G >> (ST + 1);  // distinct twiddles per group
+#pragma unroll
+  for (int u = 0; u < PS::U; ++u) {
+#pragma unroll
+    for (int b = 0; b < NB; ++b) {
+      ulonglong2 w;
+      if constexpr (PASS == 0) {
+        w = __ldg(&tw0[pass0_slot(ST, b) * P + p]);
+      } else {
+        const int j = pass_pos<LOGN, PASS>(p, u * PS::G + b * 2 * h);
+        w = __ldg(&twc[(N >> (s + 1)) + (j >> (s + 1))]);
+      }
+#pragma unroll
+      for (int c = 0; c < h; ++c) {
+        const int e0 = u * PS::G + b * 2 * h + c;
+        if constexpr (INVERSE) gs_bfly(x[e0], x[e0 + h], w.x, w.y, q, q2);
+        else ct_bfly(x[e0], x[e0 + h], w.x, w.y, q, q2);
+      }
+    }
+  }
+}
+
+// Inverse (Gentleman-Sande) pass: stages S0 .. S0+K-1 ascending.
+// tw0: pass-0 table, thread-major [15][P]; twc: compact table [N].
+template <int LOGN, int PASS>
+__device__ __forceinline__ void gs_pass(u64 (&x)[16], int p, const ulonglong2* __restrict__ tw0,
+                                        const ulonglong2* __restrict__ twc, u64 q, u64 q2) {
+  static_for<0, PassShape<LOGN, PASS>::K>([&](auto st) {
+    pass_stage<LOGN, PASS, decltype(st)::value, true>(x, p, tw0, twc, q, q2);
+  });
+}
+
+// Forward (Cooley-Tukey) pass: stages S0+K-1 .. S0 descending.
+template <int LOGN, int PASS>
+__device__ __forceinline__ void ct_pass(u64 (&x)[16], int p, const ulonglong2* __restrict__ tw0,
+                                        const ulonglong2* __restrict__ twc, u64 q, u64 q2) {
+  constexpr int K = PassShape<LOGN, PASS>::K;
+  static_for<0, K>([&](auto i) {
+    pass_stage<LOGN, PASS, K - 1 - decltype(i)::value, false>(x, p, tw0, twc, q, q2);
+  });
+}
+
+// Move the 16 words of every thread from pass A's positions to pass B's.
+// Two barriers: the buffer is reused by the next exchange.
+template <int LOGN, int PA, int PB>
+__device__ __forceinline__ void exchange(u64 (&x)[16], int p, u64* __restrict__ buf) {
+#pragma unroll
+  for (int e = 0; e < 16; ++e) buf[pad_idx(pass_pos<LOGN, PA>(p, e))] = x[e];
+  __syncthreads();
+#pragma unroll
+  for (int e = 0; e < 16; ++e) x[e] = buf[pad_idx(pass_pos<LOGN, PB>(p, e))];
+  __syncthreads();
+}
+
+// Full inverse transform (no N^-1 scaling): bit-reversed in (pass-0 layout),
+// natural order out (last-pass layout).  Values in [0, 2q) in and out.
+template <int LOGN>
+__device__ __forceinline__ void intt_regs(u64 (&x)[16], int p, u64* buf, const ulonglong2* tw0,
+                                          const ulonglong2* twc, u64 q, u64 q2) {
+  gs_pass<LOGN, 0>(x, p, tw0, twc, q, q2);
+  if constexpr (Shape<LOGN>::NPASS > 1) {
+    exchange<LOGN, 0, 1>(x, p, buf);
+    gs_pass<LOGN, 1>(x, p, tw0, twc, q, q2);
+  }
+  if constexpr (Shape<LOGN>::NPASS > 2) {
+    exchange<LOGN, 1, 2>(x, p, buf);
+    gs_pass<LOGN, 2>(x, p, tw0, twc, q, q2);
+  }
+  if constexpr (Shape<LOGN>::NPASS > 3) {
+    exchange<LOGN, 2, 3>(x, p, buf);
+    gs_pass<LOGN, 3>(x, p, tw0, twc, q, q2);
+  }
+}
+
+// Full forward transform: natural order in (last-pass layout), bit-reversed
+// out (pass-0 layout).  Values in [0, 4q) in and out.
+template <int LOGN>
+__device__ __forceinline__ void ntt_regs(u64 (&x)[16], int p, u64* buf, const ulonglong2* tw0,
+                                         const ulonglong2* twc, u64 q, u64 q2) {
+  constexpr int NP = Shape<LOGN>::NPASS;
+  if constexpr (NP > 3) {
+    ct_pass<LOGN, 3>(x, p, tw0, twc, q, q2);
+    exchange<LOGN, 3, 2>(x, p, buf);
+  }
+  if constexpr (NP > 2) {
+    ct_pass<LOGN, 2>(x, p, tw0, twc, q, q2);
+    exchange<LOGN, 2, 1>(x, p, buf);
+  }
+  if constexpr (NP > 1) {
+    ct_pass<LOGN, 1>(x, p, tw0, twc, q, q2);
+    exchange<LOGN, 1, 0>(x, p, buf);
+  }
+  ct_pass<LOGN, 0>(x, p, tw0, twc, q, q2);
+}
+
+// Layout of transformed inputs (A_hat): word r of pass-0 thread p of a block
+// of N words, pair-interleaved so that a warp reads 512 contiguous bytes.
+template <int LOGN>
+__device__ __forceinline__ int ahat_idx(int p, int r) {
+  return (((r >> 1) * Shape<LOGN>::P + p) << 1) | (r & 1);
+}
+// Layout of transformed weights (W_hat, stored as (w, w') pairs): pair r of thread p.
+template <int LOGN>
+__device__ __forceinline__ int what_idx(int p, int r) {
+  return r * Shape<LOGN>::P + p;
+}
+
+}  // namespace phe

@@ -1,0 +1,100 @@
+// Host-side structures of libphe shared by the C-ABI layer and the kernel
+// launchers.  Not part of the public interface (include/phe.h).
+#pragma once
+
+#include <cstddef>
+#include <cstdint>
+#include <string>
+
+#include <cuda_runtime.h>
+
+#include "phe_device.cuh"
+#include "../../include/phe.h"
+
+namespace phe {
+
+constexpr int kMaxJobs = 32;      // jobs in one batched launch (passed by value)
+constexpr int kMinLogN = 8;
+constexpr int kMaxLogN = 13;
+
+// One matrix product of the hot path, as the lwedot kernel sees it.
+struct LweJob {
+  const ulonglong2* what;   // W_hat pairs [rows][L][N] (what_idx layout)
+  const u64* ahat;          // A_hat [T][L][N] (ahat_idx layout)
+  void* out;                // mask out: [T][rows][N] u32 (switched) or u64 (raw / ring product)
+  const int32_t* err;       // client encryption only: E [T*L][N]
+  const int8_t* msg;        // client encryption only: x [T][msg_d]
+  u64 delta, delta_p;       // client encryption only: delta and its Shoup quotient
+  u32 rows, T, L, tok_chunk, tiles, msg_d;
+};
+struct LweJobTable {
+  u32 n;
+  u32 prefix[kMaxJobs + 1];  // tile prefix sums
+  LweJob j[kMaxJobs];
+};
+
+struct BodyJob {
+  const uint32_t* wb;       // packed weights [ceil(K/4)][R], 4 int8 per word
+  const u64* B;             // body words, token t at B + t*ldB, k < K used
+  void* out;                // [T][R] u32 (switched) or u64 (raw)
+  u32 R, K, T, ldB, tiles_r, tiles;
+};
+struct BodyJobTable {
+  u32 n;
+  u32 prefix[kMaxJobs + 1];
+  BodyJob j[kMaxJobs];
+};
+
+struct NttJob {             // forward transform of T*L input blocks
+  const u64* src;           // natural order [blocks][N]
+  u64* dst;                 // A_hat layout [blocks][N]
+  u32 blocks;
+};
+
+enum OutMode : int { kOutSwitched = 0, kOutRaw = 1, kOutRing = 2 };
+
+struct Tables {
+  ulonglong2* fwd_c = nullptr;  // psi^brv(k) and Shoup quotient, [N]
+  ulonglong2* inv_c = nullptr;  // psi^-brv(k) and Shoup quotient, [N]
+  ulonglong2* fwd_0 = nullptr;  // pass-0 forward twiddles, thread-major [15][P]
+  ulonglong2* inv_0 = nullptr;  // pass-0 inverse twiddles, thread-major [15][P]
+};
+
+}  // namespace phe
+
+struct phe_ctx {
+  phe_params prm;
+  int device = 0;
+  int logn = 0;
+  phe::RingConst rc{};
+  phe::u64 n_inv = 0, n_inv_p = 0;  // N^-1 mod q and its Shoup quotient
+  phe::Tables tab;
+  int num_sms = 0;
+};
+
+struct phe_weights {
+  phe_ctx* ctx = nullptr;
+  uint32_t d_out = 0, d_in = 0, dirs = 0;
+  struct Dir {
+    ulonglong2* what = nullptr;  // [rows][L][N] pairs
+    uint32_t* wb = nullptr;      // [ceil(cols/4)][rows]
+    uint32_t rows = 0, cols = 0, L = 0;
+  } dir[2];
+  uint64_t bytes = 0;
+};
+
+namespace phe {
+
+// Launchers (phe_kernels.cu).  All asynchronous on `s`.
+cudaError_t launch_input_ntt(const phe_ctx* c, const NttJob* jobs, int n, cudaStream_t s);
+cudaError_t launch_weight_ntt(const phe_ctx* c, const int8_t* W, u32 rows, u32 cols, u32 row_stride,
+                              u32 col_stride, u32 L, int rev, ulonglong2* what, cudaStream_t s);
+cudaError_t launch_lwedot(const phe_ctx* c, const LweJobTable& jt, int mode, int grid_limit, cudaStream_t s);
+cudaError_t launch_body(const phe_ctx* c, const BodyJobTable& jt, int mode, cudaStream_t s);
+cudaError_t launch_modswitch(const phe_ctx* c, const u64* in, u32* out, size_t n, cudaStream_t s);
+cudaError_t launch_pack_body_weights(const int8_t* W, u32 rows, u32 cols, u32 row_stride, u32 col_stride,
+                                     uint32_t* wb, cudaStream_t s);
+int lwedot_threads(int logn);
+size_t lwedot_smem(int logn);
+
+}  // namespace phe

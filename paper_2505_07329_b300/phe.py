@@ -1,0 +1,161 @@
+"""Thin Python binding of libphe (include/phe.h): argument marshalling only.
+
+Function names match the C ABI.  Device buffers are passed as torch CUDA
+tensors (or raw integer device pointers), host buffers as numpy arrays.
+Every call raises PheError when the library returns a status other than
+PHE_OK.  There is no fallback: if libphe.so is missing, loading fails.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+import threading
+
+PKG = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(PKG, "libphe.so")
+
+PHE_OK, PHE_EINVAL, PHE_ENOMEM, PHE_EBUSY, PHE_ETIMEOUT, PHE_ECUDA, PHE_EUNSUPPORTED = range(7)
+PHE_FWD, PHE_BWD = 0, 1
+PHE_DIR_FWD_BIT, PHE_DIR_BWD_BIT = 1, 2
+PHE_OUT_SWITCHED, PHE_OUT_RAW = 0, 1
+
+
+class PheError(RuntimeError):
+    def __init__(self, status: int, name: str, message: str):
+        super().__init__(f"{name}: {message}")
+        self.status = status
+        self.name = name
+
+
+class phe_params(ctypes.Structure):
+    _fields_ = [("N", ctypes.c_uint32), ("log2_qout", ctypes.c_uint32), ("q", ctypes.c_uint64)]
+
+
+_vp = ctypes.c_void_p
+_u32 = ctypes.c_uint32
+_u64 = ctypes.c_uint64
+_i32 = ctypes.c_int
+_sz = ctypes.c_size_t
+
+# name -> (restype, argtypes); the C-ABI surface declared in include/phe.h.
+SIGNATURES = {
+    "phe_status_string": (ctypes.c_char_p, [_i32]),
+    "phe_last_error": (ctypes.c_char_p, []),
+    "phe_ctx_create": (_i32, [ctypes.POINTER(phe_params), _i32, ctypes.POINTER(_vp)]),
+    "phe_ctx_destroy": (None, [_vp]),
+    "phe_weights_upload": (_i32, [_vp, _vp, _u32, _u32, _u32, _vp, ctypes.POINTER(_vp)]),
+    "phe_weights_free": (None, [_vp]),
+    "phe_weights_shape": (_i32, [_vp, _i32, ctypes.POINTER(_u32), ctypes.POINTER(_u32), ctypes.POINTER(_u32)]),
+    "phe_weights_device_bytes": (_u64, [_vp]),
+    "phe_matmul": (_i32, [_vp, _vp, _i32, _u32, _vp, _vp, _vp, _vp, _u32, _vp]),
+    "phe_modswitch": (_i32, [_vp, _vp, _vp, _sz, _vp]),
+    "phe_client_encrypt": (_i32, [_vp, _u32, _u32, _vp, _vp, _vp, _vp, _u64, _vp, _vp]),
+}
+
+_lib = None
+_lock = threading.Lock()
+
+
+def lib() -> ctypes.CDLL:
+    """Load libphe.so (raises if it has not been built)."""
+    global _lib
+    with _lock:
+        if _lib is None:
+            if not os.path.exists(LIB_PATH):
+                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+                                   "`python -m paper_2505_07329_b300.build` (or __graft_entry__.build())")
+            L = ctypes.CDLL(LIB_PATH)
+            for name, (res, args) in SIGNATURES.items():
+                f = getattr(L, name)
+                f.restype = res
+                f.argtypes = args
+            _lib = L
+    return _lib
+
+
+def _check(status: int) -> None:
+    if status != PHE_OK:
+        L = lib()
+        raise PheError(status, L.phe_status_string(status).decode(), L.phe_last_error().decode())
+
+
+def _dptr(x):
+    """Device pointer of a torch CUDA tensor (must be contiguous), an int, or None."""
+    if x is None:
+        return None
+    if isinstance(x, int):
+        return x
+    if hasattr(x, "data_ptr"):
+        if not x.is_cuda:
+            raise ValueError("expected a CUDA tensor")
+        if not x.is_contiguous():
+            raise ValueError("expected a contiguous tensor")
+        return x.data_ptr()
+    raise TypeError(f"cannot take a device pointer of {type(x)}")
+
+
+def _stream(s):
+    if s is None:
+        import torch
+        return torch.cuda.current_stream().cuda_stream
+    if isinstance(s, int):
+        return s
+    return s.cuda_stream
+
+
+def phe_status_string(status: int) -> str:
+    return lib().phe_status_string(status).decode()
+
+
+def phe_last_error() -> str:
+    return lib().phe_last_error().decode()
+
+
+def phe_ctx_create(N: int, q: int, log2_qout: int, device: int = 0):
+    prm = phe_params(N, log2_qout, q)
+    out = _vp()
+    _check(lib().phe_ctx_create(ctypes.byref(prm), device, ctypes.byref(out)))
+    return out
+
+
+def phe_ctx_destroy(ctx) -> None:
+    lib().phe_ctx_destroy(ctx)
+
+
+def phe_weights_upload(ctx, W, dirs: int = PHE_DIR_FWD_BIT | PHE_DIR_BWD_BIT, stream=None):
+    """W: host int8 array [d_out, d_in] (numpy or CPU torch tensor)."""
+    import numpy as np
+    Wn = np.ascontiguousarray(W.numpy() if hasattr(W, "numpy") else np.asarray(W), dtype=np.int8)
+    d_out, d_in = Wn.shape
+    out = _vp()
+    _check(lib().phe_weights_upload(ctx, Wn.ctypes.data, d_out, d_in, dirs, _stream(stream), ctypes.byref(out)))
+    return out
+
+
+def phe_weights_free(w) -> None:
+    lib().phe_weights_free(w)
+
+
+def phe_weights_shape(w, direction: int):
+    r, c, L = _u32(), _u32(), _u32()
+    _check(lib().phe_weights_shape(w, direction, ctypes.byref(r), ctypes.byref(c), ctypes.byref(L)))
+    return r.value, c.value, L.value
+
+
+def phe_weights_device_bytes(w) -> int:
+    return int(lib().phe_weights_device_bytes(w))
+
+
+def phe_matmul(ctx, w, direction: int, T: int, in_mask, in_body, out_mask, out_body,
+               flags: int = PHE_OUT_SWITCHED, stream=None) -> None:
+    _check(lib().phe_matmul(ctx, w, direction, T, _dptr(in_mask), _dptr(in_body), _dptr(out_mask),
+                            _dptr(out_body), flags, _stream(stream)))
+
+
+def phe_modswitch(ctx, d_in, d_out, n: int, stream=None) -> None:
+    _check(lib().phe_modswitch(ctx, _dptr(d_in), _dptr(d_out), n, _stream(stream)))
+
+
+def phe_client_encrypt(ctx, T: int, d: int, A, S, E, x, delta: int, B, stream=None) -> None:
+    _check(lib().phe_client_encrypt(ctx, T, d, _dptr(A), _dptr(S), _dptr(E), _dptr(x), delta, _dptr(B),
+                                    _stream(stream)))

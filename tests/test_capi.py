@@ -1,0 +1,74 @@
+"""CPU-only checks of the C ABI: the library loads without a GPU, exports every
+entry point include/phe.h declares, and rejects bad parameter sets on the host
+before any CUDA call."""
+import ctypes
+import os
+import re
+
+import pytest
+
+import synth
+from paper_2505_07329_b300 import build, phe
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def header_functions():
+    names = set()
+    for hdr in os.listdir(os.path.join(ROOT, "include")):
+        if hdr.endswith(".h"):
+            text = open(os.path.join(ROOT, "include", hdr)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"^[A-Za-z_][\w\s\*]*?\b(phe_\w+)\s*\(", text, flags=re.M))
+    return names
+
+
+@pytest.fixture(scope="module")
+def L():
+    build.build()
+    return phe.lib()
+
+
+def test_library_exports_every_declared_symbol(L):
+    names = header_functions()
+    assert len(names) >= 10
+    for n in sorted(names):
+        assert hasattr(L, n), f"libphe.so does not export {n}"
+
+
+def test_binding_covers_the_header():
+    assert set(phe.SIGNATURES) == header_functions()
+
+
+def test_status_strings(L):
+    for code, name in enumerate(["PHE_OK", "PHE_EINVAL", "PHE_ENOMEM", "PHE_EBUSY", "PHE_ETIMEOUT",
+                                 "PHE_ECUDA", "PHE_EUNSUPPORTED"]):
+        assert phe.phe_status_string(code) == name
+
+
+@pytest.mark.parametrize("N,q,k,msg", [
+    (1000, synth.Q60, 32, "power of two"),
+    (128, synth.Q60, 32, "power of two"),
+    (16384, synth.Q60, 32, "power of two"),
+    (4096, synth.Q60 + 2, 32, "not 1 mod 2N"),
+    (4096, (1 << 60) + 8193 * 2, 32, "not 1 mod"),
+    (4096, 1 + 8192 * 3 * (2 ** 50 // 8192) * 8, 32, "not prime"),
+    (4096, (1 << 52) + 1, 32, "2^53 < q"),
+    (4096, synth.Q60, 0, "log2_qout"),
+    (4096, synth.Q60, 33, "log2_qout"),
+])
+def test_ctx_create_rejects_bad_parameters(L, N, q, k, msg):
+    with pytest.raises(phe.PheError) as ei:
+        phe.phe_ctx_create(N, q, k, 0)
+    assert ei.value.status == phe.PHE_EINVAL
+    assert msg in str(ei.value)
+
+
+def test_null_arguments_are_rejected(L):
+    assert L.phe_ctx_create(None, 0, None) == phe.PHE_EINVAL
+    assert L.phe_matmul(None, None, 0, 1, None, None, None, None, 0, None) == phe.PHE_EINVAL
+    assert L.phe_modswitch(None, None, None, 0, None) == phe.PHE_EINVAL
+    assert L.phe_weights_upload(None, None, 1, 1, 1, None, None) == phe.PHE_EINVAL
+    assert phe.phe_weights_device_bytes(None) == 0
+    L.phe_ctx_destroy(None)
+    L.phe_weights_free(None)
