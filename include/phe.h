@@ -123,6 +123,36 @@ phe_status phe_matmul(phe_ctx* ctx, const phe_weights* w, int dir, uint32_t T, c
  * mod q first.  Errors: PHE_EINVAL, PHE_ECUDA. */
 phe_status phe_modswitch(phe_ctx* ctx, const uint64_t* d_in, uint32_t* d_out, size_t n, void* stream);
 
+/* End-to-end form with HOST buffers: copies the inputs host->device, runs
+ * the hot path and copies the results device->host, token chunk by token
+ * chunk, so that device memory stays bounded (at most `max_chunk_bytes` of
+ * device outputs per chunk; 0 selects 1 GiB).  h_* are host pointers with the
+ * same layouts as phe_matmul's device buffers; page-locked host memory makes
+ * the copies asynchronous.  Blocking: returns after the last result has
+ * reached the host (the stream is synchronized).  Errors: as phe_matmul. */
+phe_status phe_matmul_host(phe_ctx* ctx, const phe_weights* w, int dir, uint32_t T, const uint64_t* h_in_mask,
+                           const uint64_t* h_in_body, void* h_out_mask, void* h_out_body, uint32_t flags,
+                           uint64_t max_chunk_bytes, void* stream);
+
+/* Tracing (for measurement): while enabled, every kernel the library
+ * launches with this context is bracketed by CUDA events recorded on the
+ * launching stream, and every phe_matmul call by a pair around the whole
+ * call.  phe_trace_read waits for the recorded events, fills up to `cap`
+ * entries (one per kernel name, plus "phe_matmul" for whole calls) and
+ * clears the record.  Not thread-safe: trace one stream at a time.
+ * Errors: PHE_EINVAL, PHE_ECUDA. */
+typedef struct phe_trace_entry {
+    char name[32];
+    uint64_t launches;
+    double total_ms;
+    double p50_ms;
+    double p99_ms;
+    double max_ms;
+} phe_trace_entry;
+
+phe_status phe_trace_enable(phe_ctx* ctx, int on);
+phe_status phe_trace_read(phe_ctx* ctx, phe_trace_entry* out, uint32_t cap, uint32_t* n_out);
+
 /* Client-side helper for tests and benchmarks (not part of the server
  * path, which never holds the key): RLWE encryption of T int8 vectors of
  * length d (Sec. 3.1, blocks of Sec. 4.3.1):

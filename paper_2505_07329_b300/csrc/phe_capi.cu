@@ -1,5 +1,7 @@
 // C ABI of libphe (include/phe.h): parameter validation, twiddle tables,
 // weight upload and the per-call hot path.
+#include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <cstring>
@@ -121,6 +123,85 @@ phe_status check_dir(const phe_weights* w, int dir) {
   return PHE_OK;
 }
 
+cudaEvent_t trace_event(phe_ctx* c) {
+  if (!c->tracer.pool.empty()) {
+    cudaEvent_t e = c->tracer.pool.back();
+    c->tracer.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Brackets one launch (or one call) with events on its stream while tracing is on.
+struct Span {
+  phe_ctx* c;
+  int kid;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  Span(phe_ctx* c_, int kid_, cudaStream_t s_) : c(c_), kid(kid_), s(s_) {
+    if (c->tracer.on && (a = trace_event(c)) != nullptr) cudaEventRecord(a, s);
+  }
+  ~Span() {
+    if (!a) return;
+    cudaEvent_t b = trace_event(c);
+    if (!b) {
+      c->tracer.pool.push_back(a);
+      return;
+    }
+    cudaEventRecord(b, s);
+    c->tracer.recs.push_back({kid, a, b});
+  }
+};
+
+// The device form of the hot path for one projection.
+cudaError_t matmul_device(phe_ctx* c, const phe_weights::Dir& D, u32 T, const u64* in_mask, const u64* in_body,
+                          void* out_mask, void* out_body, int mode, cudaStream_t s) {
+  const u32 N = c->prm.N;
+  Span call(c, phe::kKCall, s);
+  u64* ahat = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&ahat, (size_t)T * D.L * N * sizeof(u64), s);
+  if (e != cudaSuccess) return e;
+  {
+    Span sp(c, phe::kKInputNtt, s);
+    phe::NttJob nj{in_mask, ahat, T * D.L};
+    e = phe::launch_input_ntt(c, &nj, 1, s);
+  }
+  if (e == cudaSuccess) {
+    phe::LweJobTable jt{};
+    jt.n = 1;
+    phe::LweJob& J = jt.j[0];
+    J.what = D.what;
+    J.ahat = ahat;
+    J.out = out_mask;
+    J.wrow = D.wrow;
+    J.bin = in_body;
+    J.out_body = out_body;
+    J.rows = D.rows;
+    J.cols = D.cols;
+    J.T = T;
+    J.L = D.L;
+    J.tok_chunk = 16;
+    J.tiles = D.rows * ((T + J.tok_chunk - 1) / J.tok_chunk);
+    jt.prefix[0] = 0;
+    jt.prefix[1] = J.tiles;
+    Span sp(c, phe::kKLwedot, s);
+    e = phe::launch_lwedot(c, jt, mode, 0, s);
+  }
+  cudaError_t ef = cudaFreeAsync(ahat, s);
+  return e != cudaSuccess ? e : ef;
+}
+
+phe_status check_matmul_args(phe_ctx* c, const phe_weights* w, int dir, uint32_t flags) {
+  if (!c || !w) return fail(PHE_EINVAL, "phe_matmul: null handle");
+  if (w->ctx != c) return fail(PHE_EINVAL, "phe_matmul: weights belong to another context");
+  phe_status st = check_dir(w, dir);
+  if (st != PHE_OK) return st;
+  if (flags != PHE_OUT_SWITCHED && flags != PHE_OUT_RAW) return fail(PHE_EINVAL, "phe_matmul: flags=%u", flags);
+  return PHE_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -172,6 +253,7 @@ phe_status phe_ctx_create(const phe_params* prm, int device, phe_ctx** out) {
   phe::RingConst& rc = c->rc;
   rc.q = q;
   rc.q2 = 2 * q;
+  rc.q4 = 4 * q;
   rc.half_q = q / 2;
   rc.ms_s = (u32)floor_log2(q);
   rc.ms_mu = (u64)(((u128)1 << (64 + rc.ms_s)) / q);
@@ -222,6 +304,13 @@ phe_status phe_ctx_create(const phe_params* prm, int device, phe_ctx** out) {
 void phe_ctx_destroy(phe_ctx* c) {
   if (!c) return;
   DeviceGuard g(c->device);
+  for (auto& s : c->side)
+    if (s) cudaStreamDestroy(s);
+  for (auto& r : c->tracer.recs) {
+    cudaEventDestroy(r.a);
+    cudaEventDestroy(r.b);
+  }
+  for (auto e : c->tracer.pool) cudaEventDestroy(e);
   free_tables(c->tab);
   delete c;
 }
@@ -244,28 +333,29 @@ phe_status phe_weights_upload(phe_ctx* c, const int8_t* h_W, uint32_t d_out, uin
   w->d_in = d_in;
   w->dirs = dirs;
   const u32 N = c->prm.N;
-  int8_t* dW = nullptr;
   const size_t wbytes = (size_t)d_out * d_in;
-  cudaError_t e = cudaMalloc(&dW, wbytes);
-  if (e != cudaSuccess) { delete w; return cuda_fail(e, "cudaMalloc(W)"); }
-  e = cudaMemcpyAsync(dW, h_W, wbytes, cudaMemcpyHostToDevice, s);
+  std::vector<int8_t> WT;
+  if (dirs & PHE_DIR_BWD_BIT) {
+    WT.resize(wbytes);
+    for (u32 j = 0; j < d_out; ++j)
+      for (u32 k = 0; k < d_in; ++k) WT[(size_t)k * d_out + j] = h_W[(size_t)j * d_in + k];
+  }
+  cudaError_t e = cudaSuccess;
   for (int dir = 0; dir < 2 && e == cudaSuccess; ++dir) {
     if (!(dirs & (1u << dir))) continue;
     phe_weights::Dir& D = w->dir[dir];
     D.rows = dir == PHE_FWD ? d_out : d_in;
     D.cols = dir == PHE_FWD ? d_in : d_out;
     D.L = (D.cols + N - 1) / N;
-    const u32 rs = dir == PHE_FWD ? d_in : 1, cs = dir == PHE_FWD ? 1 : d_in;
     const size_t what_bytes = (size_t)D.rows * D.L * N * sizeof(ulonglong2);
-    const size_t wb_bytes = (size_t)((D.cols + 3) / 4) * D.rows * sizeof(uint32_t);
     if ((e = cudaMalloc(&D.what, what_bytes)) != cudaSuccess) break;
-    if ((e = cudaMalloc(&D.wb, wb_bytes)) != cudaSuccess) break;
-    w->bytes += what_bytes + wb_bytes;
-    if ((e = phe::launch_weight_ntt(c, dW, D.rows, D.cols, rs, cs, D.L, 1, D.what, s)) != cudaSuccess) break;
-    if ((e = phe::launch_pack_body_weights(dW, D.rows, D.cols, rs, cs, D.wb, s)) != cudaSuccess) break;
+    if ((e = cudaMalloc(&D.wrow, wbytes)) != cudaSuccess) break;
+    w->bytes += what_bytes + wbytes;
+    const int8_t* src = dir == PHE_FWD ? h_W : WT.data();
+    if ((e = cudaMemcpyAsync(D.wrow, src, wbytes, cudaMemcpyHostToDevice, s)) != cudaSuccess) break;
+    if ((e = phe::launch_weight_ntt(c, D.wrow, D.rows, D.cols, D.cols, 1, D.L, 1, D.what, s)) != cudaSuccess) break;
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
-  cudaFree(dW);
   if (e != cudaSuccess) {
     phe_weights_free(w);
     return cuda_fail(e, "phe_weights_upload");
@@ -279,7 +369,7 @@ void phe_weights_free(phe_weights* w) {
   DeviceGuard g(w->ctx->device);
   for (auto& D : w->dir) {
     cudaFree(D.what);
-    cudaFree(D.wb);
+    cudaFree(D.wrow);
   }
   delete w;
 }
@@ -298,64 +388,130 @@ uint64_t phe_weights_device_bytes(const phe_weights* w) { return w ? w->bytes : 
 
 phe_status phe_matmul(phe_ctx* c, const phe_weights* w, int dir, uint32_t T, const uint64_t* d_in_mask,
                       const uint64_t* d_in_body, void* d_out_mask, void* d_out_body, uint32_t flags, void* stream) {
-  if (!c || !w) return fail(PHE_EINVAL, "phe_matmul: null handle");
-  if (w->ctx != c) return fail(PHE_EINVAL, "phe_matmul: weights belong to another context");
-  phe_status st = check_dir(w, dir);
+  phe_status st = check_matmul_args(c, w, dir, flags);
   if (st != PHE_OK) return st;
-  if (flags != PHE_OUT_SWITCHED && flags != PHE_OUT_RAW) return fail(PHE_EINVAL, "phe_matmul: flags=%u", flags);
   if (T == 0) return PHE_OK;
   if (!d_in_mask || !d_in_body || !d_out_mask || !d_out_body) return fail(PHE_EINVAL, "phe_matmul: null buffer");
   if (T > (1u << 24)) return fail(PHE_EINVAL, "phe_matmul: T=%u exceeds 2^24", T);
   DeviceGuard g(c->device);
   if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
-  cudaStream_t s = (cudaStream_t)stream;
+  const int mode = flags == PHE_OUT_RAW ? phe::kOutRaw : phe::kOutSwitched;
+  cudaError_t e = matmul_device(c, w->dir[dir], T, reinterpret_cast<const u64*>(d_in_mask),
+                                reinterpret_cast<const u64*>(d_in_body), d_out_mask, d_out_body, mode,
+                                (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "phe_matmul");
+  return PHE_OK;
+}
+
+phe_status phe_matmul_host(phe_ctx* c, const phe_weights* w, int dir, uint32_t T, const uint64_t* h_in_mask,
+                           const uint64_t* h_in_body, void* h_out_mask, void* h_out_body, uint32_t flags,
+                           uint64_t max_chunk_bytes, void* stream) {
+  phe_status st = check_matmul_args(c, w, dir, flags);
+  if (st != PHE_OK) return st;
+  if (T == 0) return PHE_OK;
+  if (!h_in_mask || !h_in_body || !h_out_mask || !h_out_body) return fail(PHE_EINVAL, "phe_matmul_host: null buffer");
+  if (T > (1u << 24)) return fail(PHE_EINVAL, "phe_matmul_host: T=%u exceeds 2^24", T);
+  DeviceGuard g(c->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
   const phe_weights::Dir& D = w->dir[dir];
   const u32 N = c->prm.N;
   const int mode = flags == PHE_OUT_RAW ? phe::kOutRaw : phe::kOutSwitched;
-
-  u64* ahat = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&ahat, (size_t)T * D.L * N * sizeof(u64), s);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(A_hat)");
-
-  phe::NttJob nj{reinterpret_cast<const u64*>(d_in_mask), ahat, T * D.L};
-  e = phe::launch_input_ntt(c, &nj, 1, s);
-
-  if (e == cudaSuccess) {
-    phe::LweJobTable jt{};
-    jt.n = 1;
-    phe::LweJob& J = jt.j[0];
-    J.what = D.what;
-    J.ahat = ahat;
-    J.out = d_out_mask;
-    J.rows = D.rows;
-    J.T = T;
-    J.L = D.L;
-    J.tok_chunk = 16;
-    J.tiles = D.rows * ((T + J.tok_chunk - 1) / J.tok_chunk);
-    jt.prefix[0] = 0;
-    jt.prefix[1] = J.tiles;
-    e = phe::launch_lwedot(c, jt, mode, 0, s);
+  const size_t osz = mode == phe::kOutRaw ? 8 : 4;
+  const size_t in_tok = (size_t)D.L * N * sizeof(u64);
+  const size_t om_tok = (size_t)D.rows * N * osz, ob_tok = (size_t)D.rows * osz;
+  if (max_chunk_bytes == 0) max_chunk_bytes = 1ull << 30;
+  u32 tc = (u32)(max_chunk_bytes / (om_tok + ob_tok));
+  if (tc < 1) tc = 1;
+  if (tc > T) tc = T;
+  cudaStream_t caller = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+    if (!c->side[i]) e = cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+  cudaEvent_t ev = nullptr;
+  if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+  e = cudaEventRecord(ev, caller);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(c->side[i], ev, 0);
+  // Two buffer sets on two streams: chunk n uses set n % 2, so the copies of
+  // one chunk overlap the kernels of the next.
+  struct Buf { u64 *a = nullptr, *b = nullptr; char *om = nullptr, *ob = nullptr; } buf[2];
+  const u32 nchunks = (T + tc - 1) / tc;
+  for (int i = 0; i < 2 && i < (int)nchunks && e == cudaSuccess; ++i) {
+    cudaStream_t s = c->side[i];
+    if ((e = cudaMallocAsync((void**)&buf[i].a, tc * in_tok, s)) != cudaSuccess) break;
+    if ((e = cudaMallocAsync((void**)&buf[i].b, tc * in_tok, s)) != cudaSuccess) break;
+    if ((e = cudaMallocAsync((void**)&buf[i].om, tc * om_tok, s)) != cudaSuccess) break;
+    e = cudaMallocAsync((void**)&buf[i].ob, tc * ob_tok, s);
   }
-  if (e == cudaSuccess) {
-    phe::BodyJobTable bt{};
-    bt.n = 1;
-    phe::BodyJob& B = bt.j[0];
-    B.wb = D.wb;
-    B.B = reinterpret_cast<const u64*>(d_in_body);
-    B.out = d_out_body;
-    B.R = D.rows;
-    B.K = D.cols;
-    B.T = T;
-    B.ldB = D.L * N;
-    B.tiles_r = (D.rows + 127) / 128;
-    B.tiles = B.tiles_r * ((T + 15) / 16);
-    bt.prefix[0] = 0;
-    bt.prefix[1] = B.tiles;
-    e = phe::launch_body(c, bt, mode, s);
+  for (u32 n = 0; n < nchunks && e == cudaSuccess; ++n) {
+    const u32 t0 = n * tc, tn = (T - t0 < tc) ? T - t0 : tc;
+    cudaStream_t s = c->side[n % 2];
+    Buf& B = buf[n % 2];
+    const char* hm = reinterpret_cast<const char*>(h_in_mask) + t0 * in_tok;
+    const char* hb = reinterpret_cast<const char*>(h_in_body) + t0 * in_tok;
+    if ((e = cudaMemcpyAsync(B.a, hm, tn * in_tok, cudaMemcpyHostToDevice, s)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(B.b, hb, tn * in_tok, cudaMemcpyHostToDevice, s)) != cudaSuccess) break;
+    if ((e = matmul_device(c, D, tn, B.a, B.b, B.om, B.ob, mode, s)) != cudaSuccess) break;
+    char* om = reinterpret_cast<char*>(h_out_mask) + t0 * om_tok;
+    char* ob = reinterpret_cast<char*>(h_out_body) + t0 * ob_tok;
+    if ((e = cudaMemcpyAsync(om, B.om, tn * om_tok, cudaMemcpyDeviceToHost, s)) != cudaSuccess) break;
+    e = cudaMemcpyAsync(ob, B.ob, tn * ob_tok, cudaMemcpyDeviceToHost, s);
   }
-  cudaError_t ef = cudaFreeAsync(ahat, s);
-  if (e != cudaSuccess) return cuda_fail(e, "phe_matmul launch");
-  if (ef != cudaSuccess) return cuda_fail(ef, "cudaFreeAsync(A_hat)");
+  for (int i = 0; i < 2; ++i) {
+    cudaStream_t s = c->side[i];
+    cudaFreeAsync(buf[i].a, s);
+    cudaFreeAsync(buf[i].b, s);
+    cudaFreeAsync(buf[i].om, s);
+    cudaFreeAsync(buf[i].ob, s);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = e2;
+  }
+  cudaEventDestroy(ev);
+  if (e != cudaSuccess) return cuda_fail(e, "phe_matmul_host");
+  return PHE_OK;
+}
+
+phe_status phe_trace_enable(phe_ctx* c, int on) {
+  if (!c) return fail(PHE_EINVAL, "phe_trace_enable: null context");
+  c->tracer.on = on != 0;
+  return PHE_OK;
+}
+
+phe_status phe_trace_read(phe_ctx* c, phe_trace_entry* out, uint32_t cap, uint32_t* n_out) {
+  if (!c || !n_out || (cap && !out)) return fail(PHE_EINVAL, "phe_trace_read: null argument");
+  DeviceGuard g(c->device);
+  std::vector<std::vector<double>> ms(phe::kKCount);
+  cudaError_t err = cudaSuccess;
+  for (const auto& r : c->tracer.recs) {
+    float t = 0.f;
+    cudaError_t e = cudaEventSynchronize(r.b);
+    if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
+    if (e != cudaSuccess && err == cudaSuccess) err = e;
+    ms[r.kid].push_back(t);
+    c->tracer.pool.push_back(r.a);
+    c->tracer.pool.push_back(r.b);
+  }
+  c->tracer.recs.clear();
+  if (err != cudaSuccess) return cuda_fail(err, "phe_trace_read");
+  uint32_t n = 0;
+  for (int k = 0; k < phe::kKCount; ++k) {
+    if (ms[k].empty()) continue;
+    if (n < cap) {
+      auto& v = ms[k];
+      std::sort(v.begin(), v.end());
+      phe_trace_entry& E = out[n];
+      std::memset(&E, 0, sizeof(E));
+      std::snprintf(E.name, sizeof(E.name), "%s", phe::kernel_name(k));
+      E.launches = v.size();
+      for (double x : v) E.total_ms += x;
+      auto rank = [&](double pct) { size_t i = (size_t)std::ceil(pct * v.size()); return v[i ? i - 1 : 0]; };
+      E.p50_ms = rank(0.50);
+      E.p99_ms = rank(0.99);
+      E.max_ms = v.back();
+    }
+    ++n;
+  }
+  *n_out = n < cap ? n : cap;
   return PHE_OK;
 }
 
@@ -365,6 +521,7 @@ phe_status phe_modswitch(phe_ctx* c, const uint64_t* d_in, uint32_t* d_out, size
   if (!d_in || !d_out) return fail(PHE_EINVAL, "phe_modswitch: null buffer");
   DeviceGuard g(c->device);
   if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  Span sp(c, phe::kKModswitch, (cudaStream_t)stream);
   cudaError_t e = phe::launch_modswitch(c, reinterpret_cast<const u64*>(d_in), d_out, n, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "phe_modswitch launch");
   return PHE_OK;

@@ -28,6 +28,7 @@ using u32 = unsigned int;
 struct RingConst {
   u64 q;          // ciphertext modulus, prime, 2^53 < q < 2^61, q = 1 mod 2N
   u64 q2;         // 2q
+  u64 q4;         // 4q
   u64 half_q;     // floor(q/2)
   u64 ms_mu;      // floor(2^(64+s) / q), s = floor(log2 q): Barrett constant of the switch
   u64 red_mu;     // floor(2^64 / q): Barrett constant for reducing a 64-bit word
@@ -43,13 +44,27 @@ __device__ __forceinline__ u64 mul_shoup(u64 x, u64 w, u64 wp, u64 q) {
   return x * w - quo * q;
 }
 
-// Gentleman-Sande butterfly, Harvey's lazy form.  In: X, Y in [0, 2q).
-// Out: X <- X + Y, Y <- (X - Y) w, both in [0, 2q).
-__device__ __forceinline__ void gs_bfly(u64& X, u64& Y, u64 w, u64 wp, u64 q, u64 q2) {
+// Shoup product with a cheaper quotient estimate.  With x = x1 2^32 + x0 and
+// wp = w1 2^32 + w0, the estimate w1 x1 + hi32(w1 x0) + hi32(w0 x1) drops
+// the low x low partial product and the carries of the two cross terms, so
+// it is at most 2 below floor(wp x / 2^64) and never above it: the result
+// x w - quo q lies in [0, 4q).  One wide and two high-half 32-bit multiplies
+// replace the four wide multiplies of a full 64x64 high product.
+__device__ __forceinline__ u64 mul_shoup_lazy(u64 x, u64 w, u64 wp, u64 q) {
+  const u32 x0 = (u32)x, x1 = (u32)(x >> 32);
+  const u32 w0 = (u32)wp, w1 = (u32)(wp >> 32);
+  const u64 quo = (u64)w1 * x1 + __umulhi(w1, x0) + __umulhi(w0, x1);
+  return x * w - quo * q;
+}
+
+// Gentleman-Sande butterfly kept in [0, 4q) (Harvey's lazy butterfly with
+// one more factor of two of headroom, valid for 8q < 2^64).
+// In: X, Y in [0, 4q).  Out: X <- X + Y, Y <- (X - Y) w, both in [0, 4q).
+__device__ __forceinline__ void gs_bfly(u64& X, u64& Y, u64 w, u64 wp, u64 q, u64 q4) {
   u64 s = X + Y;
-  s = (s >= q2) ? s - q2 : s;
-  const u64 d = X - Y + q2;
-  Y = mul_shoup(d, w, wp, q);
+  s = (s >= q4) ? s - q4 : s;
+  const u64 d = X - Y + q4;
+  Y = mul_shoup_lazy(d, w, wp, q);
   X = s;
 }
 
@@ -150,9 +165,10 @@ __device__ __forceinline__ void static_for(F&& f) {
 
 // One stage of a pass: stage ST of pass PASS (ST counted inside the pass).
 // Every twiddle is loaded once and applied to the 2^ST butterflies sharing it.
+// qb is the butterfly's bound: 2q for the forward, 4q for the inverse form.
 template <int LOGN, int PASS, int ST, bool INVERSE>
 __device__ __forceinline__ void pass_stage(u64 (&x)[16], int p, const ulonglong2* __restrict__ tw0,
-                                           const ulonglong2* __restrict__ twc, u64 q, u64 q2) {
+                                           const ulonglong2* __restrict__ twc, u64 q, u64 qb) {
   using PS = PassShape<LOGN, PASS>;
   constexpr int N = Shape<LOGN>::N;
   constexpr int P = Shape<LOGN>::P;
@@ -173,20 +189,20 @@ __device__ __forceinline__ void pass_stage(u64 (&x)[16], int p, const ulonglong2
 #pragma unroll
       for (int c = 0; c < h; ++c) {
         const int e0 = u * PS::G + b * 2 * h + c;
-        if constexpr (INVERSE) gs_bfly(x[e0], x[e0 + h], w.x, w.y, q, q2);
-        else ct_bfly(x[e0], x[e0 + h], w.x, w.y, q, q2);
+        if constexpr (INVERSE) gs_bfly(x[e0], x[e0 + h], w.x, w.y, q, qb);
+        else ct_bfly(x[e0], x[e0 + h], w.x, w.y, q, qb);
       }
     }
   }
 }
 
-// Inverse (Gentleman-Sande) pass: stages S0 .. S0+K-1 ascending.
+// Inverse (Gentleman-Sande) pass: stages S0 .. S0+K-1 ascending; q4 = 4q.
 // tw0: pass-0 table, thread-major [15][P]; twc: compact table [N].
 template <int LOGN, int PASS>
 __device__ __forceinline__ void gs_pass(u64 (&x)[16], int p, const ulonglong2* __restrict__ tw0,
-                                        const ulonglong2* __restrict__ twc, u64 q, u64 q2) {
+                                        const ulonglong2* __restrict__ twc, u64 q, u64 q4) {
   static_for<0, PassShape<LOGN, PASS>::K>([&](auto st) {
-    pass_stage<LOGN, PASS, decltype(st)::value, true>(x, p, tw0, twc, q, q2);
+    pass_stage<LOGN, PASS, decltype(st)::value, true>(x, p, tw0, twc, q, q4);
   });
 }
 
@@ -213,22 +229,22 @@ __device__ __forceinline__ void exchange(u64 (&x)[16], int p, u64* __restrict__ 
 }
 
 // Full inverse transform (no N^-1 scaling): bit-reversed in (pass-0 layout),
-// natural order out (last-pass layout).  Values in [0, 2q) in and out.
+// natural order out (last-pass layout).  Values in [0, 4q) in and out.
 template <int LOGN>
 __device__ __forceinline__ void intt_regs(u64 (&x)[16], int p, u64* buf, const ulonglong2* tw0,
-                                          const ulonglong2* twc, u64 q, u64 q2) {
-  gs_pass<LOGN, 0>(x, p, tw0, twc, q, q2);
+                                          const ulonglong2* twc, u64 q, u64 q4) {
+  gs_pass<LOGN, 0>(x, p, tw0, twc, q, q4);
   if constexpr (Shape<LOGN>::NPASS > 1) {
     exchange<LOGN, 0, 1>(x, p, buf);
-    gs_pass<LOGN, 1>(x, p, tw0, twc, q, q2);
+    gs_pass<LOGN, 1>(x, p, tw0, twc, q, q4);
   }
   if constexpr (Shape<LOGN>::NPASS > 2) {
     exchange<LOGN, 1, 2>(x, p, buf);
-    gs_pass<LOGN, 2>(x, p, tw0, twc, q, q2);
+    gs_pass<LOGN, 2>(x, p, tw0, twc, q, q4);
   }
   if constexpr (Shape<LOGN>::NPASS > 3) {
     exchange<LOGN, 2, 3>(x, p, buf);
-    gs_pass<LOGN, 3>(x, p, tw0, twc, q, q2);
+    gs_pass<LOGN, 3>(x, p, tw0, twc, q, q4);
   }
 }
 

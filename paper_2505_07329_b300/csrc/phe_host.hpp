@@ -5,6 +5,7 @@
 #include <cstddef>
 #include <cstdint>
 #include <string>
+#include <vector>
 
 #include <cuda_runtime.h>
 
@@ -22,27 +23,18 @@ struct LweJob {
   const ulonglong2* what;   // W_hat pairs [rows][L][N] (what_idx layout)
   const u64* ahat;          // A_hat [T][L][N] (ahat_idx layout)
   void* out;                // mask out: [T][rows][N] u32 (switched) or u64 (raw / ring product)
+  const int8_t* wrow;       // clear weights of this direction, [rows][cols] int8 (body product)
+  const u64* bin;           // input bodies, token t at bin + t*L*N
+  void* out_body;           // [T][rows] u32 (switched) or u64 (raw)
   const int32_t* err;       // client encryption only: E [T*L][N]
   const int8_t* msg;        // client encryption only: x [T][msg_d]
   u64 delta, delta_p;       // client encryption only: delta and its Shoup quotient
-  u32 rows, T, L, tok_chunk, tiles, msg_d;
+  u32 rows, cols, T, L, tok_chunk, tiles, msg_d;
 };
 struct LweJobTable {
   u32 n;
   u32 prefix[kMaxJobs + 1];  // tile prefix sums
   LweJob j[kMaxJobs];
-};
-
-struct BodyJob {
-  const uint32_t* wb;       // packed weights [ceil(K/4)][R], 4 int8 per word
-  const u64* B;             // body words, token t at B + t*ldB, k < K used
-  void* out;                // [T][R] u32 (switched) or u64 (raw)
-  u32 R, K, T, ldB, tiles_r, tiles;
-};
-struct BodyJobTable {
-  u32 n;
-  u32 prefix[kMaxJobs + 1];
-  BodyJob j[kMaxJobs];
 };
 
 struct NttJob {             // forward transform of T*L input blocks
@@ -52,6 +44,23 @@ struct NttJob {             // forward transform of T*L input blocks
 };
 
 enum OutMode : int { kOutSwitched = 0, kOutRaw = 1, kOutRing = 2 };
+
+// Kernel names for tracing; kKCall brackets a whole phe_matmul call.
+enum KernelId : int { kKInputNtt = 0, kKLwedot, kKModswitch, kKWeightNtt, kKCall, kKCount };
+inline const char* kernel_name(int k) {
+  static const char* names[kKCount] = {"input_ntt_kernel", "lwedot_kernel", "modswitch_kernel",
+                                       "weight_ntt_kernel", "phe_matmul"};
+  return (k >= 0 && k < kKCount) ? names[k] : "?";
+}
+struct TraceRec {
+  int kid;
+  cudaEvent_t a, b;
+};
+struct Tracer {
+  bool on = false;
+  std::vector<TraceRec> recs;
+  std::vector<cudaEvent_t> pool;
+};
 
 struct Tables {
   ulonglong2* fwd_c = nullptr;  // psi^brv(k) and Shoup quotient, [N]
@@ -70,6 +79,8 @@ struct phe_ctx {
   phe::u64 n_inv = 0, n_inv_p = 0;  // N^-1 mod q and its Shoup quotient
   phe::Tables tab;
   int num_sms = 0;
+  cudaStream_t side[2] = {nullptr, nullptr};  // streams for overlapped host-buffer chunks
+  phe::Tracer tracer;
 };
 
 struct phe_weights {
@@ -77,7 +88,7 @@ struct phe_weights {
   uint32_t d_out = 0, d_in = 0, dirs = 0;
   struct Dir {
     ulonglong2* what = nullptr;  // [rows][L][N] pairs
-    uint32_t* wb = nullptr;      // [ceil(cols/4)][rows]
+    int8_t* wrow = nullptr;      // [rows][cols] clear weights of the direction
     uint32_t rows = 0, cols = 0, L = 0;
   } dir[2];
   uint64_t bytes = 0;
@@ -90,10 +101,7 @@ cudaError_t launch_input_ntt(const phe_ctx* c, const NttJob* jobs, int n, cudaSt
 cudaError_t launch_weight_ntt(const phe_ctx* c, const int8_t* W, u32 rows, u32 cols, u32 row_stride,
                               u32 col_stride, u32 L, int rev, ulonglong2* what, cudaStream_t s);
 cudaError_t launch_lwedot(const phe_ctx* c, const LweJobTable& jt, int mode, int grid_limit, cudaStream_t s);
-cudaError_t launch_body(const phe_ctx* c, const BodyJobTable& jt, int mode, cudaStream_t s);
 cudaError_t launch_modswitch(const phe_ctx* c, const u64* in, u32* out, size_t n, cudaStream_t s);
-cudaError_t launch_pack_body_weights(const int8_t* W, u32 rows, u32 cols, u32 row_stride, u32 col_stride,
-                                     uint32_t* wb, cudaStream_t s);
 int lwedot_threads(int logn);
 size_t lwedot_smem(int logn);
 

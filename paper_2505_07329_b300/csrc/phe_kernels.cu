@@ -1,10 +1,10 @@
 // CUDA kernels of the hot path (sm_103a):
 //   input_ntt_kernel   forward negacyclic NTT of the input masks A_ti
 //   weight_ntt_kernel  w_hat_ij (reversed weight blocks, Sec. 4.3.1) -> NTT domain, x N^-1
-//   lwedot_kernel      Eq. (LWEdot) for the masks: pointwise sum over blocks,
-//                      inverse NTT, SampleExtract at N-1 (index reversal),
-//                      ModulusSwitch -- one fused pass per (token, row)
-//   body_kernel        the bodies b'_tj = sum_k W[j,k] B_t[k] (mod q) + switch
+//   lwedot_kernel      Eq. (LWEdot): pointwise sum over blocks, inverse NTT,
+//                      SampleExtract at N-1 (index reversal), ModulusSwitch --
+//                      one fused pass per (token, row) for the masks
+//                      and the bodies b'_tj = sum_k W[j,k] B_t[k] (mod q)
 //   modswitch_kernel   unfused ModulusSwitch
 //
 // Why the inverse NTT yields SampleExtract at N-1: with P = A_i * w_hat_ij
@@ -101,22 +101,36 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB)
 }
 
 // --------------------------------------------------------------------------
-// Eq. (LWEdot), masks.  A tile is (job, output row, chunk of tokens); the
-// block walks the chunk SLOTS tokens at a time.
+// Eq. (LWEdot).  A tile is (job, output row, chunk of tokens); the block walks
+// the chunk SLOTS tokens at a time.  Per (token, row):
+//   mask  sum_i A_hat_ti . W_hat_ij in the NTT domain, inverse transform,
+//         coefficient N-1-m to slot m (SampleExtract at N-1), switch;
+//   body  coefficient N-1 of sum_i B_ti * w_hat_ij, i.e. the plain dot
+//         product sum_k W(j,k) B_t[k], exact in two int64 partial sums
+//         (B = Bh 2^30 + Bl; |sum| < 2^14 2^7 2^31 = 2^52 < q), reduced
+//         across the block and switched.
 // --------------------------------------------------------------------------
+#ifndef PHE_LWEDOT_MIN_BLOCKS
+#define PHE_LWEDOT_MIN_BLOCKS 3
+#endif
 template <int LOGN, int MODE>
-__global__ void __launch_bounds__(Shape<LOGN>::TPB)
+__global__ void __launch_bounds__(Shape<LOGN>::TPB, PHE_LWEDOT_MIN_BLOCKS)
     lwedot_kernel(const LweJobTable jt, RingConst rc, const ulonglong2* __restrict__ tw0,
                   const ulonglong2* __restrict__ twc) {
   using S = Shape<LOGN>;
   constexpr int N = S::N;
   constexpr int P = S::P;
   constexpr int NP = S::NPASS;
+  constexpr bool BODY = MODE != kOutRing;
+  constexpr int GW = (P < 32) ? P : 32;   // lanes of one body-reduction group
+  constexpr int NGRP = P / GW;            // groups per transform
   extern __shared__ u64 smem[];
+  __shared__ long long red[2][S::SLOTS][NGRP][2];
   const int slot = threadIdx.x / P, p = threadIdx.x % P;
   u64* buf = smem + slot * S::PADN;
-  const u64 q = rc.q, q2 = rc.q2;
+  const u64 q = rc.q, q4 = rc.q4;
   const u32 total = jt.prefix[jt.n];
+  u32 seq = 0;
 
   for (u32 tile = blockIdx.x; tile < total; tile += gridDim.x) {
     u32 k = 0;
@@ -129,9 +143,10 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB)
     const ulonglong2* wrow = J.what + (size_t)row * J.L * N;
     const u32 iters = (t1 - t0 + S::SLOTS - 1) / S::SLOTS;
 
-    for (u32 it = 0; it < iters; ++it) {
+    for (u32 it = 0; it < iters; ++it, ++seq) {
       const u32 t = t0 + it * S::SLOTS + slot;
       const bool active = t < t1;
+      const int par = seq & 1;
       u64 x[16];
 #pragma unroll
       for (int r = 0; r < 16; ++r) x[r] = 0;
@@ -145,28 +160,50 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB)
             const ulonglong2 av = __ldg(&ap[(r >> 1) * P + p]);
             const ulonglong2 w0 = __ldg(&wp[what_idx<LOGN>(p, r)]);
             const ulonglong2 w1 = __ldg(&wp[what_idx<LOGN>(p, r + 1)]);
-            u64 s0 = x[r] + mul_shoup(av.x, w0.x, w0.y, q);
-            u64 s1 = x[r + 1] + mul_shoup(av.y, w1.x, w1.y, q);
-            x[r] = (s0 >= q2) ? s0 - q2 : s0;
-            x[r + 1] = (s1 >= q2) ? s1 - q2 : s1;
+            const u64 s0 = x[r] + mul_shoup_lazy(av.x, w0.x, w0.y, q);
+            const u64 s1 = x[r + 1] + mul_shoup_lazy(av.y, w1.x, w1.y, q);
+            x[r] = (s0 >= q4) ? s0 - q4 : s0;
+            x[r + 1] = (s1 >= q4) ? s1 - q4 : s1;
           }
         }
       }
-      intt_regs<LOGN>(x, p, buf, tw0, twc, q, q2);
+      if constexpr (BODY) {
+        long long al = 0, ah = 0;
+        if (active) {
+          const int8_t* wr = J.wrow + (size_t)row * J.cols;
+          const u64* bt = J.bin + (size_t)t * J.L * N;
+          for (u32 kk = p; kk < J.cols; kk += P) {
+            const u64 b = reduce_word(__ldg(&bt[kk]), rc);
+            const int w = __ldg(&wr[kk]);
+            al += (long long)w * (int)(b & 0x3fffffffull);
+            ah += (long long)w * (int)(b >> 30);
+          }
+        }
+#pragma unroll
+        for (int off = GW / 2; off > 0; off >>= 1) {
+          al += __shfl_xor_sync(0xffffffffu, al, off, GW);
+          ah += __shfl_xor_sync(0xffffffffu, ah, off, GW);
+        }
+        if (p % GW == 0) {
+          red[par][slot][p / GW][0] = al;
+          red[par][slot][p / GW][1] = ah;
+        }
+      }
+      intt_regs<LOGN>(x, p, buf, tw0, twc, q, q4);  // barriers inside also order red[]
       if (active) {
         if constexpr (MODE == kOutSwitched) {
           uint32_t* out = reinterpret_cast<uint32_t*>(J.out) + ((size_t)t * J.rows + row) * N;
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
             const int pos = pass_pos<LOGN, NP - 1>(p, e);
-            out[N - 1 - pos] = modswitch_word(reduce_2q(x[e], q), rc);
+            out[N - 1 - pos] = modswitch_word(reduce_4q(x[e], q, rc.q2), rc);
           }
         } else if constexpr (MODE == kOutRaw) {
           u64* out = reinterpret_cast<u64*>(J.out) + ((size_t)t * J.rows + row) * N;
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
             const int pos = pass_pos<LOGN, NP - 1>(p, e);
-            out[N - 1 - pos] = reduce_2q(x[e], q);
+            out[N - 1 - pos] = reduce_4q(x[e], q, rc.q2);
           }
         } else {
           // Ring product in natural order plus E + delta * x_hat: client-side
@@ -177,7 +214,7 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB)
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
             const int pos = pass_pos<LOGN, NP - 1>(p, e);
-            u64 v = reduce_2q(x[e], q);
+            u64 v = reduce_4q(x[e], q, rc.q2);
             const int32_t ev = J.err[(size_t)t * N + pos];
             v += (ev < 0) ? q - (u64)(-(int64_t)ev) : (u64)ev;
             v = reduce_2q(v, q);
@@ -188,90 +225,22 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB)
             out[pos] = reduce_2q(v, q);
           }
         }
-      }
-    }
-  }
-}
-
-// --------------------------------------------------------------------------
-// Bodies: b'_tj = sum_k W(j, k) B_t[k] (mod q), k < K (coefficient N-1 of the
-// block products of Eq. (LWEdot) is the plain dot product over the blocks).
-// Exact: B = Bh 2^30 + Bl with Bl < 2^30, Bh < 2^31; both partial sums are
-// accumulated in int64 (|sum| < 2^14 * 2^7 * 2^31 = 2^52 < q) and recombined
-// mod q.  Tile: 128 rows x 16 tokens per block of 256 threads; thread
-// (tx, ty) owns rows j0+tx, j0+tx+64 and tokens t0+ty+4b (b < 4).
-// --------------------------------------------------------------------------
-constexpr int kBodyRows = 128, kBodyToks = 16, kBodyKC = 128;
-
-template <int MODE>
-__global__ void __launch_bounds__(256) body_kernel(const BodyJobTable jt, RingConst rc) {
-  __shared__ int2 bs[kBodyToks][kBodyKC];
-  const int tx = threadIdx.x & 63, ty = threadIdx.x >> 6;
-  const u64 q = rc.q;
-  const u32 total = jt.prefix[jt.n];
-  for (u32 tile = blockIdx.x; tile < total; tile += gridDim.x) {
-    u32 k = 0;
-    while (tile >= jt.prefix[k + 1]) ++k;
-    const BodyJob& J = jt.j[k];
-    const u32 local = tile - jt.prefix[k];
-    const u32 j0 = (local % J.tiles_r) * kBodyRows;
-    const u32 t0 = (local / J.tiles_r) * kBodyToks;
-    const u32 K4 = (J.K + 3) & ~3u;
-    long long accl[2][4], acch[2][4];
+        if constexpr (BODY) {
+          if (p == 0) {
+            long long hl = 0, ll = 0;
 #pragma unroll
-    for (int a = 0; a < 2; ++a)
-#pragma unroll
-      for (int b = 0; b < 4; ++b) accl[a][b] = acch[a][b] = 0;
-
-    for (u32 k0 = 0; k0 < K4; k0 += kBodyKC) {
-      for (int idx = threadIdx.x; idx < kBodyToks * kBodyKC; idx += 256) {
-        const int tt = idx / kBodyKC, kk = idx % kBodyKC;
-        const u32 t = t0 + tt, kg = k0 + kk;
-        const u64 v = (t < J.T && kg < J.K) ? reduce_word(J.B[(size_t)t * J.ldB + kg], rc) : 0ull;
-        bs[tt][kk] = make_int2((int)(v & 0x3fffffffull), (int)(v >> 30));
-      }
-      __syncthreads();
-      const u32 kmax = min((u32)kBodyKC, K4 - k0);
-      for (u32 k4 = 0; k4 < kmax / 4; ++k4) {
-        u32 wv[2];
-#pragma unroll
-        for (int a = 0; a < 2; ++a) {
-          const u32 j = j0 + tx + 64 * a;
-          wv[a] = (j < J.R) ? __ldg(&J.wb[(size_t)(k0 / 4 + k4) * J.R + j]) : 0u;
-        }
-#pragma unroll
-        for (int by = 0; by < 4; ++by) {
-          int2 bv[4];
-#pragma unroll
-          for (int b = 0; b < 4; ++b) bv[b] = bs[ty + 4 * b][4 * k4 + by];
-#pragma unroll
-          for (int a = 0; a < 2; ++a) {
-            const int w = (int)(signed char)(wv[a] >> (8 * by));
-#pragma unroll
-            for (int b = 0; b < 4; ++b) {
-              accl[a][b] += (long long)w * bv[b].x;
-              acch[a][b] += (long long)w * bv[b].y;
+            for (int g = 0; g < NGRP; ++g) {
+              ll += red[par][slot][g][0];
+              hl += red[par][slot][g][1];
             }
-          }
-        }
-      }
-      __syncthreads();
-    }
-#pragma unroll
-    for (int a = 0; a < 2; ++a) {
-#pragma unroll
-      for (int b = 0; b < 4; ++b) {
-        const u32 j = j0 + tx + 64 * a, t = t0 + ty + 4 * b;
-        if (j < J.R && t < J.T) {
-          const long long hl = acch[a][b], ll = accl[a][b];
-          const u64 vh = (hl < 0) ? q - (u64)(-hl) : (u64)hl;
-          const u64 vl = (ll < 0) ? q - (u64)(-ll) : (u64)ll;
-          u64 v = reduce_2q(mul_shoup(vh, rc.c30, rc.c30p, q), q) + vl;
-          v = reduce_2q(v, q);
-          if constexpr (MODE == kOutSwitched) {
-            reinterpret_cast<uint32_t*>(J.out)[(size_t)t * J.R + j] = modswitch_word(v, rc);
-          } else {
-            reinterpret_cast<u64*>(J.out)[(size_t)t * J.R + j] = v;
+            const u64 vh = (hl < 0) ? q - (u64)(-hl) : (u64)hl;
+            const u64 vl = (ll < 0) ? q - (u64)(-ll) : (u64)ll;
+            u64 v = reduce_2q(mul_shoup(vh, rc.c30, rc.c30p, q), q) + vl;
+            v = reduce_2q(v, q);
+            if constexpr (MODE == kOutSwitched)
+              reinterpret_cast<uint32_t*>(J.out_body)[(size_t)t * J.rows + row] = modswitch_word(v, rc);
+            else
+              reinterpret_cast<u64*>(J.out_body)[(size_t)t * J.rows + row] = v;
           }
         }
       }
@@ -282,23 +251,6 @@ __global__ void __launch_bounds__(256) body_kernel(const BodyJobTable jt, RingCo
 __global__ void modswitch_kernel(const u64* __restrict__ in, uint32_t* __restrict__ out, size_t n, RingConst rc) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     out[i] = modswitch_word(reduce_word(in[i], rc), rc);
-}
-
-// Packed weights for the body product: wb[(k/4) R + j] holds W(j, k..k+3).
-__global__ void pack_body_weights_kernel(const int8_t* __restrict__ W, u32 R, u32 K, u32 rs, u32 cs,
-                                         uint32_t* __restrict__ wb) {
-  const u32 K4 = (K + 3) / 4;
-  const size_t n = (size_t)K4 * R;
-  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
-    const u32 j = (u32)(idx % R), k4 = (u32)(idx / R);
-    u32 word = 0;
-    for (int by = 0; by < 4; ++by) {
-      const u32 k = 4 * k4 + by;
-      const u32 v = (k < K) ? (u32)(uint8_t)W[(size_t)j * rs + (size_t)k * cs] : 0u;
-      word |= v << (8 * by);
-    }
-    wb[idx] = word;
-  }
 }
 
 // --------------------------------------------------------------------------
@@ -409,28 +361,12 @@ cudaError_t launch_lwedot(const phe_ctx* c, const LweJobTable& jt, int mode, int
   }
 }
 
-cudaError_t launch_body(const phe_ctx* c, const BodyJobTable& jt, int mode, cudaStream_t s) {
-  const u32 total = jt.prefix[jt.n];
-  if (total == 0) return cudaSuccess;
-  if (mode == kOutSwitched) body_kernel<kOutSwitched><<<total, 256, 0, s>>>(jt, c->rc);
-  else body_kernel<kOutRaw><<<total, 256, 0, s>>>(jt, c->rc);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_modswitch(const phe_ctx* c, const u64* in, uint32_t* out, size_t n, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   size_t blocks = (n + 255) / 256;
   const size_t cap = (size_t)c->num_sms * 16;
   if (blocks > cap) blocks = cap;
   modswitch_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, out, n, c->rc);
-  return cudaGetLastError();
-}
-
-cudaError_t launch_pack_body_weights(const int8_t* W, u32 R, u32 K, u32 rs, u32 cs, uint32_t* wb, cudaStream_t s) {
-  const size_t n = (size_t)((K + 3) / 4) * R;
-  size_t blocks = (n + 255) / 256;
-  if (blocks > 4096) blocks = 4096;
-  pack_body_weights_kernel<<<(unsigned)blocks, 256, 0, s>>>(W, R, K, rs, cs, wb);
   return cudaGetLastError();
 }
 

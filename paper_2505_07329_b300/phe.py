@@ -31,6 +31,11 @@ class phe_params(ctypes.Structure):
     _fields_ = [("N", ctypes.c_uint32), ("log2_qout", ctypes.c_uint32), ("q", ctypes.c_uint64)]
 
 
+class phe_trace_entry(ctypes.Structure):
+    _fields_ = [("name", ctypes.c_char * 32), ("launches", ctypes.c_uint64), ("total_ms", ctypes.c_double),
+                ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double)]
+
+
 _vp = ctypes.c_void_p
 _u32 = ctypes.c_uint32
 _u64 = ctypes.c_uint64
@@ -50,6 +55,9 @@ SIGNATURES = {
     "phe_matmul": (_i32, [_vp, _vp, _i32, _u32, _vp, _vp, _vp, _vp, _u32, _vp]),
     "phe_modswitch": (_i32, [_vp, _vp, _vp, _sz, _vp]),
     "phe_client_encrypt": (_i32, [_vp, _u32, _u32, _vp, _vp, _vp, _vp, _u64, _vp, _vp]),
+    "phe_matmul_host": (_i32, [_vp, _vp, _i32, _u32, _vp, _vp, _vp, _vp, _u32, _u64, _vp]),
+    "phe_trace_enable": (_i32, [_vp, _i32]),
+    "phe_trace_read": (_i32, [_vp, ctypes.POINTER(phe_trace_entry), _u32, ctypes.POINTER(_u32)]),
 }
 
 _lib = None
@@ -159,3 +167,35 @@ def phe_modswitch(ctx, d_in, d_out, n: int, stream=None) -> None:
 def phe_client_encrypt(ctx, T: int, d: int, A, S, E, x, delta: int, B, stream=None) -> None:
     _check(lib().phe_client_encrypt(ctx, T, d, _dptr(A), _dptr(S), _dptr(E), _dptr(x), delta, _dptr(B),
                                     _stream(stream)))
+
+
+def _hptr(a):
+    """Host pointer of a numpy array or a CPU torch tensor (contiguous)."""
+    if hasattr(a, "data_ptr"):
+        if a.is_cuda or not a.is_contiguous():
+            raise ValueError("expected a contiguous host tensor")
+        return a.data_ptr()
+    if not a.flags["C_CONTIGUOUS"]:
+        raise ValueError("expected a contiguous host array")
+    return a.ctypes.data
+
+
+def phe_matmul_host(ctx, w, direction: int, T: int, h_in_mask, h_in_body, h_out_mask, h_out_body,
+                    flags: int = PHE_OUT_SWITCHED, max_chunk_bytes: int = 0, stream=None) -> None:
+    _check(lib().phe_matmul_host(ctx, w, direction, T, _hptr(h_in_mask), _hptr(h_in_body), _hptr(h_out_mask),
+                                 _hptr(h_out_body), flags, max_chunk_bytes, _stream(stream)))
+
+
+def phe_trace_enable(ctx, on: bool = True) -> None:
+    _check(lib().phe_trace_enable(ctx, 1 if on else 0))
+
+
+def phe_trace_read(ctx) -> dict:
+    """{kernel name: {launches, total_ms, p50_ms, p99_ms, max_ms}}; clears the record."""
+    cap = 16
+    arr = (phe_trace_entry * cap)()
+    n = _u32()
+    _check(lib().phe_trace_read(ctx, arr, cap, ctypes.byref(n)))
+    return {arr[i].name.decode(): {"launches": int(arr[i].launches), "total_ms": arr[i].total_ms,
+                                   "p50_ms": arr[i].p50_ms, "p99_ms": arr[i].p99_ms, "max_ms": arr[i].max_ms}
+            for i in range(n.value)}
