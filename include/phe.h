@@ -163,6 +163,36 @@ phe_status phe_trace_read(phe_ctx* ctx, phe_trace_entry* out, uint32_t cap, uint
 phe_status phe_client_encrypt(phe_ctx* ctx, uint32_t T, uint32_t d, const uint64_t* d_A, const int8_t* d_S,
                               const int32_t* d_E, const int8_t* d_x, uint64_t delta, uint64_t* d_B, void* stream);
 
+/* Size of the fixed device scratch array used by phe_matmul_noalloc. */
+#define PHE_NOALLOC_MAX_SCRATCH_BYTES (16u << 20)
+
+/* phe_matmul without any allocation.  The paper has no counterpart: this is
+ * an engineering variant for callers that cannot allocate device memory
+ * while serving -- e.g. a process whose HBM is already owned by another
+ * allocator (a PyTorch caching allocator, an inference server with a fixed
+ * budget), where an allocation by this library could fail or fragment that
+ * budget, or a latency-critical loop that must not touch the CUDA allocator
+ * after start-up.
+ *
+ * Same arguments, layouts and results as phe_matmul.  The scratch it needs
+ * (the transformed input masks, T*L*N*8 bytes) lives in one fixed device
+ * array of PHE_NOALLOC_MAX_SCRATCH_BYTES (16 MiB) that every GPU loading the
+ * library holds until the process exits; larger requests return PHE_EINVAL
+ * (at N = 4096, L = 1: up to 512 tokens per call).  It calls no cudaMalloc,
+ * cudaFree or other allocating routine and records no trace events.
+ *
+ * The first call on a device looks up the array's device address
+ * (cudaGetSymbolAddress, once per device, with that device current); make
+ * that first call before any stream capture.  All calls share the one array
+ * and it keeps the last call's contents (each call overwrites every word it
+ * reads, so nothing needs clearing): calls whose work overlaps on the GPU --
+ * concurrent streams, or several host threads -- race on it and must be
+ * serialised by the caller.  Errors: as phe_matmul, plus PHE_EINVAL when the
+ * scratch does not fit. */
+phe_status phe_matmul_noalloc(phe_ctx* ctx, const phe_weights* w, int dir, uint32_t T, const uint64_t* d_in_mask,
+                              const uint64_t* d_in_body, void* d_out_mask, void* d_out_body, uint32_t flags,
+                              void* stream);
+
 #ifdef __cplusplus
 }
 #endif

@@ -204,6 +204,10 @@ phe_status check_matmul_args(phe_ctx* c, const phe_weights* w, int dir, uint32_t
 
 }  // namespace
 
+namespace phe {
+void set_last_error(const char* msg) { g_err = msg; }
+}  // namespace phe
+
 extern "C" {
 
 const char* phe_status_string(phe_status s) {

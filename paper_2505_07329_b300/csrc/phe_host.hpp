@@ -103,6 +103,8 @@ cudaError_t launch_weight_ntt(const phe_ctx* c, const int8_t* W, u32 rows, u32 c
 cudaError_t launch_lwedot(const phe_ctx* c, const LweJobTable& jt, int mode, int grid_limit, cudaStream_t s);
 cudaError_t launch_modswitch(const phe_ctx* c, const u64* in, u32* out, size_t n, cudaStream_t s);
 int lwedot_threads(int logn);
+// Sets the calling thread's phe_last_error() message (phe_capi.cu).
+void set_last_error(const char* msg);
 size_t lwedot_smem(int logn);
 
 }  // namespace phe

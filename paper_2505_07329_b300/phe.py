@@ -58,6 +58,7 @@ SIGNATURES = {
     "phe_matmul_host": (_i32, [_vp, _vp, _i32, _u32, _vp, _vp, _vp, _vp, _u32, _u64, _vp]),
     "phe_trace_enable": (_i32, [_vp, _i32]),
     "phe_trace_read": (_i32, [_vp, ctypes.POINTER(phe_trace_entry), _u32, ctypes.POINTER(_u32)]),
+    "phe_matmul_noalloc": (_i32, [_vp, _vp, _i32, _u32, _vp, _vp, _vp, _vp, _u32, _vp]),
 }
 
 _lib = None
@@ -199,3 +200,13 @@ def phe_trace_read(ctx) -> dict:
     return {arr[i].name.decode(): {"launches": int(arr[i].launches), "total_ms": arr[i].total_ms,
                                    "p50_ms": arr[i].p50_ms, "p99_ms": arr[i].p99_ms, "max_ms": arr[i].max_ms}
             for i in range(n.value)}
+
+
+PHE_NOALLOC_MAX_SCRATCH_BYTES = 16 << 20
+
+
+def phe_matmul_noalloc(ctx, w, direction: int, T: int, in_mask, in_body, out_mask, out_body,
+                       flags: int = PHE_OUT_SWITCHED, stream=None) -> None:
+    """phe_matmul with its scratch in the library's fixed device array (no allocation)."""
+    _check(lib().phe_matmul_noalloc(ctx, w, direction, T, _dptr(in_mask), _dptr(in_body), _dptr(out_mask),
+                                    _dptr(out_body), flags, _stream(stream)))
