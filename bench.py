@@ -38,6 +38,21 @@ import synth  # noqa: E402
 
 METRIC = "encrypted W·[x] tokens/s per Llama-1B layer; p50/p99 latency; % of roofline"
 ALU_PEAK_SOURCE = "register-only 64-bit Shoup butterfly probe"
+# DRAM bytes (read + write) per lwedot_kernel launch, measured with ncu on the
+# 14 products of one 32-token chunk of the layer workload (mean over the 14),
+# with the algorithmic bytes of the same launches.  Valid only for the kernel
+# sources the counters were taken on (hash of phe_kernels.cu + phe_device.cuh).
+TRAFFIC_KERNEL_HASH = "f44c15b967e04afd"
+TRAFFIC_BYTES_PER_LAUNCH = 2138.8e6
+TRAFFIC_ALG_BYTES_PER_LAUNCH = 1895.5e6
+
+
+def kernel_source_hash() -> str:
+    import hashlib
+    csrc = os.path.join(ROOT, "paper_2505_07329_b300", "csrc")
+    parts = [hashlib.sha256(open(os.path.join(csrc, f), "rb").read()).hexdigest()
+             for f in ("phe_kernels.cu", "phe_device.cuh")]
+    return hashlib.sha256((":".join(parts) + "\n").encode()).hexdigest()[:16]
 
 
 def parse():
@@ -47,7 +62,12 @@ def parse():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--workload", choices=["layer", "q_proj", "toy"], default="layer")
-    ap.add_argument("--chunk", type=int, default=32, help="tokens per call (output buffer reuse)")
+    ap.add_argument("--form", choices=["batched", "plain"], default="batched",
+                    help="batched: one autotuned plan (persistent launch, CUDA graph) per token chunk over all "
+                         "products; plain: one phe_matmul call per product and token chunk")
+    ap.add_argument("--chunk", type=int, default=32, help="tokens per plain-form call")
+    ap.add_argument("--batch-chunk", type=int, default=128, help="tokens per batched-form plan")
+    ap.add_argument("--no-compare", action="store_true", help="skip the secondary measurement of the other form")
     ap.add_argument("--tokens", type=int, default=0, help="override tokens per GPU (0 = the workload's)")
     ap.add_argument("--e2e-tokens", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
@@ -283,13 +303,17 @@ def main():
         inputs[key] = (A, B, X)
     keys = input_keys(wl)
     mm = matmuls(wl)
+    bchunk = min(args.batch_chunk, T)
+    uses_plans = args.form == "batched" or not args.no_compare
+    out_tokens = max(chunk, bchunk) if uses_plans else chunk
     outs = []
     for (pi, name, d, rows, cols, L) in mm:
-        outs.append((torch.empty((chunk, rows, N), dtype=torch.int32, device=dev),
-                     torch.empty((chunk, rows), dtype=torch.int32, device=dev)))
+        outs.append((torch.empty((out_tokens, rows, N), dtype=torch.int32, device=dev),
+                     torch.empty((out_tokens, rows), dtype=torch.int32, device=dev)))
     torch.cuda.synchronize()
+    side = torch.cuda.Stream(dev)
 
-    def step():
+    def plain_step():
         for t0 in range(0, T, chunk):
             tn = min(chunk, T - t0)
             for n, (pi, name, d, rows, cols, L) in enumerate(mm):
@@ -298,15 +322,50 @@ def main():
                 phe.phe_matmul(ctx, weights[pi], dirc, tn, A[t0:t0 + tn], B[t0:t0 + tn], outs[n][0], outs[n][1],
                                phe.PHE_OUT_SWITCHED, stream)
 
+    def chunk_jobs(t0, tn):
+        jobs = []
+        for n, (pi, name, d, rows, cols, L) in enumerate(mm):
+            A, B, _ = inputs[keys[(pi, d)][0]]
+            dirc = phe.PHE_FWD if d == "fwd" else phe.PHE_BWD
+            jobs.append((weights[pi], dirc, tn, A[t0:t0 + tn], B[t0:t0 + tn], outs[n][0], outs[n][1]))
+        return jobs
+
+    plans = []
+    tuning = None
+    tune_ms = None
+    if uses_plans:
+        # autotune on the first chunk's products (a 32-token sample), then one
+        # plan per chunk: pointers into the resident inputs, shared outputs
+        tuning, tune_ms = phe.phe_autotune(ctx, chunk_jobs(0, bchunk), phe.PHE_OUT_SWITCHED, 32, side)
+        for t0 in range(0, T, bchunk):
+            plans.append(phe.phe_plan_create(ctx, chunk_jobs(t0, min(bchunk, T - t0)), phe.PHE_OUT_SWITCHED, tuning))
+        plan_modmuls = sum(phe.phe_plan_info(pl)["modmuls"] for pl in plans)
+        assert plan_modmuls == modmuls_per_token(wl) * T
+
+    def batched_step(graph=True):
+        for pl in plans:
+            if graph:
+                phe.phe_plan_graph(pl, side)
+            else:
+                phe.phe_plan_run(pl, side)
+
+    run_stream = side if args.form == "batched" else stream
+    step = batched_step if args.form == "batched" else plain_step
+
+    # Library tracing is on from the first warm-up step, so that the plans'
+    # CUDA graphs are captured with event-record nodes around their lwedot
+    # launches: every timed launch is then bracketed by CUDA events on its own
+    # stream, for the plain form too.
+    phe.phe_trace_enable(ctx, True)
     for _ in range(max(args.warmup, 0)):
         step()
+        phe.phe_trace_read(ctx)
     torch.cuda.synchronize()
 
-    # sanity: the last chunk's first q-projection output decrypts to W x mod t
-    check = sanity_decrypt(wl, mm, inputs, keys, outs, S, T, chunk)
+    # sanity: outputs of the last chunk's first product decrypt to W x mod t
+    last_chunk = chunk if args.form == "plain" else bchunk
+    check = sanity_decrypt(wl, mm, inputs, keys, outs, S, T, last_chunk)
 
-    phe.phe_trace_enable(ctx, True)
-    phe.phe_trace_read(ctx)  # clear
     clocks = ClockSampler(local)
     if dist:
         dist.barrier()
@@ -315,23 +374,27 @@ def main():
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     step_ms = []
-    ev0.record(stream)
+    traces = []
+    ev0.record(run_stream)
     for _ in range(args.steps):
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
-        a.record(stream)
+        a.record(run_stream)
         step()
-        b.record(stream)
+        b.record(run_stream)
         step_ms.append((a, b))
-    ev1.record(stream)
+        if args.form == "batched":
+            traces.append(phe.phe_trace_read(ctx))  # graph events are re-recorded by the next replay
+    ev1.record(run_stream)
     torch.cuda.synchronize()
     clk = clocks.stop()
+    if args.form != "batched":
+        traces.append(phe.phe_trace_read(ctx))
+    phe.phe_trace_enable(ctx, False)
     if dist:
         dist.barrier()
     elapsed_ms = ev0.elapsed_time(ev1)
     step_ms = [a.elapsed_time(b) for a, b in step_ms]
-    trace = phe.phe_trace_read(ctx)
-    phe.phe_trace_enable(ctx, False)
     if dist:
         t = torch.tensor([elapsed_ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
@@ -339,22 +402,58 @@ def main():
     total_tokens = T * args.steps * world
     value = total_tokens / (elapsed_ms / 1e3)
 
-    # roofline of the dominant kernel (lwedot_kernel): algorithmic modmuls per
-    # launch over its event-timed duration; peak from the ALU probe.
+    trace = {}
+    for tr in traces:
+        for k, v in tr.items():
+            agg = trace.setdefault(k, {"launches": 0, "total_ms": 0.0, "p50s": [], "p99s": []})
+            agg["launches"] += v["launches"]
+            agg["total_ms"] += v["total_ms"]
+            agg["p50s"].append(v["p50_ms"])
+            agg["p99s"].append(v["p99_ms"])
+    for v in trace.values():
+        v["p50_ms"] = statistics.median(v.pop("p50s"))
+        v["p99_ms"] = max(v.pop("p99s"))
     lw = trace.get("lwedot_kernel", {})
     launches = lw.get("launches", 0)
     kernel_ms = lw.get("total_ms", 0.0)
     modmuls = modmuls_per_token(wl) * T * args.steps
     achieved = modmuls / (kernel_ms / 1e3) / 1e9 if kernel_ms else None
     peak = alu_peak_gmodmul()
+    traffic_ok = (kernel_source_hash() == TRAFFIC_KERNEL_HASH and wl.name == "layer" and chunk == 32
+                  and args.form == "plain")
     roof = {"bound": "alu", "unit": "Gmodmul/s", "achieved": achieved, "peak": peak,
-            "frac": (achieved / peak) if achieved and peak else None, "traffic": None,
+            "frac": (achieved / peak) if achieved and peak else None,
+            "traffic": TRAFFIC_BYTES_PER_LAUNCH if traffic_ok else None,
+            "traffic_alg_bytes": TRAFFIC_ALG_BYTES_PER_LAUNCH if traffic_ok else None,
             "peak_basis": f"148 SMs x {BFLY_PER_SM_CLK_MEASURED} butterflies/clk/SM ({ALU_PEAK_SOURCE}) x 2032 MHz",
             "kernel_ms_per_launch": kernel_ms / launches if launches else None,
-            "launches": launches, "share_of_step": kernel_ms / elapsed_ms if elapsed_ms else None,
+            "launches": launches,
+            "share_of_step": kernel_ms / elapsed_ms if elapsed_ms else None,
             "out_write_GBps": out_bytes_per_token(wl) * T * args.steps / (kernel_ms / 1e3) / 1e9 if kernel_ms else None}
-    gpu_launches = sum(v["launches"] for k, v in trace.items() if k != "phe_matmul")
-    calls = trace.get("phe_matmul", {})
+    if args.form == "batched":
+        # graph replays: the input transforms run inside the graphs without
+        # their own events; count them from the plans
+        per_step = sum(phe.phe_plan_info(pl)["launches"] for pl in plans)
+        gpu_launches = per_step * args.steps
+    else:
+        gpu_launches = sum(v["launches"] for k, v in trace.items() if not k.startswith("phe_"))
+
+    other = None
+    if not args.no_compare:
+        # the other form, measured the same way (1 warm-up + 1 timed step)
+        o_step = plain_step if args.form == "batched" else batched_step
+        o_stream = stream if args.form == "batched" else side
+        o_step()
+        torch.cuda.synchronize()
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(o_stream)
+        o_step()
+        b.record(o_stream)
+        torch.cuda.synchronize()
+        o_ms = a.elapsed_time(b)
+        other = {"form": "plain" if args.form == "batched" else "batched", "value": T / (o_ms / 1e3),
+                 "ms_per_step": o_ms, "steps": 1, "warmup": 1}
 
     e2e = None
     if not args.no_e2e:
@@ -364,19 +463,31 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = oracle_tokens_per_s(wl, args.cpu_seconds)
 
+    form_desc = ("batched: one autotuned plan per token chunk over all 14 products (one persistent lwedot launch, "
+                 "CUDA graph replay)" if args.form == "batched"
+                 else "plain per-call (one phe_matmul per projection and token chunk)")
+    calls = trace.get("phe_plan_graph") if args.form == "batched" else trace.get("phe_matmul")
+    calls = calls or {}
     if rank == 0:
+        cfg = workload_config(wl, args, form=form_desc)
+        cfg["batch_chunk"] = bchunk if args.form == "batched" else None
+        cfg["tuning"] = {"tok_chunk": tuning[0], "blocks_per_sm": tuning[1],
+                         "autotune_ms_per_token": tune_ms} if tuning else None
         line = {"metric": METRIC, "value": value, "unit": "tokens/s", "n_gpus": world, "steps": args.steps,
                 "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps, "higher_is_better": True,
                 "scaling": "weak", "vs_baseline": None, "dtype": "u64 mod q (u32 out mod 2^32)",
                 "data": "synthetic (seeded RLWE encryptions of uniform int8 activations; uniform int8 weights)",
-                "config": workload_config(wl, args, form="plain per-call (one phe_matmul per projection and token chunk)"),
+                "config": cfg,
                 "latency_ms": {"step_p50": statistics.median(step_ms), "step_max": max(step_ms),
                                "call_p50": calls.get("p50_ms"), "call_p99": calls.get("p99_ms"),
-                               "call_tokens": chunk},
+                               "call_tokens": bchunk if args.form == "batched" else chunk},
+                "other_form": other,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
                 "kernels": {k: {"launches": v["launches"], "total_ms": v["total_ms"]} for k, v in trace.items()},
                 "clocks": clk, "sanity_decrypt": check}
         print(json.dumps(line))
+    for pl in plans:
+        phe.phe_plan_destroy(pl)
     for w in weights:
         phe.phe_weights_free(w)
     phe.phe_ctx_destroy(ctx)

@@ -163,6 +163,72 @@ phe_status phe_trace_read(phe_ctx* ctx, phe_trace_entry* out, uint32_t cap, uint
 phe_status phe_client_encrypt(phe_ctx* ctx, uint32_t T, uint32_t d, const uint64_t* d_A, const int8_t* d_S,
                               const int32_t* d_E, const int8_t* d_x, uint64_t delta, uint64_t* d_B, void* stream);
 
+/* ---- Batched form ------------------------------------------------------
+ * Many products at once -- e.g. every projection of a layer in both
+ * directions, with uneven token counts -- as one plan.  A plan transforms
+ * each distinct input once (products that share d_in_mask, like the q, k and
+ * v projections of one x, share the transform) and runs every product's
+ * (row, token-chunk) tiles in one persistent lwedot launch per group of up
+ * to 32 products.  Buffers are fixed at creation; to process new data, write
+ * it into the same input buffers and run the plan again. */
+typedef struct phe_job {
+    const phe_weights* w;       /* weights (uploaded for `dir`) */
+    int32_t dir;                /* PHE_FWD or PHE_BWD */
+    uint32_t T;                 /* tokens (0 = skip) */
+    const uint64_t* d_in_mask;  /* [T][L][N] */
+    const uint64_t* d_in_body;  /* [T][L][N] */
+    void* d_out_mask;           /* [T][rows][N] */
+    void* d_out_body;           /* [T][rows] */
+} phe_job;
+
+/* Tile shape of a plan: tokens per (row, token-chunk) tile, and the
+ * persistent grid in blocks per SM (0 = one block per tile, not persistent). */
+typedef struct phe_tuning {
+    uint32_t tok_chunk;
+    uint32_t blocks_per_sm;
+} phe_tuning;
+
+typedef struct phe_plan_stats {
+    uint32_t launches;          /* kernel launches per run */
+    uint32_t lwedot_launches;
+    uint64_t tiles;
+    uint64_t scratch_bytes;     /* transformed inputs held by the plan */
+    uint64_t modmuls;           /* algorithmic modular multiplications per run */
+    phe_tuning tune;
+} phe_plan_stats;
+
+#define PHE_PLAN_MAX_JOBS 1024
+
+typedef struct phe_plan phe_plan;
+
+/* Build a plan over n_jobs products (same output mode `flags` for all);
+ * `tune` NULL selects {16 tokens, 3 blocks/SM}.  Allocates the transformed-
+ * input scratch (held until phe_plan_destroy).  Errors: PHE_EINVAL (a job's
+ * shapes or pointers, too many jobs), PHE_ENOMEM, PHE_ECUDA. */
+phe_status phe_plan_create(phe_ctx* ctx, const phe_job* jobs, uint32_t n_jobs, uint32_t flags,
+                           const phe_tuning* tune, phe_plan** out);
+/* Launch the plan's kernels on `stream` (asynchronous). */
+phe_status phe_plan_run(phe_plan* plan, void* stream);
+/* The same launches replayed from a CUDA graph: the first call captures
+ * them on `stream` (which must not be the legacy default stream) and
+ * instantiates the graph; every call launches it (asynchronous).  If tracing
+ * is on when the graph is captured, event-record nodes around each lwedot
+ * launch are captured too; each replay then adds their timings to the trace
+ * (read the trace before replaying the same plan again). */
+phe_status phe_plan_graph(phe_plan* plan, void* stream);
+phe_status phe_plan_info(const phe_plan* plan, phe_plan_stats* out);
+void phe_plan_destroy(phe_plan* plan);
+
+/* Autotuner: times candidate tile shapes (tokens per tile in
+ * {4, 8, 16, 32, 64} x persistent or one-block-per-tile grids) on the first
+ * `sample_tokens` tokens (0 = 64) of every job, with CUDA events on
+ * `stream` (non-default), and returns the fastest.  Writes the jobs' output
+ * buffers.  Results are cached per ring and job shapes; a cached answer is
+ * returned without timing unless best_ms_per_token is requested.
+ * Blocking.  Errors: PHE_EINVAL, PHE_ENOMEM, PHE_ECUDA. */
+phe_status phe_autotune(phe_ctx* ctx, const phe_job* jobs, uint32_t n_jobs, uint32_t flags, uint32_t sample_tokens,
+                        void* stream, phe_tuning* best, double* best_ms_per_token);
+
 /* Size of the fixed device scratch array used by phe_matmul_noalloc. */
 #define PHE_NOALLOC_MAX_SCRATCH_BYTES (16u << 20)
 

@@ -123,37 +123,7 @@ phe_status check_dir(const phe_weights* w, int dir) {
   return PHE_OK;
 }
 
-cudaEvent_t trace_event(phe_ctx* c) {
-  if (!c->tracer.pool.empty()) {
-    cudaEvent_t e = c->tracer.pool.back();
-    c->tracer.pool.pop_back();
-    return e;
-  }
-  cudaEvent_t e = nullptr;
-  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
-  return e;
-}
-
-// Brackets one launch (or one call) with events on its stream while tracing is on.
-struct Span {
-  phe_ctx* c;
-  int kid;
-  cudaStream_t s;
-  cudaEvent_t a = nullptr;
-  Span(phe_ctx* c_, int kid_, cudaStream_t s_) : c(c_), kid(kid_), s(s_) {
-    if (c->tracer.on && (a = trace_event(c)) != nullptr) cudaEventRecord(a, s);
-  }
-  ~Span() {
-    if (!a) return;
-    cudaEvent_t b = trace_event(c);
-    if (!b) {
-      c->tracer.pool.push_back(a);
-      return;
-    }
-    cudaEventRecord(b, s);
-    c->tracer.recs.push_back({kid, a, b});
-  }
-};
+using phe::Span;
 
 // The device form of the hot path for one projection.
 cudaError_t matmul_device(phe_ctx* c, const phe_weights::Dir& D, u32 T, const u64* in_mask, const u64* in_body,
@@ -311,6 +281,7 @@ void phe_ctx_destroy(phe_ctx* c) {
   for (auto& s : c->side)
     if (s) cudaStreamDestroy(s);
   for (auto& r : c->tracer.recs) {
+    if (r.borrowed) continue;
     cudaEventDestroy(r.a);
     cudaEventDestroy(r.b);
   }
@@ -492,8 +463,10 @@ phe_status phe_trace_read(phe_ctx* c, phe_trace_entry* out, uint32_t cap, uint32
     if (e == cudaSuccess) e = cudaEventElapsedTime(&t, r.a, r.b);
     if (e != cudaSuccess && err == cudaSuccess) err = e;
     ms[r.kid].push_back(t);
-    c->tracer.pool.push_back(r.a);
-    c->tracer.pool.push_back(r.b);
+    if (!r.borrowed) {
+      c->tracer.pool.push_back(r.a);
+      c->tracer.pool.push_back(r.b);
+    }
   }
   c->tracer.recs.clear();
   if (err != cudaSuccess) return cuda_fail(err, "phe_trace_read");

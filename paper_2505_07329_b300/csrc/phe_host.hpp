@@ -46,15 +46,16 @@ struct NttJob {             // forward transform of T*L input blocks
 enum OutMode : int { kOutSwitched = 0, kOutRaw = 1, kOutRing = 2 };
 
 // Kernel names for tracing; kKCall brackets a whole phe_matmul call.
-enum KernelId : int { kKInputNtt = 0, kKLwedot, kKModswitch, kKWeightNtt, kKCall, kKCount };
+enum KernelId : int { kKInputNtt = 0, kKLwedot, kKModswitch, kKWeightNtt, kKCall, kKPlan, kKGraph, kKCount };
 inline const char* kernel_name(int k) {
   static const char* names[kKCount] = {"input_ntt_kernel", "lwedot_kernel", "modswitch_kernel",
-                                       "weight_ntt_kernel", "phe_matmul"};
+                                       "weight_ntt_kernel", "phe_matmul", "phe_plan_run", "phe_plan_graph"};
   return (k >= 0 && k < kKCount) ? names[k] : "?";
 }
 struct TraceRec {
   int kid;
   cudaEvent_t a, b;
+  bool borrowed = false;  // events owned by a captured graph, not by the pool
 };
 struct Tracer {
   bool on = false;
@@ -96,6 +97,39 @@ struct phe_weights {
 
 namespace phe {
 
+// An event from the context's pool (or a new one); nullptr if none can be made.
+inline cudaEvent_t trace_event(phe_ctx* c) {
+  if (!c->tracer.pool.empty()) {
+    cudaEvent_t e = c->tracer.pool.back();
+    c->tracer.pool.pop_back();
+    return e;
+  }
+  cudaEvent_t e = nullptr;
+  if (cudaEventCreate(&e) != cudaSuccess) return nullptr;
+  return e;
+}
+
+// Brackets one launch (or one call) with events on its stream while tracing is on.
+struct Span {
+  phe_ctx* c;
+  int kid;
+  cudaStream_t s;
+  cudaEvent_t a = nullptr;
+  Span(phe_ctx* c_, int kid_, cudaStream_t s_) : c(c_), kid(kid_), s(s_) {
+    if (c->tracer.on && (a = trace_event(c)) != nullptr) cudaEventRecord(a, s);
+  }
+  ~Span() {
+    if (!a) return;
+    cudaEvent_t b = trace_event(c);
+    if (!b) {
+      c->tracer.pool.push_back(a);
+      return;
+    }
+    cudaEventRecord(b, s);
+    c->tracer.recs.push_back({kid, a, b});
+  }
+};
+
 // Launchers (phe_kernels.cu).  All asynchronous on `s`.
 cudaError_t launch_input_ntt(const phe_ctx* c, const NttJob* jobs, int n, cudaStream_t s);
 cudaError_t launch_weight_ntt(const phe_ctx* c, const int8_t* W, u32 rows, u32 cols, u32 row_stride,
@@ -103,6 +137,9 @@ cudaError_t launch_weight_ntt(const phe_ctx* c, const int8_t* W, u32 rows, u32 c
 cudaError_t launch_lwedot(const phe_ctx* c, const LweJobTable& jt, int mode, int grid_limit, cudaStream_t s);
 cudaError_t launch_modswitch(const phe_ctx* c, const u64* in, u32* out, size_t n, cudaStream_t s);
 int lwedot_threads(int logn);
+// Sets the dynamic shared-memory limits of the context's kernels (needed
+// before a launch is captured into a graph when a kernel exceeds 48 KB).
+cudaError_t prepare_launches(const phe_ctx* c);
 // Sets the calling thread's phe_last_error() message (phe_capi.cu).
 void set_last_error(const char* msg);
 size_t lwedot_smem(int logn);

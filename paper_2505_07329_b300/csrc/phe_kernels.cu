@@ -361,6 +361,30 @@ cudaError_t launch_lwedot(const phe_ctx* c, const LweJobTable& jt, int mode, int
   }
 }
 
+template <int LOGN>
+static cudaError_t prepare_impl() {
+  using S = Shape<LOGN>;
+  const size_t smem = (size_t)S::SLOTS * S::PADN * sizeof(u64);
+  cudaError_t e = set_smem(input_ntt_kernel<LOGN>, smem);
+  if (e == cudaSuccess) e = set_smem(weight_ntt_kernel<LOGN>, smem);
+  if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutSwitched>, smem);
+  if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutRaw>, smem);
+  if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutRing>, smem);
+  return e;
+}
+
+cudaError_t prepare_launches(const phe_ctx* c) {
+  switch (c->logn) {
+    case 8: return prepare_impl<8>();
+    case 9: return prepare_impl<9>();
+    case 10: return prepare_impl<10>();
+    case 11: return prepare_impl<11>();
+    case 12: return prepare_impl<12>();
+    case 13: return prepare_impl<13>();
+    default: return cudaErrorInvalidValue;
+  }
+}
+
 cudaError_t launch_modswitch(const phe_ctx* c, const u64* in, uint32_t* out, size_t n, cudaStream_t s) {
   if (n == 0) return cudaSuccess;
   size_t blocks = (n + 255) / 256;

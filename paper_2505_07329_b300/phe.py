@@ -36,6 +36,21 @@ class phe_trace_entry(ctypes.Structure):
                 ("p50_ms", ctypes.c_double), ("p99_ms", ctypes.c_double), ("max_ms", ctypes.c_double)]
 
 
+class phe_job(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_void_p), ("dir", ctypes.c_int32), ("T", ctypes.c_uint32),
+                ("d_in_mask", ctypes.c_void_p), ("d_in_body", ctypes.c_void_p),
+                ("d_out_mask", ctypes.c_void_p), ("d_out_body", ctypes.c_void_p)]
+
+
+class phe_tuning(ctypes.Structure):
+    _fields_ = [("tok_chunk", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32)]
+
+
+class phe_plan_stats(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_uint32), ("lwedot_launches", ctypes.c_uint32), ("tiles", ctypes.c_uint64),
+                ("scratch_bytes", ctypes.c_uint64), ("modmuls", ctypes.c_uint64), ("tune", phe_tuning)]
+
+
 _vp = ctypes.c_void_p
 _u32 = ctypes.c_uint32
 _u64 = ctypes.c_uint64
@@ -59,6 +74,14 @@ SIGNATURES = {
     "phe_trace_enable": (_i32, [_vp, _i32]),
     "phe_trace_read": (_i32, [_vp, ctypes.POINTER(phe_trace_entry), _u32, ctypes.POINTER(_u32)]),
     "phe_matmul_noalloc": (_i32, [_vp, _vp, _i32, _u32, _vp, _vp, _vp, _vp, _u32, _vp]),
+    "phe_plan_create": (_i32, [_vp, ctypes.POINTER(phe_job), _u32, _u32, ctypes.POINTER(phe_tuning),
+                               ctypes.POINTER(_vp)]),
+    "phe_plan_run": (_i32, [_vp, _vp]),
+    "phe_plan_graph": (_i32, [_vp, _vp]),
+    "phe_plan_info": (_i32, [_vp, ctypes.POINTER(phe_plan_stats)]),
+    "phe_plan_destroy": (None, [_vp]),
+    "phe_autotune": (_i32, [_vp, ctypes.POINTER(phe_job), _u32, _u32, _u32, _vp, ctypes.POINTER(phe_tuning),
+                            ctypes.POINTER(ctypes.c_double)]),
 }
 
 _lib = None
@@ -210,3 +233,49 @@ def phe_matmul_noalloc(ctx, w, direction: int, T: int, in_mask, in_body, out_mas
     """phe_matmul with its scratch in the library's fixed device array (no allocation)."""
     _check(lib().phe_matmul_noalloc(ctx, w, direction, T, _dptr(in_mask), _dptr(in_body), _dptr(out_mask),
                                     _dptr(out_body), flags, _stream(stream)))
+
+
+def _jobs(jobs):
+    """jobs: list of (weights, direction, T, in_mask, in_body, out_mask, out_body)."""
+    arr = (phe_job * max(len(jobs), 1))()
+    for i, (w, d, T, im, ib, om, ob) in enumerate(jobs):
+        arr[i] = phe_job(w, d, T, _dptr(im), _dptr(ib), _dptr(om), _dptr(ob))
+    return arr
+
+
+def phe_plan_create(ctx, jobs, flags: int = PHE_OUT_SWITCHED, tune=None):
+    arr = _jobs(jobs)
+    out = _vp()
+    t = phe_tuning(*tune) if tune is not None else None
+    _check(lib().phe_plan_create(ctx, arr, len(jobs), flags, ctypes.byref(t) if t is not None else None,
+                                 ctypes.byref(out)))
+    return out
+
+
+def phe_plan_run(plan, stream=None) -> None:
+    _check(lib().phe_plan_run(plan, _stream(stream)))
+
+
+def phe_plan_graph(plan, stream=None) -> None:
+    _check(lib().phe_plan_graph(plan, _stream(stream)))
+
+
+def phe_plan_info(plan) -> dict:
+    st = phe_plan_stats()
+    _check(lib().phe_plan_info(plan, ctypes.byref(st)))
+    return {"launches": st.launches, "lwedot_launches": st.lwedot_launches, "tiles": st.tiles,
+            "scratch_bytes": st.scratch_bytes, "modmuls": st.modmuls,
+            "tune": (st.tune.tok_chunk, st.tune.blocks_per_sm)}
+
+
+def phe_plan_destroy(plan) -> None:
+    lib().phe_plan_destroy(plan)
+
+
+def phe_autotune(ctx, jobs, flags: int = PHE_OUT_SWITCHED, sample_tokens: int = 64, stream=None, timed=True):
+    arr = _jobs(jobs)
+    best = phe_tuning()
+    ms = ctypes.c_double(0.0)
+    _check(lib().phe_autotune(ctx, arr, len(jobs), flags, sample_tokens, _stream(stream), ctypes.byref(best),
+                              ctypes.byref(ms) if timed else None))
+    return (best.tok_chunk, best.blocks_per_sm), (ms.value if timed else None)
