@@ -73,6 +73,8 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--serve-requests", type=int, default=48, help="requests in the serving measurement (0 = skip)")
+    ap.add_argument("--serve-rate", type=float, default=200.0, help="mean Poisson arrival rate, requests/s")
     return ap.parse_args()
 
 
@@ -459,6 +461,14 @@ def main():
     if not args.no_e2e:
         e2e = measure_e2e(phe, ctx, weights, wl, mm, keys, inputs, args.e2e_tokens, stream)
 
+    serving = None
+    if args.serve_requests > 0 and wl.name == "layer":
+        # release the batched plans' scratch first; the server allocates per chunk
+        for pl in plans:
+            phe.phe_plan_destroy(pl)
+        plans = []
+        serving = measure_serving(phe, ctx, weights, wl, inputs, keys, args.serve_requests, args.serve_rate, T)
+
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = oracle_tokens_per_s(wl, args.cpu_seconds)
@@ -482,6 +492,7 @@ def main():
                                "call_p50": calls.get("p50_ms"), "call_p99": calls.get("p99_ms"),
                                "call_tokens": bchunk if args.form == "batched" else chunk},
                 "other_form": other,
+                "serving": serving,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
                 "kernels": {k: {"launches": v["launches"], "total_ms": v["total_ms"]} for k, v in trace.items()},
                 "clocks": clk, "sanity_decrypt": check}
@@ -528,6 +539,58 @@ def sanity_decrypt(wl, mm, inputs, keys, outs, S, T, chunk):
             ok += int((dec - y) % synth.T_PLAIN == 0)
             tot += 1
     return f"{ok}/{tot}"
+
+
+def measure_serving(phe, ctx, weights, wl, inputs, keys, n_requests, rate, T_avail):
+    """The served form: requests from 64 clients arrive as a Poisson process
+    (mean `rate` per second); each is one projection of the layer in one
+    direction with U{64..2048} tokens (its inputs are slices of the resident
+    encrypted inputs).  A bounded horizon of `n_requests` requests; results
+    are computed and dropped.  Latency is submission -> last chunk done."""
+    r = synth.rng(synth.SEED_ARRIVALS)
+    gaps = r.exponential(1.0 / rate, size=n_requests)
+    arrivals = np.cumsum(gaps) - gaps[0]
+    projs = r.integers(0, len(wl.projections), size=n_requests)
+    dirs = r.integers(0, 2, size=n_requests)
+    toks = r.integers(64, 2049, size=n_requests)
+    N = wl.ring.N
+    srv = phe.phe_server_create(ctx, 24 << 30, chunk_tokens=32, tok_chunk=8, blocks_per_sm=0, max_active=64,
+                                max_jobs_per_iteration=64, max_queue=4096, wait_timeout_ms=600000)
+    ids = []
+    items = 0
+    tokens = 0
+    t0 = time.perf_counter()
+    try:
+        for k in range(n_requests):
+            pi, d, Tk = int(projs[k]), ("fwd", "bwd")[int(dirs[k])], int(toks[k])
+            key = keys[(pi, d)][0]
+            A, B, _ = inputs[key]
+            off = (k * 97) % max(1, T_avail - Tk + 1)
+            name, d_in, d_out = wl.projections[pi]
+            rows = d_out if d == "fwd" else d_in
+            items += Tk * rows
+            tokens += Tk
+            delay = arrivals[k] - (time.perf_counter() - t0)
+            if delay > 0:
+                time.sleep(delay)
+            ids.append(phe.phe_server_submit(srv, weights[pi], phe.PHE_FWD if d == "fwd" else phe.PHE_BWD, Tk,
+                                             A[off:off + Tk], B[off:off + Tk]))
+        for i in ids:
+            phe.phe_server_wait(srv, i, 600000)
+        wall = time.perf_counter() - t0
+        st = phe.phe_server_stats(srv)
+    finally:
+        phe.phe_server_destroy(srv)
+    busy = st["busy_ms"] / 1e3
+    per_layer_token = sum(rows for _, _, _, rows, _, _ in matmuls(wl))
+    return {"requests": n_requests, "clients": 64, "offered_rate_req_s": rate,
+            "offered_span_s": float(arrivals[-1]), "wall_s": wall, "served_req_s": n_requests / busy,
+            "served_tokens_s": tokens / busy, "layer_equiv_tokens_s": items / busy / per_layer_token,
+            "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"], "mean_ms": st["mean_ms"],
+            "iterations": st["iterations"], "mem_budget_bytes": 24 << 30,
+            "peak_reserved_bytes": st["peak_reserved_bytes"],
+            "note": "offered load is far above capacity, so latency is mostly queueing; tokens/s here are tokens of "
+                    "single-projection requests, layer_equiv divides (token,row) items by the 44032 of a layer token"}
 
 
 def measure_e2e(phe, ctx, weights, wl, mm, keys, inputs, tokens, stream):

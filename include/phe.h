@@ -229,6 +229,66 @@ void phe_plan_destroy(phe_plan* plan);
 phe_status phe_autotune(phe_ctx* ctx, const phe_job* jobs, uint32_t n_jobs, uint32_t flags, uint32_t sample_tokens,
                         void* stream, phe_tuning* best, double* best_ms_per_token);
 
+/* ---- Served form ---------------------------------------------------------
+ * A server that takes encrypted-matmul requests from many clients and layers
+ * as they arrive (continuous batching).  A worker thread runs iterations:
+ * each takes the next chunk of `chunk_tokens` tokens of every admitted
+ * request that still has tokens, in arrival order, as long as the chunk's
+ * device buffers fit `mem_budget_bytes`, and runs them all in one batched
+ * launch.  Requests arriving meanwhile join at the next iteration; buffers
+ * are reserved per chunk and released when it completes.  Two iterations
+ * are kept in flight.  Results of a chunk are copied to the request's host
+ * buffers, or dropped when none are given (benchmarking).  Every host wait
+ * is bounded by `wait_timeout_ms` (PHE_ETIMEOUT); a failed iteration fails
+ * the server and every unfinished request. */
+typedef struct phe_server_config {
+    uint64_t mem_budget_bytes;        /* device bytes for in-flight chunk buffers */
+    uint32_t chunk_tokens;            /* tokens of one request per iteration */
+    uint32_t tok_chunk;               /* tokens per kernel tile */
+    uint32_t blocks_per_sm;           /* persistent grid (0 = one block per tile) */
+    uint32_t max_active;              /* requests admitted at once */
+    uint32_t max_jobs_per_iteration;  /* chunks per iteration */
+    uint32_t max_queue;               /* waiting requests before PHE_EBUSY */
+    uint32_t wait_timeout_ms;         /* bound on every host wait */
+    uint32_t flags;                   /* PHE_OUT_SWITCHED or PHE_OUT_RAW */
+    uint32_t simulate;                /* 1: host-only scheduler test backend, no GPU */
+    double sim_ns_per_item;           /* simulated cost per (token, row) */
+} phe_server_config;
+
+typedef struct phe_request {
+    const phe_weights* w;
+    int32_t dir;
+    uint32_t T;
+    const uint64_t* d_in_mask;        /* device [T][L][N], valid until the request completes */
+    const uint64_t* d_in_body;
+    void* h_out_mask;                 /* host [T][rows][N] (pinned for async copies), or NULL */
+    void* h_out_body;                 /* host [T][rows], or NULL */
+    uint32_t sim_rows;                /* simulated backend only: output rows */
+} phe_request;
+
+typedef struct phe_serving_stats {
+    uint64_t submitted, completed, failed, tokens_completed, iterations;
+    uint64_t waiting, active, reserved_bytes, peak_reserved_bytes;
+    double p50_ms, p99_ms, max_ms, mean_ms;  /* submit -> results complete */
+    double busy_ms;                          /* first launch -> last completion */
+} phe_serving_stats;
+
+typedef struct phe_server phe_server;
+
+/* Errors: PHE_EINVAL (null or zero sizes), PHE_ECUDA. */
+phe_status phe_server_create(phe_ctx* ctx, const phe_server_config* cfg, phe_server** out);
+/* Thread-safe, non-blocking.  Errors: PHE_EINVAL, PHE_ENOMEM (one chunk of
+ * this request exceeds the budget), PHE_EBUSY (queue full), or the error
+ * that failed the server. */
+phe_status phe_server_submit(phe_server* srv, const phe_request* req, uint64_t* id);
+/* Wait at most timeout_ms for a request (PHE_ETIMEOUT otherwise). */
+phe_status phe_server_wait(phe_server* srv, uint64_t id, uint32_t timeout_ms, double* latency_ms);
+/* done: 1 complete, 0 pending, -1 failed. */
+phe_status phe_server_poll(phe_server* srv, uint64_t id, int* done, double* latency_ms);
+phe_status phe_server_stats(phe_server* srv, phe_serving_stats* out);
+/* Drains the admitted and waiting requests, then stops the worker. */
+void phe_server_destroy(phe_server* srv);
+
 /* Size of the fixed device scratch array used by phe_matmul_noalloc. */
 #define PHE_NOALLOC_MAX_SCRATCH_BYTES (16u << 20)
 

@@ -51,6 +51,26 @@ class phe_plan_stats(ctypes.Structure):
                 ("scratch_bytes", ctypes.c_uint64), ("modmuls", ctypes.c_uint64), ("tune", phe_tuning)]
 
 
+class phe_server_config(ctypes.Structure):
+    _fields_ = [("mem_budget_bytes", ctypes.c_uint64), ("chunk_tokens", ctypes.c_uint32),
+                ("tok_chunk", ctypes.c_uint32), ("blocks_per_sm", ctypes.c_uint32), ("max_active", ctypes.c_uint32),
+                ("max_jobs_per_iteration", ctypes.c_uint32), ("max_queue", ctypes.c_uint32),
+                ("wait_timeout_ms", ctypes.c_uint32), ("flags", ctypes.c_uint32), ("simulate", ctypes.c_uint32),
+                ("sim_ns_per_item", ctypes.c_double)]
+
+
+class phe_request(ctypes.Structure):
+    _fields_ = [("w", ctypes.c_void_p), ("dir", ctypes.c_int32), ("T", ctypes.c_uint32),
+                ("d_in_mask", ctypes.c_void_p), ("d_in_body", ctypes.c_void_p),
+                ("h_out_mask", ctypes.c_void_p), ("h_out_body", ctypes.c_void_p), ("sim_rows", ctypes.c_uint32)]
+
+
+class phe_serving_stats(ctypes.Structure):
+    _fields_ = [(n, ctypes.c_uint64) for n in ("submitted", "completed", "failed", "tokens_completed", "iterations",
+                                               "waiting", "active", "reserved_bytes", "peak_reserved_bytes")] + \
+               [(n, ctypes.c_double) for n in ("p50_ms", "p99_ms", "max_ms", "mean_ms", "busy_ms")]
+
+
 _vp = ctypes.c_void_p
 _u32 = ctypes.c_uint32
 _u64 = ctypes.c_uint64
@@ -82,6 +102,12 @@ SIGNATURES = {
     "phe_plan_destroy": (None, [_vp]),
     "phe_autotune": (_i32, [_vp, ctypes.POINTER(phe_job), _u32, _u32, _u32, _vp, ctypes.POINTER(phe_tuning),
                             ctypes.POINTER(ctypes.c_double)]),
+    "phe_server_create": (_i32, [_vp, ctypes.POINTER(phe_server_config), ctypes.POINTER(_vp)]),
+    "phe_server_submit": (_i32, [_vp, ctypes.POINTER(phe_request), ctypes.POINTER(_u64)]),
+    "phe_server_wait": (_i32, [_vp, _u64, _u32, ctypes.POINTER(ctypes.c_double)]),
+    "phe_server_poll": (_i32, [_vp, _u64, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double)]),
+    "phe_server_stats": (_i32, [_vp, ctypes.POINTER(phe_serving_stats)]),
+    "phe_server_destroy": (None, [_vp]),
 }
 
 _lib = None
@@ -279,3 +305,48 @@ def phe_autotune(ctx, jobs, flags: int = PHE_OUT_SWITCHED, sample_tokens: int = 
     _check(lib().phe_autotune(ctx, arr, len(jobs), flags, sample_tokens, _stream(stream), ctypes.byref(best),
                               ctypes.byref(ms) if timed else None))
     return (best.tok_chunk, best.blocks_per_sm), (ms.value if timed else None)
+
+
+def phe_server_create(ctx, mem_budget_bytes: int, chunk_tokens: int = 32, tok_chunk: int = 8, blocks_per_sm: int = 0,
+                      max_active: int = 64, max_jobs_per_iteration: int = 64, max_queue: int = 4096,
+                      wait_timeout_ms: int = 60000, flags: int = PHE_OUT_SWITCHED, simulate: bool = False,
+                      sim_ns_per_item: float = 0.0):
+    cfg = phe_server_config(mem_budget_bytes, chunk_tokens, tok_chunk, blocks_per_sm, max_active,
+                            max_jobs_per_iteration, max_queue, wait_timeout_ms, flags, 1 if simulate else 0,
+                            sim_ns_per_item)
+    out = _vp()
+    _check(lib().phe_server_create(ctx, ctypes.byref(cfg), ctypes.byref(out)))
+    return out
+
+
+def phe_server_submit(srv, w, direction: int, T: int, in_mask=None, in_body=None, h_out_mask=None, h_out_body=None,
+                      sim_rows: int = 0) -> int:
+    req = phe_request(w, direction, T, _dptr(in_mask), _dptr(in_body),
+                      _hptr(h_out_mask) if h_out_mask is not None else None,
+                      _hptr(h_out_body) if h_out_body is not None else None, sim_rows)
+    rid = _u64()
+    _check(lib().phe_server_submit(srv, ctypes.byref(req), ctypes.byref(rid)))
+    return rid.value
+
+
+def phe_server_wait(srv, rid: int, timeout_ms: int = 60000) -> float:
+    lat = ctypes.c_double()
+    _check(lib().phe_server_wait(srv, rid, timeout_ms, ctypes.byref(lat)))
+    return lat.value
+
+
+def phe_server_poll(srv, rid: int):
+    done = _i32()
+    lat = ctypes.c_double()
+    _check(lib().phe_server_poll(srv, rid, ctypes.byref(done), ctypes.byref(lat)))
+    return done.value, lat.value
+
+
+def phe_server_stats(srv) -> dict:
+    st = phe_serving_stats()
+    _check(lib().phe_server_stats(srv, ctypes.byref(st)))
+    return {name: getattr(st, name) for name, _ in phe_serving_stats._fields_}
+
+
+def phe_server_destroy(srv) -> None:
+    lib().phe_server_destroy(srv)
