@@ -262,9 +262,9 @@ def workload_config(wl, args, form):
 def main():
     args = parse()
     wl = synth.WORKLOADS[args.workload]
-    rank = int(os.environ.get("RANK", "0"))
-    world = int(os.environ.get("WORLD_SIZE", "1"))
-    local = int(os.environ.get("LOCAL_RANK", "0"))
+    from paper_2505_07329_b300.dist import max_over_ranks, weak_scaling_range
+    from paper_2505_07329_b300.dist import world as dist_world
+    rank, world, local = dist_world()
     if args.impl == "reference":
         return run_reference(args, wl, rank)
 
@@ -282,8 +282,11 @@ def main():
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
     ctx = phe.phe_ctx_create(N, q, wl.ring.log2_qout, local)
+    # this rank's shard of the global batch (weak scaling: T tokens per rank,
+    # seeded by the shard's first token; no collective on the data path)
+    shard = weak_scaling_range(T, rank)
     gen = torch.Generator(device=dev)
-    gen.manual_seed(synth.SEED_MASK + 1000 * rank)
+    gen.manual_seed(synth.SEED_MASK + shard[0])
 
     # weights (public, int8) for every projection, both directions
     weights = []
@@ -397,10 +400,7 @@ def main():
         dist.barrier()
     elapsed_ms = ev0.elapsed_time(ev1)
     step_ms = [a.elapsed_time(b) for a, b in step_ms]
-    if dist:
-        t = torch.tensor([elapsed_ms], device=dev)
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        elapsed_ms = float(t.item())
+    elapsed_ms = max_over_ranks(elapsed_ms, device=dev)
     total_tokens = T * args.steps * world
     value = total_tokens / (elapsed_ms / 1e3)
 
