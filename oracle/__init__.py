@@ -85,8 +85,7 @@ def lib():
             L.oracle_decode.restype = ctypes.c_int64
             L.oracle_decode.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint64]
             L.oracle_chacha20_block.argtypes = [_u32p, ctypes.c_uint32, _u32p, _u32p]
-            L.oracle_expand_mask.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint32,
-                                             ctypes.c_uint64, _u64p]
+            L.oracle_expand_mask.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, _u64p]
             L.oracle_num_threads.restype = ctypes.c_int
             _lib = L
     return _lib
@@ -281,10 +280,20 @@ def chacha20_block(key_words, counter: int, nonce_words) -> np.ndarray:
     return out
 
 
-def expand_mask(seed: int, token: int, block: int, N: int, q: int) -> np.ndarray:
+def expand_mask(seed: int, N: int, q: int) -> np.ndarray:
+    """Mask of one ciphertext from its 64-bit seed (ChaCha20 keystream, nonce 0)."""
     A = np.zeros(N, dtype=np.uint64)
-    lib().oracle_expand_mask(seed, token, block, N, q, _p(A, _u64p))
+    lib().oracle_expand_mask(seed, N, q, _p(A, _u64p))
     return A
+
+
+def expand_masks(seeds, N: int, q: int) -> np.ndarray:
+    """Masks for an array of seeds, shape seeds.shape + (N,)."""
+    seeds = np.asarray(seeds, dtype=np.uint64)
+    out = np.zeros(seeds.shape + (N,), dtype=np.uint64)
+    for idx in np.ndindex(seeds.shape):
+        out[idx] = expand_mask(int(seeds[idx]), N, q)
+    return out
 
 
 def num_threads() -> int:

@@ -386,13 +386,15 @@ void oracle_chacha20_block(const uint32_t key[8], uint32_t counter, const uint32
     for (int i = 0; i < 16; ++i) out[i] = x[i] + init[i];
 }
 
-/* Mask polynomial A of block `block` of token `token` from a 64-bit seed.
- * key = (seed lo, seed hi, 0, ..., 0); nonce = (block, token, 0);
- * coefficient m takes the 128-bit little-endian integer formed by words
- * 4*(m%4) .. 4*(m%4)+3 of the block with counter m/4, reduced mod q. */
-void oracle_expand_mask(uint64_t seed, uint32_t token, uint32_t block, uint32_t N, uint64_t q, uint64_t* A) {
+/* Mask polynomial A of one ciphertext from its 64-bit seed (Sec. 3.1: the
+ * client sends the seed and the body; both sides regenerate A).  Each
+ * ciphertext carries its own seed, so the expansion does not depend on where
+ * the ciphertext sits in a batch: key = (seed lo, seed hi, 0, ..., 0),
+ * nonce = 0; coefficient m takes the 128-bit little-endian integer formed by
+ * words 4*(m%4) .. 4*(m%4)+3 of the block with counter m/4, reduced mod q. */
+void oracle_expand_mask(uint64_t seed, uint32_t N, uint64_t q, uint64_t* A) {
     uint32_t key[8] = {(uint32_t)seed, (uint32_t)(seed >> 32), 0, 0, 0, 0, 0, 0};
-    uint32_t nonce[3] = {block, token, 0};
+    uint32_t nonce[3] = {0, 0, 0};
     uint32_t ks[16];
     for (uint32_t m = 0; m < N; ++m) {
         if (m % 4 == 0) oracle_chacha20_block(key, m / 4, nonce, ks);

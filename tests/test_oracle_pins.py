@@ -342,14 +342,16 @@ def test_chacha20_block_matches_cryptography_library(orc):
 
 
 def test_expand_mask_reads_chacha_keystream(orc):
+    # seeded mask: ChaCha20 keystream under key = seed, nonce = 0, 128 bits
+    # per coefficient reduced mod q (reading of the unnamed PRNG of Sec. 3.1)
     from cryptography.hazmat.primitives.ciphers import Cipher, algorithms
-    seed, token, block, N = 0x1234_5678_9ABC_DEF0, 7, 1, 64
-    A = orc.expand_mask(seed, token, block, N, Q)
+    seed, N = 0x1234_5678_9ABC_DEF0, 64
+    A = orc.expand_mask(seed, N, Q)
     key = seed.to_bytes(8, "little") + b"\x00" * 24
-    nonce = (0).to_bytes(4, "little") + block.to_bytes(4, "little") + token.to_bytes(4, "little") + b"\x00" * 4
-    ks = Cipher(algorithms.ChaCha20(key, nonce), mode=None).encryptor().update(b"\x00" * (16 * N))
+    ks = Cipher(algorithms.ChaCha20(key, b"\x00" * 16), mode=None).encryptor().update(b"\x00" * (16 * N))
     for m in range(N):
         v = int.from_bytes(ks[16 * m:16 * m + 16], "little")
         assert int(A[m]) == v % Q
-    A39 = orc.expand_mask(seed, token, block, N, 2 ** 39)
+    A39 = orc.expand_mask(seed, N, 2 ** 39)
     assert int(A39.max()) < 2 ** 39
+    assert not np.array_equal(orc.expand_mask(seed + 1, N, Q), A)
