@@ -118,6 +118,22 @@ uint64_t phe_weights_device_bytes(const phe_weights* w);
 phe_status phe_matmul(phe_ctx* ctx, const phe_weights* w, int dir, uint32_t T, const uint64_t* d_in_mask,
                       const uint64_t* d_in_body, void* d_out_mask, void* d_out_body, uint32_t flags, void* stream);
 
+/* Seeded input (Sec. 3.1, "Mask Generation via PRNG"): the client sends a
+ * 64-bit seed and the body per ciphertext; the server regenerates the mask.
+ * The paper does not name the PRNG; this library reads it as the ChaCha20
+ * keystream (RFC 8439) under key = seed (zero-extended), nonce = 0, with
+ * coefficient m taken from the 128 bits of words 4(m%4)..4(m%4)+3 of block
+ * m/4 (little-endian), reduced mod q.
+ *
+ * phe_matmul_seeded: as phe_matmul with d_in_seeds [T][L] uint64 in place of
+ * the masks; the masks are expanded inside the input transform and never
+ * stored.  phe_expand_masks: writes the n masks of d_seeds [n] to
+ * d_masks [n][N] (natural order).  Errors: as phe_matmul. */
+phe_status phe_matmul_seeded(phe_ctx* ctx, const phe_weights* w, int dir, uint32_t T, const uint64_t* d_in_seeds,
+                             const uint64_t* d_in_body, void* d_out_mask, void* d_out_body, uint32_t flags,
+                             void* stream);
+phe_status phe_expand_masks(phe_ctx* ctx, const uint64_t* d_seeds, uint32_t n, uint64_t* d_masks, void* stream);
+
 /* Unfused ModulusSwitch (Sec. 3.2): out[i] = round(in[i] * 2^k / q) mod 2^k,
  * ties rounded up, for n words (device buffers).  Input words are reduced
  * mod q first.  Errors: PHE_EINVAL, PHE_ECUDA. */
@@ -179,6 +195,8 @@ typedef struct phe_job {
     const uint64_t* d_in_body;  /* [T][L][N] */
     void* d_out_mask;           /* [T][rows][N] */
     void* d_out_body;           /* [T][rows] */
+    const uint64_t* d_in_seeds; /* [T][L] seeds; when not NULL the masks are expanded from them
+                                   (see phe_matmul_seeded) and d_in_mask is ignored */
 } phe_job;
 
 /* Tile shape of a plan: tokens per (row, token-chunk) tile, and the
@@ -264,6 +282,7 @@ typedef struct phe_request {
     void* h_out_mask;                 /* host [T][rows][N] (pinned for async copies), or NULL */
     void* h_out_body;                 /* host [T][rows], or NULL */
     uint32_t sim_rows;                /* simulated backend only: output rows */
+    const uint64_t* d_in_seeds;       /* [T][L] seeds in place of d_in_mask (NULL: use the masks) */
 } phe_request;
 
 typedef struct phe_serving_stats {

@@ -127,7 +127,7 @@ using phe::Span;
 
 // The device form of the hot path for one projection.
 cudaError_t matmul_device(phe_ctx* c, const phe_weights::Dir& D, u32 T, const u64* in_mask, const u64* in_body,
-                          void* out_mask, void* out_body, int mode, cudaStream_t s) {
+                          void* out_mask, void* out_body, int mode, cudaStream_t s, const u64* in_seeds = nullptr) {
   const u32 N = c->prm.N;
   Span call(c, phe::kKCall, s);
   u64* ahat = nullptr;
@@ -135,7 +135,7 @@ cudaError_t matmul_device(phe_ctx* c, const phe_weights::Dir& D, u32 T, const u6
   if (e != cudaSuccess) return e;
   {
     Span sp(c, phe::kKInputNtt, s);
-    phe::NttJob nj{in_mask, ahat, T * D.L};
+    phe::NttJob nj{in_mask, ahat, T * D.L, in_seeds};
     e = phe::launch_input_ntt(c, &nj, 1, s);
   }
   if (e == cudaSuccess) {
@@ -234,6 +234,8 @@ phe_status phe_ctx_create(const phe_params* prm, int device, phe_ctx** out) {
   rc.red_mu = (u64)(((u128)1 << 64) / q);
   rc.c30 = (1ull << 30) % q;
   rc.c30p = shoup(rc.c30, q);
+  rc.c64 = (u64)(((u128)1 << 64) % q);
+  rc.c64p = shoup(rc.c64, q);
   rc.log2_qout = prm->log2_qout;
   c->n_inv = powmod(N, q - 2, q);
   c->n_inv_p = shoup(c->n_inv, q);
@@ -375,6 +377,37 @@ phe_status phe_matmul(phe_ctx* c, const phe_weights* w, int dir, uint32_t T, con
                                 reinterpret_cast<const u64*>(d_in_body), d_out_mask, d_out_body, mode,
                                 (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "phe_matmul");
+  return PHE_OK;
+}
+
+phe_status phe_matmul_seeded(phe_ctx* c, const phe_weights* w, int dir, uint32_t T, const uint64_t* d_in_seeds,
+                             const uint64_t* d_in_body, void* d_out_mask, void* d_out_body, uint32_t flags,
+                             void* stream) {
+  phe_status st = check_matmul_args(c, w, dir, flags);
+  if (st != PHE_OK) return st;
+  if (T == 0) return PHE_OK;
+  if (!d_in_seeds || !d_in_body || !d_out_mask || !d_out_body)
+    return fail(PHE_EINVAL, "phe_matmul_seeded: null buffer");
+  if (T > (1u << 24)) return fail(PHE_EINVAL, "phe_matmul_seeded: T=%u exceeds 2^24", T);
+  DeviceGuard g(c->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  const int mode = flags == PHE_OUT_RAW ? phe::kOutRaw : phe::kOutSwitched;
+  cudaError_t e = matmul_device(c, w->dir[dir], T, nullptr, reinterpret_cast<const u64*>(d_in_body), d_out_mask,
+                                d_out_body, mode, (cudaStream_t)stream, reinterpret_cast<const u64*>(d_in_seeds));
+  if (e != cudaSuccess) return cuda_fail(e, "phe_matmul_seeded");
+  return PHE_OK;
+}
+
+phe_status phe_expand_masks(phe_ctx* c, const uint64_t* d_seeds, uint32_t n, uint64_t* d_masks, void* stream) {
+  if (!c) return fail(PHE_EINVAL, "phe_expand_masks: null context");
+  if (n == 0) return PHE_OK;
+  if (!d_seeds || !d_masks) return fail(PHE_EINVAL, "phe_expand_masks: null buffer");
+  DeviceGuard g(c->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  Span sp(c, phe::kKExpand, (cudaStream_t)stream);
+  cudaError_t e = phe::launch_expand_masks(c, reinterpret_cast<const u64*>(d_seeds), n,
+                                           reinterpret_cast<u64*>(d_masks), (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "phe_expand_masks");
   return PHE_OK;
 }
 

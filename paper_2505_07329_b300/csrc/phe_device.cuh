@@ -34,6 +34,8 @@ struct RingConst {
   u64 red_mu;     // floor(2^64 / q): Barrett constant for reducing a 64-bit word
   u64 c30;        // 2^30 mod q (recombines the split body accumulators)
   u64 c30p;       // Shoup quotient of c30
+  u64 c64;        // 2^64 mod q (reduces 128-bit keystream words of seeded masks)
+  u64 c64p;       // Shoup quotient of c64
   u32 ms_s;       // s = floor(log2 q)
   u32 log2_qout;  // k: output modulus 2^k, 1 <= k <= 32
 };
@@ -108,6 +110,58 @@ __device__ __forceinline__ u32 modswitch_word(u64 c, const RingConst& rc) {
   if (r >= rc.q) { r -= rc.q; ++quo; }
   if (r >= rc.q) { ++quo; }
   return (u32)(quo & ((k == 32) ? 0xffffffffull : ((1ull << k) - 1)));
+}
+
+// ---------------------------------------------------------------------------
+// Seeded masks (Sec. 3.1, "Mask Generation via PRNG", read as ChaCha20 with
+// the ciphertext's 64-bit seed as key and a zero nonce): coefficient m is the
+// 128-bit little-endian integer in words 4(m%4)..4(m%4)+3 of keystream block
+// m/4, reduced mod q.  The block function follows RFC 8439, Sec. 2.3.
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void chacha_quarter(u32& a, u32& b, u32& c, u32& d) {
+  a += b; d ^= a; d = __funnelshift_l(d, d, 16);
+  c += d; b ^= c; b = __funnelshift_l(b, b, 12);
+  a += b; d ^= a; d = __funnelshift_l(d, d, 8);
+  c += d; b ^= c; b = __funnelshift_l(b, b, 7);
+}
+
+// Keystream block `ctr` for key (seed, 0, ..., 0), nonce 0.
+__device__ __forceinline__ void chacha20_block(u64 seed, u32 ctr, u32 (&o)[16]) {
+  const u32 init[16] = {0x61707865u, 0x3320646eu, 0x79622d32u, 0x6b206574u, (u32)seed, (u32)(seed >> 32),
+                        0u, 0u, 0u, 0u, 0u, 0u, ctr, 0u, 0u, 0u};
+#pragma unroll
+  for (int i = 0; i < 16; ++i) o[i] = init[i];
+#pragma unroll 2
+  for (int r = 0; r < 10; ++r) {
+    chacha_quarter(o[0], o[4], o[8], o[12]);
+    chacha_quarter(o[1], o[5], o[9], o[13]);
+    chacha_quarter(o[2], o[6], o[10], o[14]);
+    chacha_quarter(o[3], o[7], o[11], o[15]);
+    chacha_quarter(o[0], o[5], o[10], o[15]);
+    chacha_quarter(o[1], o[6], o[11], o[12]);
+    chacha_quarter(o[2], o[7], o[8], o[13]);
+    chacha_quarter(o[3], o[4], o[9], o[14]);
+  }
+#pragma unroll
+  for (int i = 0; i < 16; ++i) o[i] += init[i];
+}
+
+// (hi 2^64 + lo) mod q, for the 128-bit keystream words.
+__device__ __forceinline__ u64 reduce_u128(u64 hi, u64 lo, const RingConst& rc) {
+  const u64 h = reduce_2q(mul_shoup(reduce_word(hi, rc), rc.c64, rc.c64p, rc.q), rc.q);
+  return reduce_2q(h + reduce_word(lo, rc), rc.q);
+}
+
+// The four mask coefficients 4*cb .. 4*cb+3 of the ciphertext with `seed`.
+__device__ __forceinline__ void seeded_mask4(u64 seed, u32 cb, const RingConst& rc, u64 (&v)[4]) {
+  u32 o[16];
+  chacha20_block(seed, cb, o);
+#pragma unroll
+  for (int c = 0; c < 4; ++c) {
+    const u64 lo = (u64)o[4 * c] | ((u64)o[4 * c + 1] << 32);
+    const u64 hi = (u64)o[4 * c + 2] | ((u64)o[4 * c + 3] << 32);
+    v[c] = reduce_u128(hi, lo, rc);
+  }
 }
 
 // ---------------------------------------------------------------------------

@@ -38,18 +38,21 @@ struct LweJobTable {
 };
 
 struct NttJob {             // forward transform of T*L input blocks
-  const u64* src;           // natural order [blocks][N]
+  const u64* src;           // natural order [blocks][N], or nullptr when `seeds` is given
   u64* dst;                 // A_hat layout [blocks][N]
   u32 blocks;
+  const u64* seeds = nullptr;  // [blocks] 64-bit seeds: masks expanded on the fly
 };
 
 enum OutMode : int { kOutSwitched = 0, kOutRaw = 1, kOutRing = 2 };
 
 // Kernel names for tracing; kKCall brackets a whole phe_matmul call.
-enum KernelId : int { kKInputNtt = 0, kKLwedot, kKModswitch, kKWeightNtt, kKCall, kKPlan, kKGraph, kKCount };
+enum KernelId : int {
+  kKInputNtt = 0, kKLwedot, kKModswitch, kKWeightNtt, kKExpand, kKCall, kKPlan, kKGraph, kKCount
+};
 inline const char* kernel_name(int k) {
-  static const char* names[kKCount] = {"input_ntt_kernel", "lwedot_kernel", "modswitch_kernel",
-                                       "weight_ntt_kernel", "phe_matmul", "phe_plan_run", "phe_plan_graph"};
+  static const char* names[kKCount] = {"input_ntt_kernel", "lwedot_kernel", "modswitch_kernel", "weight_ntt_kernel",
+                                       "expand_masks_kernel", "phe_matmul", "phe_plan_run", "phe_plan_graph"};
   return (k >= 0 && k < kKCount) ? names[k] : "?";
 }
 struct TraceRec {
@@ -136,6 +139,7 @@ cudaError_t launch_weight_ntt(const phe_ctx* c, const int8_t* W, u32 rows, u32 c
                               u32 col_stride, u32 L, int rev, ulonglong2* what, cudaStream_t s);
 cudaError_t launch_lwedot(const phe_ctx* c, const LweJobTable& jt, int mode, int grid_limit, cudaStream_t s);
 cudaError_t launch_modswitch(const phe_ctx* c, const u64* in, u32* out, size_t n, cudaStream_t s);
+cudaError_t launch_expand_masks(const phe_ctx* c, const u64* seeds, u32 n, u64* masks, cudaStream_t s);
 int lwedot_threads(int logn);
 // Sets the dynamic shared-memory limits of the context's kernels (needed
 // before a launch is captured into a graph when a kernel exceeds 48 KB).

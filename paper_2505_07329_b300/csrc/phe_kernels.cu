@@ -33,10 +33,28 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB)
   u64* buf = smem + slot * S::PADN;
   const u32 b = blockIdx.x * S::SLOTS + slot;
   const bool active = b < job.blocks;
-  const u64* src = job.src + (size_t)(active ? b : 0) * S::N;
   u64 x[16];
+  if (job.seeds) {
+    // Seeded mask: each thread expands 4 keystream blocks (16 coefficients)
+    // into shared memory in natural order, then loads its transform words.
+    const u64 seed = active ? job.seeds[b] : 0ull;
+#pragma unroll 1
+    for (int k = 0; k < 4; ++k) {
+      const u32 cb = p + k * S::P;
+      u64 v[4];
+      seeded_mask4(seed, cb, rc, v);
 #pragma unroll
-  for (int e = 0; e < 16; ++e) x[e] = active ? reduce_word(src[pass_pos<LOGN, NP - 1>(p, e)], rc) : 0ull;
+      for (int c = 0; c < 4; ++c) buf[pad_idx(4 * cb + c)] = v[c];
+    }
+    __syncthreads();
+#pragma unroll
+    for (int e = 0; e < 16; ++e) x[e] = buf[pad_idx(pass_pos<LOGN, NP - 1>(p, e))];
+    __syncthreads();
+  } else {
+    const u64* src = job.src + (size_t)(active ? b : 0) * S::N;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) x[e] = active ? reduce_word(src[pass_pos<LOGN, NP - 1>(p, e)], rc) : 0ull;
+  }
   ntt_regs<LOGN>(x, p, buf, tw0, twc, rc.q, rc.q2);
   if (active) {
     ulonglong2* dst = reinterpret_cast<ulonglong2*>(job.dst + (size_t)b * S::N);
@@ -248,6 +266,22 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, PHE_LWEDOT_MIN_BLOCKS)
   }
 }
 
+// Seeded masks written out in natural order: masks[i][m], m < N.
+__global__ void expand_masks_kernel(const u64* __restrict__ seeds, u32 n, u32 N, u64* __restrict__ masks,
+                                    RingConst rc) {
+  const size_t nblocks = (size_t)n * (N / 4);
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < nblocks;
+       idx += (size_t)gridDim.x * blockDim.x) {
+    const size_t i = idx / (N / 4);
+    const u32 cb = (u32)(idx % (N / 4));
+    u64 v[4];
+    seeded_mask4(seeds[i], cb, rc, v);
+    u64* out = masks + i * N + 4 * cb;
+#pragma unroll
+    for (int c = 0; c < 4; ++c) out[c] = v[c];
+  }
+}
+
 __global__ void modswitch_kernel(const u64* __restrict__ in, uint32_t* __restrict__ out, size_t n, RingConst rc) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
     out[i] = modswitch_word(reduce_word(in[i], rc), rc);
@@ -383,6 +417,16 @@ cudaError_t prepare_launches(const phe_ctx* c) {
     case 13: return prepare_impl<13>();
     default: return cudaErrorInvalidValue;
   }
+}
+
+cudaError_t launch_expand_masks(const phe_ctx* c, const u64* seeds, u32 n, u64* masks, cudaStream_t s) {
+  if (n == 0) return cudaSuccess;
+  const size_t work = (size_t)n * (c->prm.N / 4);
+  size_t blocks = (work + 255) / 256;
+  const size_t cap = (size_t)c->num_sms * 16;
+  if (blocks > cap) blocks = cap;
+  expand_masks_kernel<<<(unsigned)blocks, 256, 0, s>>>(seeds, n, c->prm.N, masks, c->rc);
+  return cudaGetLastError();
 }
 
 cudaError_t launch_modswitch(const phe_ctx* c, const u64* in, uint32_t* out, size_t n, cudaStream_t s) {

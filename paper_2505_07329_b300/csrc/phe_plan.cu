@@ -22,6 +22,7 @@ struct phe_plan {
   phe_tuning tune{};
   struct Input {
     const u64* mask = nullptr;
+    const u64* seeds = nullptr;
     u32 blocks = 0;
     u64* ahat = nullptr;
   };
@@ -73,7 +74,7 @@ phe_status check_job(const phe_ctx* c, const phe_job& j, uint32_t idx) {
   if (j.dir != PHE_FWD && j.dir != PHE_BWD) return fail(PHE_EINVAL, "job %u: bad direction %d", idx, j.dir);
   if (!(j.w->dirs & (1u << j.dir))) return fail(PHE_EINVAL, "job %u: direction was not uploaded", idx);
   if (j.T > (1u << 24)) return fail(PHE_EINVAL, "job %u: T=%u exceeds 2^24", idx, j.T);
-  if (j.T && (!j.d_in_mask || !j.d_in_body || !j.d_out_mask || !j.d_out_body))
+  if (j.T && ((!j.d_in_mask && !j.d_in_seeds) || !j.d_in_body || !j.d_out_mask || !j.d_out_body))
     return fail(PHE_EINVAL, "job %u: null buffer", idx);
   return PHE_OK;
 }
@@ -102,7 +103,7 @@ cudaError_t run_plan(phe_plan* p, cudaStream_t s, bool trace, bool capture_event
   phe_ctx* c = p->ctx;
   cudaError_t e = cudaSuccess;
   for (auto& in : p->inputs) {
-    phe::NttJob nj{in.mask, in.ahat, in.blocks};
+    phe::NttJob nj{in.mask, in.ahat, in.blocks, in.seeds};
     if (trace) {
       phe::Span sp(c, phe::kKInputNtt, s);
       e = phe::launch_input_ntt(c, &nj, 1, s);
@@ -184,14 +185,16 @@ phe_status phe_plan_create(phe_ctx* c, const phe_job* jobs, uint32_t n_jobs, uin
     if (j.T == 0) continue;
     const phe_weights::Dir& D = j.w->dir[j.dir];
     // one forward transform per distinct input
-    const u64* mask = reinterpret_cast<const u64*>(j.d_in_mask);
+    const u64* seeds = reinterpret_cast<const u64*>(j.d_in_seeds);
+    const u64* mask = seeds ? nullptr : reinterpret_cast<const u64*>(j.d_in_mask);
     const u32 blocks = j.T * D.L;
     size_t k = 0;
     for (; k < p->inputs.size(); ++k)
-      if (p->inputs[k].mask == mask && p->inputs[k].blocks == blocks) break;
+      if (p->inputs[k].mask == mask && p->inputs[k].seeds == seeds && p->inputs[k].blocks == blocks) break;
     if (k == p->inputs.size()) {
       phe_plan::Input in;
       in.mask = mask;
+      in.seeds = seeds;
       in.blocks = blocks;
       e = cudaMalloc((void**)&in.ahat, (size_t)blocks * N * sizeof(u64));
       if (e != cudaSuccess) {

@@ -145,7 +145,11 @@ cudaError_t launch_iteration(phe_server* s, Iteration& it) {
     if ((e = cudaMallocAsync(&j.om, (size_t)j.tn * D.rows * N * osz, s->stream)) != cudaSuccess) return e;
     if ((e = cudaMallocAsync(&j.ob, (size_t)j.tn * D.rows * osz, s->stream)) != cudaSuccess) return e;
     const size_t tok_words = (size_t)D.L * N;
-    phe::NttJob nj{reinterpret_cast<const u64*>(q->r.d_in_mask) + (size_t)j.t0 * tok_words, j.ahat, j.tn * D.L};
+    phe::NttJob nj{nullptr, j.ahat, j.tn * D.L};
+    if (q->r.d_in_seeds)
+      nj.seeds = reinterpret_cast<const u64*>(q->r.d_in_seeds) + (size_t)j.t0 * D.L;
+    else
+      nj.src = reinterpret_cast<const u64*>(q->r.d_in_mask) + (size_t)j.t0 * tok_words;
     if ((e = phe::launch_input_ntt(c, &nj, 1, s->stream)) != cudaSuccess) return e;
     phe::LweJobTable& t = tables.back();
     phe::LweJob& J = t.j[t.n];
@@ -346,7 +350,8 @@ phe_status phe_server_submit(phe_server* s, const phe_request* r, uint64_t* id) 
     if (!r->w || r->w->ctx != s->ctx) return fail(PHE_EINVAL, "phe_server_submit: weights of another context");
     if (r->dir != PHE_FWD && r->dir != PHE_BWD) return fail(PHE_EINVAL, "phe_server_submit: bad direction");
     if (!(r->w->dirs & (1u << r->dir))) return fail(PHE_EINVAL, "phe_server_submit: direction not uploaded");
-    if (r->T && (!r->d_in_mask || !r->d_in_body)) return fail(PHE_EINVAL, "phe_server_submit: null input");
+    if (r->T && ((!r->d_in_mask && !r->d_in_seeds) || !r->d_in_body))
+      return fail(PHE_EINVAL, "phe_server_submit: null input");
     if ((r->h_out_mask == nullptr) != (r->h_out_body == nullptr))
       return fail(PHE_EINVAL, "phe_server_submit: give both host outputs or neither");
     const phe_weights::Dir& D = r->w->dir[r->dir];

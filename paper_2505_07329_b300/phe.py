@@ -39,7 +39,7 @@ class phe_trace_entry(ctypes.Structure):
 class phe_job(ctypes.Structure):
     _fields_ = [("w", ctypes.c_void_p), ("dir", ctypes.c_int32), ("T", ctypes.c_uint32),
                 ("d_in_mask", ctypes.c_void_p), ("d_in_body", ctypes.c_void_p),
-                ("d_out_mask", ctypes.c_void_p), ("d_out_body", ctypes.c_void_p)]
+                ("d_out_mask", ctypes.c_void_p), ("d_out_body", ctypes.c_void_p), ("d_in_seeds", ctypes.c_void_p)]
 
 
 class phe_tuning(ctypes.Structure):
@@ -62,7 +62,8 @@ class phe_server_config(ctypes.Structure):
 class phe_request(ctypes.Structure):
     _fields_ = [("w", ctypes.c_void_p), ("dir", ctypes.c_int32), ("T", ctypes.c_uint32),
                 ("d_in_mask", ctypes.c_void_p), ("d_in_body", ctypes.c_void_p),
-                ("h_out_mask", ctypes.c_void_p), ("h_out_body", ctypes.c_void_p), ("sim_rows", ctypes.c_uint32)]
+                ("h_out_mask", ctypes.c_void_p), ("h_out_body", ctypes.c_void_p), ("sim_rows", ctypes.c_uint32),
+                ("d_in_seeds", ctypes.c_void_p)]
 
 
 class phe_serving_stats(ctypes.Structure):
@@ -108,6 +109,8 @@ SIGNATURES = {
     "phe_server_poll": (_i32, [_vp, _u64, ctypes.POINTER(_i32), ctypes.POINTER(ctypes.c_double)]),
     "phe_server_stats": (_i32, [_vp, ctypes.POINTER(phe_serving_stats)]),
     "phe_server_destroy": (None, [_vp]),
+    "phe_matmul_seeded": (_i32, [_vp, _vp, _i32, _u32, _vp, _vp, _vp, _vp, _u32, _vp]),
+    "phe_expand_masks": (_i32, [_vp, _vp, _u32, _vp, _vp]),
 }
 
 _lib = None
@@ -262,10 +265,12 @@ def phe_matmul_noalloc(ctx, w, direction: int, T: int, in_mask, in_body, out_mas
 
 
 def _jobs(jobs):
-    """jobs: list of (weights, direction, T, in_mask, in_body, out_mask, out_body)."""
+    """jobs: list of (weights, direction, T, in_mask, in_body, out_mask, out_body[, in_seeds])."""
     arr = (phe_job * max(len(jobs), 1))()
-    for i, (w, d, T, im, ib, om, ob) in enumerate(jobs):
-        arr[i] = phe_job(w, d, T, _dptr(im), _dptr(ib), _dptr(om), _dptr(ob))
+    for i, job in enumerate(jobs):
+        w, d, T, im, ib, om, ob = job[:7]
+        seeds = job[7] if len(job) > 7 else None
+        arr[i] = phe_job(w, d, T, _dptr(im), _dptr(ib), _dptr(om), _dptr(ob), _dptr(seeds))
     return arr
 
 
@@ -320,10 +325,10 @@ def phe_server_create(ctx, mem_budget_bytes: int, chunk_tokens: int = 32, tok_ch
 
 
 def phe_server_submit(srv, w, direction: int, T: int, in_mask=None, in_body=None, h_out_mask=None, h_out_body=None,
-                      sim_rows: int = 0) -> int:
+                      sim_rows: int = 0, in_seeds=None) -> int:
     req = phe_request(w, direction, T, _dptr(in_mask), _dptr(in_body),
                       _hptr(h_out_mask) if h_out_mask is not None else None,
-                      _hptr(h_out_body) if h_out_body is not None else None, sim_rows)
+                      _hptr(h_out_body) if h_out_body is not None else None, sim_rows, _dptr(in_seeds))
     rid = _u64()
     _check(lib().phe_server_submit(srv, ctypes.byref(req), ctypes.byref(rid)))
     return rid.value
@@ -350,3 +355,14 @@ def phe_server_stats(srv) -> dict:
 
 def phe_server_destroy(srv) -> None:
     lib().phe_server_destroy(srv)
+
+
+def phe_matmul_seeded(ctx, w, direction: int, T: int, in_seeds, in_body, out_mask, out_body,
+                      flags: int = PHE_OUT_SWITCHED, stream=None) -> None:
+    """phe_matmul with per-ciphertext 64-bit seeds [T][L] in place of the masks."""
+    _check(lib().phe_matmul_seeded(ctx, w, direction, T, _dptr(in_seeds), _dptr(in_body), _dptr(out_mask),
+                                   _dptr(out_body), flags, _stream(stream)))
+
+
+def phe_expand_masks(ctx, seeds, n: int, masks, stream=None) -> None:
+    _check(lib().phe_expand_masks(ctx, _dptr(seeds), n, _dptr(masks), _stream(stream)))
