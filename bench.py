@@ -37,7 +37,6 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "encrypted W·[x] tokens/s per Llama-1B layer; p50/p99 latency; % of roofline"
-ALU_PEAK_SOURCE = "register-only 64-bit Shoup butterfly probe"
 # DRAM bytes (read + write) per lwedot_kernel launch, measured with ncu on the
 # 14 products of one 32-token chunk of the layer workload (mean over the 14),
 # with the algorithmic bytes of the same launches.  Valid only for the kernel
@@ -73,6 +72,9 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--modulus", choices=["rns", "prime"], default="rns",
+                    help="rns: q = p1 p2 (two 30-bit NTT primes, 32-bit residue kernels); "
+                         "prime: q = 2^60 - 2^14 + 1 (64-bit kernels)")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests in the serving measurement (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="mean Poisson arrival rate, requests/s")
     return ap.parse_args()
@@ -247,9 +249,11 @@ def run_reference(args, wl, rank):
 
 
 def workload_config(wl, args, form):
+    qdesc = (f"{synth.RNS_P1}*{synth.RNS_P2} (RNS, two 30-bit NTT primes)"
+             if getattr(args, "modulus", "prime") == "rns" else "2^60-2^14+1 (prime)")
     return {"workload": f"llama3.2-1b-{wl.name}" if wl.name != "toy" else "toy",
             "description": wl.description, "tokens_per_gpu": args.tokens or wl.tokens,
-            "N": wl.ring.N, "q": "2^60-2^14+1", "q_out": f"2^{wl.ring.log2_qout}",
+            "N": wl.ring.N, "q": qdesc, "q_out": f"2^{wl.ring.log2_qout}",
             "projections": [f"{n} {di}->{do}" for n, di, do in wl.projections],
             "directions": list(wl.directions), "form": form, "token_chunk": args.chunk,
             "l2": "inputs larger than L2 (encrypted inputs and encoded weights are several GB)"}
@@ -276,12 +280,18 @@ def main():
         import torch.distributed as dist
         dist.init_process_group("nccl", device_id=torch.device("cuda", local))
 
-    N, q = wl.ring.N, wl.ring.q
+    N = wl.ring.N
     T = args.tokens or wl.tokens
     chunk = min(args.chunk, T)
     dev = torch.device("cuda", local)
     stream = torch.cuda.current_stream(dev)
-    ctx = phe.phe_ctx_create(N, q, wl.ring.log2_qout, local)
+    if args.modulus == "rns":
+        q = synth.Q_RNS
+        ctx = phe.phe_ctx_create(N, q, wl.ring.log2_qout, local, rns=(synth.RNS_P1, synth.RNS_P2))
+    else:
+        q = wl.ring.q
+        ctx = phe.phe_ctx_create(N, q, wl.ring.log2_qout, local)
+    delta = q // wl.ring.t
     # this rank's shard of the global batch (weak scaling: T tokens per rank,
     # seeded by the shard's first token; no collective on the data path)
     shard = weak_scaling_range(T, rank)
@@ -304,7 +314,7 @@ def main():
         E = torch.round(torch.randn((T, L, N), device=dev, generator=gen) * wl.ring.sigma).to(torch.int32)
         X = torch.randint(-127, 128, (T, cols), device=dev, generator=gen, dtype=torch.int8)
         B = torch.empty_like(A)
-        phe.phe_client_encrypt(ctx, T, cols, A, S, E, X, wl.ring.delta, B)
+        phe.phe_client_encrypt(ctx, T, cols, A, S, E, X, delta, B)
         inputs[key] = (A, B, X)
     keys = input_keys(wl)
     mm = matmuls(wl)
@@ -420,14 +430,17 @@ def main():
     kernel_ms = lw.get("total_ms", 0.0)
     modmuls = modmuls_per_token(wl) * T * args.steps
     achieved = modmuls / (kernel_ms / 1e3) / 1e9 if kernel_ms else None
-    peak = alu_peak_gmodmul()
+    peak = alu_peak_gmodmul(args.modulus)
     traffic_ok = (kernel_source_hash() == TRAFFIC_KERNEL_HASH and wl.name == "layer" and chunk == 32
                   and args.form == "plain")
     roof = {"bound": "alu", "unit": "Gmodmul/s", "achieved": achieved, "peak": peak,
             "frac": (achieved / peak) if achieved and peak else None,
             "traffic": TRAFFIC_BYTES_PER_LAUNCH if traffic_ok else None,
             "traffic_alg_bytes": TRAFFIC_ALG_BYTES_PER_LAUNCH if traffic_ok else None,
-            "peak_basis": f"148 SMs x {BFLY_PER_SM_CLK_MEASURED} butterflies/clk/SM ({ALU_PEAK_SOURCE}) x 2032 MHz",
+            "peak_basis": (f"148 SMs x {BFLY32_PER_SM_CLK} 32-bit butterflies/clk/SM / 2 residues x 2032 MHz"
+                           if args.modulus == "rns" else
+                           f"148 SMs x {BFLY64_PER_SM_CLK} 64-bit butterflies/clk/SM x 2032 MHz") +
+                          " (register-only butterfly probe); unit: coefficient modmuls",
             "kernel_ms_per_launch": kernel_ms / launches if launches else None,
             "launches": launches,
             "share_of_step": kernel_ms / elapsed_ms if elapsed_ms else None,
@@ -507,11 +520,20 @@ def main():
     return 0
 
 
-BFLY_PER_SM_CLK_MEASURED = 2.62
+# Register-only, dependency-free butterfly probes on B300 (one full wave,
+# 0.1-0.2 s per run, clocks 1950-2032 MHz): 750.7 G 64-bit Harvey/Shoup
+# butterflies/s and 3030 G 32-bit ones/s, i.e. 2.50 and 10.07 per SM per clock
+# taken at the 2032 MHz maximum (so the peaks below are not understated).
+BFLY64_PER_SM_CLK = 2.50
+BFLY32_PER_SM_CLK = 10.07
 
 
-def alu_peak_gmodmul():
-    return 148 * BFLY_PER_SM_CLK_MEASURED * 2.032
+def alu_peak_gmodmul(modulus: str) -> float:
+    """Peak coefficient modmuls/s: one 64-bit Shoup butterfly per coefficient
+    modmul in the 64-bit form; two 32-bit ones (one per residue) in the RNS form."""
+    if modulus == "rns":
+        return 148 * BFLY32_PER_SM_CLK / 2 * 2.032
+    return 148 * BFLY64_PER_SM_CLK * 2.032
 
 
 def sanity_decrypt(wl, mm, inputs, keys, outs, S, T, chunk):

@@ -61,14 +61,26 @@ typedef struct phe_weights phe_weights;
 /* Ring and switch parameters (Sec. 3.1 RLWE ciphertexts over
  * R_q = Z_q[X]/(X^N+1); Sec. 3.2 ModulusSwitch q -> q_out).
  *   N          ring degree, a power of two in [256, 8192]
- *   q          ciphertext modulus: a prime with q = 1 (mod 2N) and
- *              2^53 < q < 2^61 (e.g. 2^60 - 2^14 + 1)
- *   log2_qout  k of the output modulus q' = 2^k, 1 <= k <= 32 */
+ *   q          ciphertext modulus, 2^53 < q < 2^61, either
+ *                - a prime with q = 1 (mod 2N) (e.g. 2^60 - 2^14 + 1;
+ *                  rns_p1 = rns_p2 = 0), or
+ *                - an RNS modulus q = rns_p1 * rns_p2 of two distinct primes
+ *                  below 2^30, each = 1 (mod 2N) (e.g. 1073643521 *
+ *                  1073692673); the hot path then runs on 32-bit residues
+ *                  and returns to q by the CRT before the switch
+ *   log2_qout  k of the output modulus q' = 2^k, 1 <= k <= 32
+ *   flags      PHE_CTX_FORCE_U64: with an RNS modulus, run the 64-bit form
+ *              anyway (the results are identical; for cross-checks) */
 typedef struct phe_params {
     uint32_t N;
     uint32_t log2_qout;
     uint64_t q;
+    uint32_t rns_p1;
+    uint32_t rns_p2;
+    uint32_t flags;
 } phe_params;
+
+#define PHE_CTX_FORCE_U64 1u
 
 #define PHE_FWD 0              /* W   . [x] : rows = d_out, contraction over d_in */
 #define PHE_BWD 1              /* W^T . [g] : rows = d_in,  contraction over d_out */

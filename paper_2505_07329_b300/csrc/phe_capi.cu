@@ -1,6 +1,7 @@
 // C ABI of libphe (include/phe.h): parameter validation, twiddle tables,
 // weight upload and the per-call hot path.
 #include <algorithm>
+#include <cstdint>
 #include <cmath>
 #include <cstdarg>
 #include <cstdio>
@@ -82,6 +83,30 @@ bool is_prime(u64 n) {
   return true;
 }
 u64 shoup(u64 w, u64 q) { return (u64)(((u128)w << 64) / q); }
+u32 shoup32(u32 w, u32 p) { return (u32)(((u64)w << 32) / p); }
+
+// a^-1 mod m for gcd(a, m) = 1, by the extended Euclidean algorithm (m need
+// not be prime).
+u64 modinv(u64 a, u64 m) {
+  __int128 t = 0, nt = 1, r = m, nr = a % m;
+  while (nr != 0) {
+    const __int128 qq = r / nr;
+    __int128 tmp = t - qq * nt;
+    t = nt;
+    nt = tmp;
+    tmp = r - qq * nr;
+    r = nr;
+    nr = tmp;
+  }
+  if (t < 0) t += m;
+  return (u64)t;
+}
+
+// The x mod p1 p2 with x = a (mod p1), x = b (mod p2).
+u64 crt2(u64 a, u64 p1, u64 b, u64 p2) {
+  const u64 h = mulmod((b + p2 - a % p2) % p2, modinv(p1 % p2, p2), p2);
+  return a + p1 * h;
+}
 u32 bitrev(u32 x, int bits) {
   u32 r = 0;
   for (int i = 0; i < bits; ++i) r |= ((x >> i) & 1u) << (bits - 1 - i);
@@ -98,6 +123,41 @@ u64 primitive_root_2n(u64 q, u32 N) {
     if (powmod(psi, N, q) == q - 1) return psi;
   }
   return 0;
+}
+
+phe_status upload(void** dptr, const void* host, size_t bytes);
+
+// Compact and pass-0 tables (forward and inverse) from entry(brv(k), inverse).
+// Pass-0 twiddles in thread-major order: slot (st, b) of thread p is the
+// twiddle of stage st for butterfly group b of positions [16p, 16p+16).
+template <class F>
+phe_status build_tables(const phe_ctx* c, F entry, phe::Tables& tab) {
+  const u32 N = c->prm.N;
+  const int logn = c->logn;
+  std::vector<ulonglong2> fwd(N), inv(N);
+  for (u32 k = 0; k < N; ++k) {
+    const u32 br = bitrev(k, logn);
+    fwd[k] = entry(br, false);
+    inv[k] = entry(br, true);
+  }
+  const u32 P = N / 16;
+  std::vector<ulonglong2> fwd0(15 * P), inv0(15 * P);
+  for (int st = 0; st < 4; ++st) {
+    for (int b = 0; b < (8 >> st); ++b) {
+      for (u32 p = 0; p < P; ++p) {
+        const u32 idx = (N >> (st + 1)) + ((16 * p) >> (st + 1)) + b;
+        fwd0[phe::pass0_slot(st, b) * P + p] = fwd[idx];
+        inv0[phe::pass0_slot(st, b) * P + p] = inv[idx];
+      }
+    }
+  }
+  phe_status st;
+  if ((st = upload((void**)&tab.fwd_c, fwd.data(), N * sizeof(ulonglong2))) != PHE_OK ||
+      (st = upload((void**)&tab.inv_c, inv.data(), N * sizeof(ulonglong2))) != PHE_OK ||
+      (st = upload((void**)&tab.fwd_0, fwd0.data(), fwd0.size() * sizeof(ulonglong2))) != PHE_OK ||
+      (st = upload((void**)&tab.inv_0, inv0.data(), inv0.size() * sizeof(ulonglong2))) != PHE_OK)
+    return st;
+  return PHE_OK;
 }
 
 phe_status upload(void** dptr, const void* host, size_t bytes) {
@@ -206,8 +266,20 @@ phe_status phe_ctx_create(const phe_params* prm, int device, phe_ctx** out) {
     return fail(PHE_EINVAL, "q=%llu must satisfy 2^53 < q < 2^61", (unsigned long long)q);
   if ((q - 1) % (2ull * N) != 0)
     return fail(PHE_EINVAL, "q=%llu is not 1 mod 2N=%u", (unsigned long long)q, 2 * N);
-  if (!is_prime(q)) return fail(PHE_EINVAL, "q=%llu is not prime", (unsigned long long)q);
+  const bool rns_modulus = prm->rns_p1 || prm->rns_p2;
+  const u32 p1 = std::min(prm->rns_p1, prm->rns_p2), p2 = std::max(prm->rns_p1, prm->rns_p2);
+  if (rns_modulus) {
+    if (!p1 || p1 == p2 || p2 >= (1u << 30) || (u64)p1 * p2 != q)
+      return fail(PHE_EINVAL, "RNS modulus: need q = p1 * p2 with distinct p1, p2 < 2^30");
+    if (!is_prime(p1) || !is_prime(p2)) return fail(PHE_EINVAL, "RNS modulus: p1 and p2 must be prime");
+    if ((p1 - 1) % (2u * N) != 0 || (p2 - 1) % (2u * N) != 0)
+      return fail(PHE_EINVAL, "RNS modulus: p1 and p2 must be 1 mod 2N=%u", 2 * N);
+  } else if (!is_prime(q)) {
+    return fail(PHE_EINVAL, "q=%llu is not prime (give rns_p1, rns_p2 for an RNS modulus)",
+                (unsigned long long)q);
+  }
   if (prm->log2_qout < 1 || prm->log2_qout > 32) return fail(PHE_EINVAL, "log2_qout=%u not in [1, 32]", prm->log2_qout);
+  if (prm->flags & ~PHE_CTX_FORCE_U64) return fail(PHE_EINVAL, "flags=%u", prm->flags);
 
   int ndev = 0;
   cudaError_t e = cudaGetDeviceCount(&ndev);
@@ -237,39 +309,58 @@ phe_status phe_ctx_create(const phe_params* prm, int device, phe_ctx** out) {
   rc.c64 = (u64)(((u128)1 << 64) % q);
   rc.c64p = shoup(rc.c64, q);
   rc.log2_qout = prm->log2_qout;
-  c->n_inv = powmod(N, q - 2, q);
+  c->n_inv = modinv(N, q);
   c->n_inv_p = shoup(c->n_inv, q);
+  c->ninv.n64 = c->n_inv;
+  c->ninv.n64p = c->n_inv_p;
 
-  const u64 psi = primitive_root_2n(q, N);
+  // Primitive 2N-th root of unity mod q: directly for a prime q; for q = p1 p2
+  // the CRT combination of the two primes' roots (its order is 2N in both).
+  u64 psi = 0;
+  u32 psi1 = 0, psi2 = 0;
+  if (rns_modulus) {
+    psi1 = (u32)primitive_root_2n(p1, N);
+    psi2 = (u32)primitive_root_2n(p2, N);
+    if (!psi1 || !psi2) { delete c; return fail(PHE_EINVAL, "no primitive 2N-th root of unity mod p1 or p2"); }
+    psi = crt2(psi1, p1, psi2, p2);
+  } else {
+    psi = primitive_root_2n(q, N);
+  }
   if (!psi) { delete c; return fail(PHE_EINVAL, "no primitive 2N-th root of unity found for q"); }
-  const u64 psi_inv = powmod(psi, q - 2, q);
-  const int logn = c->logn;
-  std::vector<ulonglong2> fwd(N), inv(N);
-  for (u32 k = 0; k < N; ++k) {
-    const u32 br = bitrev(k, logn);
-    const u64 a = powmod(psi, br, q), b = powmod(psi_inv, br, q);
-    fwd[k] = make_ulonglong2(a, shoup(a, q));
-    inv[k] = make_ulonglong2(b, shoup(b, q));
+
+  phe_status st = build_tables(c, [&](u32 br, bool inverse) -> ulonglong2 {
+    const u64 root = inverse ? modinv(psi, q) : psi;
+    const u64 a = powmod(root, br, q);
+    return make_ulonglong2(a, shoup(a, q));
+  }, c->tab);
+  if (st == PHE_OK && rns_modulus) {
+    phe::RnsConst& k = c->rk;
+    k.p1 = p1;
+    k.p2 = p2;
+    k.inv = (u32)modinv(p1 % p2, p2);
+    k.invp = shoup32(k.inv, p2);
+    k.c32a = (u32)((1ull << 32) % p1);
+    k.c32ap = shoup32(k.c32a, p1);
+    k.c32b = (u32)((1ull << 32) % p2);
+    k.c32bp = shoup32(k.c32b, p2);
+    c->ninv.n1 = (u32)modinv(N, p1);
+    c->ninv.n1p = shoup32(c->ninv.n1, p1);
+    c->ninv.n2 = (u32)modinv(N, p2);
+    c->ninv.n2p = shoup32(c->ninv.n2, p2);
+    const u64 i1 = modinv(psi1, p1), i2 = modinv(psi2, p2);
+    st = build_tables(c, [&](u32 br, bool inverse) -> ulonglong2 {
+      const u32 a = (u32)powmod(inverse ? i1 : psi1, br, p1);
+      const u32 b = (u32)powmod(inverse ? i2 : psi2, br, p2);
+      // (w1, w1', w2, w2') packed as two 64-bit words: bytes of a uint4
+      const u64 lo = (u64)a | ((u64)shoup32(a, p1) << 32);
+      const u64 hi = (u64)b | ((u64)shoup32(b, p2) << 32);
+      return make_ulonglong2(lo, hi);
+    }, c->tab32);
+    c->rns = !(prm->flags & PHE_CTX_FORCE_U64);
   }
-  // Pass-0 twiddles in thread-major order: slot (st, b) of thread p is the
-  // twiddle of stage st for butterfly group b of positions [16p, 16p+16).
-  const u32 P = N / 16;
-  std::vector<ulonglong2> fwd0(15 * P), inv0(15 * P);
-  for (int st = 0; st < 4; ++st) {
-    for (int b = 0; b < (8 >> st); ++b) {
-      for (u32 p = 0; p < P; ++p) {
-        const u32 idx = (N >> (st + 1)) + ((16 * p) >> (st + 1)) + b;
-        fwd0[phe::pass0_slot(st, b) * P + p] = fwd[idx];
-        inv0[phe::pass0_slot(st, b) * P + p] = inv[idx];
-      }
-    }
-  }
-  phe_status st;
-  if ((st = upload((void**)&c->tab.fwd_c, fwd.data(), N * sizeof(ulonglong2))) != PHE_OK ||
-      (st = upload((void**)&c->tab.inv_c, inv.data(), N * sizeof(ulonglong2))) != PHE_OK ||
-      (st = upload((void**)&c->tab.fwd_0, fwd0.data(), fwd0.size() * sizeof(ulonglong2))) != PHE_OK ||
-      (st = upload((void**)&c->tab.inv_0, inv0.data(), inv0.size() * sizeof(ulonglong2))) != PHE_OK) {
+  if (st != PHE_OK) {
     free_tables(c->tab);
+    free_tables(c->tab32);
     delete c;
     return st;
   }
@@ -289,6 +380,7 @@ void phe_ctx_destroy(phe_ctx* c) {
   }
   for (auto e : c->tracer.pool) cudaEventDestroy(e);
   free_tables(c->tab);
+  free_tables(c->tab32);
   delete c;
 }
 
@@ -557,9 +649,9 @@ phe_status phe_client_encrypt(phe_ctx* c, uint32_t T, uint32_t d, const uint64_t
   e = cudaMallocAsync((void**)&shat, (size_t)N * sizeof(ulonglong2), s);
   if (e == cudaSuccess) {
     phe::NttJob nj{reinterpret_cast<const u64*>(d_A), ahat, blocks};
-    e = phe::launch_input_ntt(c, &nj, 1, s);
+    e = phe::launch_input_ntt(c, &nj, 1, s, /*force64=*/true);
   }
-  if (e == cudaSuccess) e = phe::launch_weight_ntt(c, d_S, 1, N, 0, 1, 1, 0, shat, s);
+  if (e == cudaSuccess) e = phe::launch_weight_ntt(c, d_S, 1, N, 0, 1, 1, 0, shat, s, /*force64=*/true);
   if (e == cudaSuccess) {
     phe::LweJobTable jt{};
     jt.n = 1;
@@ -578,7 +670,7 @@ phe_status phe_client_encrypt(phe_ctx* c, uint32_t T, uint32_t d, const uint64_t
     J.msg_d = d;
     J.tiles = (blocks + 15) / 16;
     jt.prefix[1] = J.tiles;
-    e = phe::launch_lwedot(c, jt, phe::kOutRing, 0, s);
+    e = phe::launch_lwedot(c, jt, phe::kOutRing, 0, s, /*force64=*/true);
   }
   if (shat) cudaFreeAsync(shat, s);
   cudaFreeAsync(ahat, s);

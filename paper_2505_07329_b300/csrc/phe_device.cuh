@@ -93,6 +93,75 @@ __device__ __forceinline__ u64 reduce_word(u64 c, const RingConst& rc) {
   return (r >= rc.q) ? r - rc.q : r;
 }
 
+// ---------------------------------------------------------------------------
+// 32-bit residue arithmetic for an RNS modulus q = p1 p2 (p_i < 2^30): the
+// same Shoup / Harvey forms on 32-bit words, values kept in [0, 2p) or [0, 4p).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ u32 mul_shoup32(u32 x, u32 w, u32 wp, u32 p) {
+  return x * w - __umulhi(wp, x) * p;  // [0, 2p) for any 32-bit x
+}
+__device__ __forceinline__ u32 sub_if32(u32 x, u32 m) { return min(x, x - m); }  // x < 2m -> [0, m)
+__device__ __forceinline__ void gs_bfly32(u32& X, u32& Y, u32 w, u32 wp, u32 p, u32 p2) {
+  const u32 s = sub_if32(X + Y, p2);
+  const u32 d = X - Y + p2;
+  Y = mul_shoup32(d, w, wp, p);
+  X = s;
+}
+__device__ __forceinline__ void ct_bfly32(u32& X, u32& Y, u32 w, u32 wp, u32 p, u32 p2) {
+  const u32 x = sub_if32(X, p2);
+  const u32 t = mul_shoup32(Y, w, wp, p);
+  X = x + t;
+  Y = x - t + p2;
+}
+
+// Constants of the RNS modulus q = p1 p2 (p1 < p2 < 2^30, both = 1 mod 2N).
+struct RnsConst {
+  u32 p1, p2;
+  u32 inv, invp;      // p1^-1 mod p2 and its Shoup quotient (CRT)
+  u32 c32a, c32ap;    // 2^32 mod p1 and its Shoup quotient
+  u32 c32b, c32bp;    // 2^32 mod p2 and its Shoup quotient
+};
+
+// A word of [0, 2^61) to its residues (mod p1, mod p2).
+__device__ __forceinline__ uint2 to_residues(u64 a, const RnsConst& k) {
+  const u32 hi = (u32)(a >> 32), lo = (u32)a;  // hi < 2^29 < p_i
+  const u32 r1 = sub_if32(sub_if32(lo, 2 * k.p1), k.p1);
+  const u32 r2 = sub_if32(sub_if32(lo, 2 * k.p2), k.p2);
+  const u32 h1 = sub_if32(mul_shoup32(hi, k.c32a, k.c32ap, k.p1), k.p1);
+  const u32 h2 = sub_if32(mul_shoup32(hi, k.c32b, k.c32bp, k.p2), k.p2);
+  return make_uint2(sub_if32(h1 + r1, k.p1), sub_if32(h2 + r2, k.p2));
+}
+
+// CRT: the unique c in [0, p1 p2) with c = c1 (mod p1), c = c2 (mod p2),
+// for c1 in [0, p1), c2 in [0, p2): c = c1 + p1 ((c2 - c1) p1^-1 mod p2).
+__device__ __forceinline__ u64 from_residues(u32 c1, u32 c2, const RnsConst& k) {
+  const u32 d = sub_if32(c2 + k.p2 - c1, k.p2);  // c1 < p1 < p2
+  const u32 h = sub_if32(mul_shoup32(d, k.inv, k.invp, k.p2), k.p2);
+  return (u64)c1 + (u64)k.p1 * h;
+}
+
+// Arithmetic policies of the NTT passes.
+struct Ring64 {
+  using Word = u64;
+  using Tw = ulonglong2;  // (w, floor(w 2^64 / q))
+  u64 q, qb;              // qb: butterfly bound (2q forward, 4q inverse)
+  __device__ __forceinline__ void gs(Word& X, Word& Y, const Tw& w) const { gs_bfly(X, Y, w.x, w.y, q, qb); }
+  __device__ __forceinline__ void ct(Word& X, Word& Y, const Tw& w) const { ct_bfly(X, Y, w.x, w.y, q, qb); }
+};
+struct Ring2x32 {
+  using Word = uint2;     // (residue mod p1, residue mod p2)
+  using Tw = uint4;       // (w1, w1', w2, w2') with w' = floor(w 2^32 / p)
+  u32 p1, p2;
+  __device__ __forceinline__ void gs(Word& X, Word& Y, const Tw& w) const {
+    gs_bfly32(X.x, Y.x, w.x, w.y, p1, 2 * p1);
+    gs_bfly32(X.y, Y.y, w.z, w.w, p2, 2 * p2);
+  }
+  __device__ __forceinline__ void ct(Word& X, Word& Y, const Tw& w) const {
+    ct_bfly32(X.x, Y.x, w.x, w.y, p1, 2 * p1);
+    ct_bfly32(X.y, Y.y, w.z, w.w, p2, 2 * p2);
+  }
+};
+
 // ModulusSwitch q -> 2^k of c in [0, q):
 //   floor((c 2^k + floor(q/2)) / q) mod 2^k   (round half up).
 // X = c 2^k + floor(q/2) < 2^(s+1+k).  With x' = floor(X / 2^s) < 2^(k+1) and
@@ -219,10 +288,9 @@ __device__ __forceinline__ void static_for(F&& f) {
 
 // One stage of a pass: stage ST of pass PASS (ST counted inside the pass).
 // Every twiddle is loaded once and applied to the 2^ST butterflies sharing it.
-// qb is the butterfly's bound: 2q for the forward, 4q for the inverse form.
-template <int LOGN, int PASS, int ST, bool INVERSE>
-__device__ __forceinline__ void pass_stage(u64 (&x)[16], int p, const ulonglong2* __restrict__ tw0,
-                                           const ulonglong2* __restrict__ twc, u64 q, u64 qb) {
+template <int LOGN, int PASS, int ST, bool INVERSE, class R>
+__device__ __forceinline__ void pass_stage(typename R::Word (&x)[16], int p, const typename R::Tw* __restrict__ tw0,
+                                           const typename R::Tw* __restrict__ twc, const R& ring) {
   using PS = PassShape<LOGN, PASS>;
   constexpr int N = Shape<LOGN>::N;
   constexpr int P = Shape<LOGN>::P;
@@ -233,7 +301,7 @@ __device__ __forceinline__ void pass_stage(u64 (&x)[16], int p, const ulonglong2
   for (int u = 0; u < PS::U; ++u) {
 #pragma unroll
     for (int b = 0; b < NB; ++b) {
-      ulonglong2 w;
+      typename R::Tw w;
       if constexpr (PASS == 0) {
         w = __ldg(&tw0[pass0_slot(ST, b) * P + p]);
       } else {
@@ -243,37 +311,37 @@ __device__ __forceinline__ void pass_stage(u64 (&x)[16], int p, const ulonglong2
 #pragma unroll
       for (int c = 0; c < h; ++c) {
         const int e0 = u * PS::G + b * 2 * h + c;
-        if constexpr (INVERSE) gs_bfly(x[e0], x[e0 + h], w.x, w.y, q, qb);
-        else ct_bfly(x[e0], x[e0 + h], w.x, w.y, q, qb);
+        if constexpr (INVERSE) ring.gs(x[e0], x[e0 + h], w);
+        else ring.ct(x[e0], x[e0 + h], w);
       }
     }
   }
 }
 
-// Inverse (Gentleman-Sande) pass: stages S0 .. S0+K-1 ascending; q4 = 4q.
+// Inverse (Gentleman-Sande) pass: stages S0 .. S0+K-1 ascending.
 // tw0: pass-0 table, thread-major [15][P]; twc: compact table [N].
-template <int LOGN, int PASS>
-__device__ __forceinline__ void gs_pass(u64 (&x)[16], int p, const ulonglong2* __restrict__ tw0,
-                                        const ulonglong2* __restrict__ twc, u64 q, u64 q4) {
+template <int LOGN, int PASS, class R>
+__device__ __forceinline__ void gs_pass(typename R::Word (&x)[16], int p, const typename R::Tw* __restrict__ tw0,
+                                        const typename R::Tw* __restrict__ twc, const R& ring) {
   static_for<0, PassShape<LOGN, PASS>::K>([&](auto st) {
-    pass_stage<LOGN, PASS, decltype(st)::value, true>(x, p, tw0, twc, q, q4);
+    pass_stage<LOGN, PASS, decltype(st)::value, true>(x, p, tw0, twc, ring);
   });
 }
 
 // Forward (Cooley-Tukey) pass: stages S0+K-1 .. S0 descending.
-template <int LOGN, int PASS>
-__device__ __forceinline__ void ct_pass(u64 (&x)[16], int p, const ulonglong2* __restrict__ tw0,
-                                        const ulonglong2* __restrict__ twc, u64 q, u64 q2) {
+template <int LOGN, int PASS, class R>
+__device__ __forceinline__ void ct_pass(typename R::Word (&x)[16], int p, const typename R::Tw* __restrict__ tw0,
+                                        const typename R::Tw* __restrict__ twc, const R& ring) {
   constexpr int K = PassShape<LOGN, PASS>::K;
   static_for<0, K>([&](auto i) {
-    pass_stage<LOGN, PASS, K - 1 - decltype(i)::value, false>(x, p, tw0, twc, q, q2);
+    pass_stage<LOGN, PASS, K - 1 - decltype(i)::value, false>(x, p, tw0, twc, ring);
   });
 }
 
 // Move the 16 words of every thread from pass A's positions to pass B's.
 // Two barriers: the buffer is reused by the next exchange.
-template <int LOGN, int PA, int PB>
-__device__ __forceinline__ void exchange(u64 (&x)[16], int p, u64* __restrict__ buf) {
+template <int LOGN, int PA, int PB, class W>
+__device__ __forceinline__ void exchange(W (&x)[16], int p, W* __restrict__ buf) {
 #pragma unroll
   for (int e = 0; e < 16; ++e) buf[pad_idx(pass_pos<LOGN, PA>(p, e))] = x[e];
   __syncthreads();
@@ -283,44 +351,45 @@ __device__ __forceinline__ void exchange(u64 (&x)[16], int p, u64* __restrict__ 
 }
 
 // Full inverse transform (no N^-1 scaling): bit-reversed in (pass-0 layout),
-// natural order out (last-pass layout).  Values in [0, 4q) in and out.
-template <int LOGN>
-__device__ __forceinline__ void intt_regs(u64 (&x)[16], int p, u64* buf, const ulonglong2* tw0,
-                                          const ulonglong2* twc, u64 q, u64 q4) {
-  gs_pass<LOGN, 0>(x, p, tw0, twc, q, q4);
+// natural order out (last-pass layout).  Values stay within the policy's
+// inverse bound ([0, 4q) for Ring64, [0, 2p) for Ring2x32).
+template <int LOGN, class R>
+__device__ __forceinline__ void intt_regs(typename R::Word (&x)[16], int p, typename R::Word* buf,
+                                          const typename R::Tw* tw0, const typename R::Tw* twc, const R& ring) {
+  gs_pass<LOGN, 0>(x, p, tw0, twc, ring);
   if constexpr (Shape<LOGN>::NPASS > 1) {
     exchange<LOGN, 0, 1>(x, p, buf);
-    gs_pass<LOGN, 1>(x, p, tw0, twc, q, q4);
+    gs_pass<LOGN, 1>(x, p, tw0, twc, ring);
   }
   if constexpr (Shape<LOGN>::NPASS > 2) {
     exchange<LOGN, 1, 2>(x, p, buf);
-    gs_pass<LOGN, 2>(x, p, tw0, twc, q, q4);
+    gs_pass<LOGN, 2>(x, p, tw0, twc, ring);
   }
   if constexpr (Shape<LOGN>::NPASS > 3) {
     exchange<LOGN, 2, 3>(x, p, buf);
-    gs_pass<LOGN, 3>(x, p, tw0, twc, q, q4);
+    gs_pass<LOGN, 3>(x, p, tw0, twc, ring);
   }
 }
 
 // Full forward transform: natural order in (last-pass layout), bit-reversed
-// out (pass-0 layout).  Values in [0, 4q) in and out.
-template <int LOGN>
-__device__ __forceinline__ void ntt_regs(u64 (&x)[16], int p, u64* buf, const ulonglong2* tw0,
-                                         const ulonglong2* twc, u64 q, u64 q2) {
+// out (pass-0 layout).  Values in [0, 4q) (or [0, 4p)) in and out.
+template <int LOGN, class R>
+__device__ __forceinline__ void ntt_regs(typename R::Word (&x)[16], int p, typename R::Word* buf,
+                                         const typename R::Tw* tw0, const typename R::Tw* twc, const R& ring) {
   constexpr int NP = Shape<LOGN>::NPASS;
   if constexpr (NP > 3) {
-    ct_pass<LOGN, 3>(x, p, tw0, twc, q, q2);
+    ct_pass<LOGN, 3>(x, p, tw0, twc, ring);
     exchange<LOGN, 3, 2>(x, p, buf);
   }
   if constexpr (NP > 2) {
-    ct_pass<LOGN, 2>(x, p, tw0, twc, q, q2);
+    ct_pass<LOGN, 2>(x, p, tw0, twc, ring);
     exchange<LOGN, 2, 1>(x, p, buf);
   }
   if constexpr (NP > 1) {
-    ct_pass<LOGN, 1>(x, p, tw0, twc, q, q2);
+    ct_pass<LOGN, 1>(x, p, tw0, twc, ring);
     exchange<LOGN, 1, 0>(x, p, buf);
   }
-  ct_pass<LOGN, 0>(x, p, tw0, twc, q, q2);
+  ct_pass<LOGN, 0>(x, p, tw0, twc, ring);
 }
 
 // Layout of transformed inputs (A_hat): word r of pass-0 thread p of a block

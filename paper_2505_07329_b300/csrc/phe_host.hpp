@@ -66,11 +66,19 @@ struct Tracer {
   std::vector<cudaEvent_t> pool;
 };
 
+// Twiddle tables (16 bytes per entry): (w, w') mod q for the 64-bit form,
+// (w1, w1', w2, w2') mod (p1, p2) for the RNS form.
 struct Tables {
   ulonglong2* fwd_c = nullptr;  // psi^brv(k) and Shoup quotient, [N]
   ulonglong2* inv_c = nullptr;  // psi^-brv(k) and Shoup quotient, [N]
   ulonglong2* fwd_0 = nullptr;  // pass-0 forward twiddles, thread-major [15][P]
   ulonglong2* inv_0 = nullptr;  // pass-0 inverse twiddles, thread-major [15][P]
+};
+
+// N^-1 with Shoup quotients: mod q (64-bit form) and mod p1, p2 (RNS form).
+struct NInv {
+  u64 n64, n64p;
+  u32 n1, n1p, n2, n2p;
 };
 
 }  // namespace phe
@@ -81,7 +89,11 @@ struct phe_ctx {
   int logn = 0;
   phe::RingConst rc{};
   phe::u64 n_inv = 0, n_inv_p = 0;  // N^-1 mod q and its Shoup quotient
-  phe::Tables tab;
+  phe::NInv ninv{};
+  phe::Tables tab;        // 64-bit form (every context)
+  bool rns = false;       // hot path in the RNS form (q = p1 p2)
+  phe::RnsConst rk{};
+  phe::Tables tab32;      // RNS form (RNS contexts)
   int num_sms = 0;
   cudaStream_t side[2] = {nullptr, nullptr};  // streams for overlapped host-buffer chunks
   phe::Tracer tracer;
@@ -134,10 +146,13 @@ struct Span {
 };
 
 // Launchers (phe_kernels.cu).  All asynchronous on `s`.
-cudaError_t launch_input_ntt(const phe_ctx* c, const NttJob* jobs, int n, cudaStream_t s);
+// The hot-path launchers use the context's form (RNS when c->rns) unless
+// force64 asks for the 64-bit form (client-side encryption).
+cudaError_t launch_input_ntt(const phe_ctx* c, const NttJob* jobs, int n, cudaStream_t s, bool force64 = false);
 cudaError_t launch_weight_ntt(const phe_ctx* c, const int8_t* W, u32 rows, u32 cols, u32 row_stride,
-                              u32 col_stride, u32 L, int rev, ulonglong2* what, cudaStream_t s);
-cudaError_t launch_lwedot(const phe_ctx* c, const LweJobTable& jt, int mode, int grid_limit, cudaStream_t s);
+                              u32 col_stride, u32 L, int rev, void* what, cudaStream_t s, bool force64 = false);
+cudaError_t launch_lwedot(const phe_ctx* c, const LweJobTable& jt, int mode, int grid_limit, cudaStream_t s,
+                          bool force64 = false);
 cudaError_t launch_modswitch(const phe_ctx* c, const u64* in, u32* out, size_t n, cudaStream_t s);
 cudaError_t launch_expand_masks(const phe_ctx* c, const u64* seeds, u32 n, u64* masks, cudaStream_t s);
 int lwedot_threads(int logn);

@@ -1,11 +1,18 @@
 // CUDA kernels of the hot path (sm_103a):
-//   input_ntt_kernel   forward negacyclic NTT of the input masks A_ti
+//   input_ntt_kernel   forward negacyclic NTT of the input masks A_ti (or of
+//                      masks expanded from seeds)
 //   weight_ntt_kernel  w_hat_ij (reversed weight blocks, Sec. 4.3.1) -> NTT domain, x N^-1
 //   lwedot_kernel      Eq. (LWEdot): pointwise sum over blocks, inverse NTT,
 //                      SampleExtract at N-1 (index reversal), ModulusSwitch --
 //                      one fused pass per (token, row) for the masks
 //                      and the bodies b'_tj = sum_k W[j,k] B_t[k] (mod q)
 //   modswitch_kernel   unfused ModulusSwitch
+//   expand_masks_kernel seeded masks written out
+//
+// Each transform kernel has two arithmetic forms: 64-bit words mod q (any
+// NTT-friendly q < 2^61), and -- when q = p1 p2 is a product of two 30-bit
+// NTT primes -- a pair of 32-bit residues (RNS), which halves the multiply
+// work per butterfly; the epilogue returns to q by the CRT before the switch.
 //
 // Why the inverse NTT yields SampleExtract at N-1: with P = A_i * w_hat_ij
 // in R_q, SampleExtract(., N-1) takes a'_m = P_{N-1-m} for every m (the
@@ -14,26 +21,42 @@
 // sums A_hat_ti . W_hat_ij over i in the NTT domain, runs one inverse
 // transform per (token, row) and writes coefficient N-1-m to slot m.
 #include <cstdio>
+#include <type_traits>
 
 #include "phe_host.hpp"
 
 namespace phe {
 
+template <bool RNS>
+using RingOf = std::conditional_t<RNS, Ring2x32, Ring64>;
+
+template <bool RNS>
+__device__ __forceinline__ RingOf<RNS> make_ring(const RingConst& rc, const RnsConst& rk, bool inverse) {
+  if constexpr (RNS) {
+    return Ring2x32{rk.p1, rk.p2};
+  } else {
+    return Ring64{rc.q, inverse ? rc.q4 : rc.q2};
+  }
+}
+
 // --------------------------------------------------------------------------
 // Forward transform of input masks: [blocks][N] natural -> A_hat layout.
 // --------------------------------------------------------------------------
-template <int LOGN>
+template <int LOGN, bool RNS>
 __global__ void __launch_bounds__(Shape<LOGN>::TPB)
-    input_ntt_kernel(NttJob job, RingConst rc, const ulonglong2* __restrict__ tw0,
-                     const ulonglong2* __restrict__ twc) {
+    input_ntt_kernel(NttJob job, RingConst rc, RnsConst rk, const void* __restrict__ tw0v,
+                     const void* __restrict__ twcv) {
   using S = Shape<LOGN>;
+  using R = RingOf<RNS>;
+  using W = typename R::Word;
   constexpr int NP = S::NPASS;
   extern __shared__ u64 smem[];
   const int slot = threadIdx.x / S::P, p = threadIdx.x % S::P;
-  u64* buf = smem + slot * S::PADN;
+  u64* buf64 = smem + slot * S::PADN;
+  W* buf = reinterpret_cast<W*>(buf64);
   const u32 b = blockIdx.x * S::SLOTS + slot;
   const bool active = b < job.blocks;
-  u64 x[16];
+  u64 v[16];
   if (job.seeds) {
     // Seeded mask: each thread expands 4 keystream blocks (16 coefficients)
     // into shared memory in natural order, then loads its transform words.
@@ -41,34 +64,47 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB)
 #pragma unroll 1
     for (int k = 0; k < 4; ++k) {
       const u32 cb = p + k * S::P;
-      u64 v[4];
-      seeded_mask4(seed, cb, rc, v);
+      u64 m4[4];
+      seeded_mask4(seed, cb, rc, m4);
 #pragma unroll
-      for (int c = 0; c < 4; ++c) buf[pad_idx(4 * cb + c)] = v[c];
+      for (int c = 0; c < 4; ++c) buf64[pad_idx(4 * cb + c)] = m4[c];
     }
     __syncthreads();
 #pragma unroll
-    for (int e = 0; e < 16; ++e) x[e] = buf[pad_idx(pass_pos<LOGN, NP - 1>(p, e))];
+    for (int e = 0; e < 16; ++e) v[e] = buf64[pad_idx(pass_pos<LOGN, NP - 1>(p, e))];
     __syncthreads();
   } else {
     const u64* src = job.src + (size_t)(active ? b : 0) * S::N;
 #pragma unroll
-    for (int e = 0; e < 16; ++e) x[e] = active ? reduce_word(src[pass_pos<LOGN, NP - 1>(p, e)], rc) : 0ull;
+    for (int e = 0; e < 16; ++e) v[e] = active ? reduce_word(src[pass_pos<LOGN, NP - 1>(p, e)], rc) : 0ull;
   }
-  ntt_regs<LOGN>(x, p, buf, tw0, twc, rc.q, rc.q2);
-  if (active) {
-    ulonglong2* dst = reinterpret_cast<ulonglong2*>(job.dst + (size_t)b * S::N);
+  W x[16];
 #pragma unroll
-    for (int r = 0; r < 16; r += 2) dst[(r >> 1) * S::P + p] = make_ulonglong2(x[r], x[r + 1]);
+  for (int e = 0; e < 16; ++e) {
+    if constexpr (RNS) x[e] = to_residues(v[e], rk);
+    else x[e] = v[e];
+  }
+  ntt_regs<LOGN>(x, p, buf, reinterpret_cast<const typename R::Tw*>(tw0v),
+                 reinterpret_cast<const typename R::Tw*>(twcv), make_ring<RNS>(rc, rk, false));
+  if (active) {
+    // words (r, r+1) of a thread stored together: 16 bytes, a warp covers 512
+    W* dst = reinterpret_cast<W*>(job.dst + (size_t)b * S::N);
+#pragma unroll
+    for (int r = 0; r < 16; r += 2) {
+      W* d = dst + 2 * ((r >> 1) * S::P + p);
+      d[0] = x[r];
+      d[1] = x[r + 1];
+    }
   }
 }
 
 // --------------------------------------------------------------------------
 // Weight encoding: block i of output row j holds w_hat_ij[k] = W(j, iN+N-1-k)
 // (zero past cols); W(j, k) = W[j*rs + k*cs] lets one kernel read W for the
-// forward pass and W^T for the backward pass.  Output: (N^-1 NTT(w_hat), Shoup
-// quotient) pairs, fully reduced.  rev = 0 skips the reversal (the client's
-// key polynomial in phe_client_encrypt).
+// forward pass and W^T for the backward pass.  Output: N^-1 NTT(w_hat) with
+// Shoup quotients, fully reduced: (w, w') pairs mod q, or (w1, w1', w2, w2')
+// for the RNS form.  rev = 0 skips the reversal (the client's key
+// polynomial in phe_client_encrypt).
 // --------------------------------------------------------------------------
 __device__ __forceinline__ u64 shoup_quotient(u64 w, u64 q) {
   // floor(w 2^64 / q) by restoring long division (w < q < 2^61).
@@ -85,35 +121,55 @@ __device__ __forceinline__ u64 shoup_quotient(u64 w, u64 q) {
   return quo;
 }
 
-template <int LOGN>
+template <int LOGN, bool RNS>
 __global__ void __launch_bounds__(Shape<LOGN>::TPB)
     weight_ntt_kernel(const int8_t* __restrict__ W, u32 rows, u32 cols, u32 rs, u32 cs, u32 L, int rev,
-                      ulonglong2* __restrict__ what, RingConst rc, u64 ninv, u64 ninv_p,
-                      const ulonglong2* __restrict__ tw0, const ulonglong2* __restrict__ twc) {
+                      void* __restrict__ whatv, RingConst rc, RnsConst rk, NInv ninv, const void* __restrict__ tw0v,
+                      const void* __restrict__ twcv) {
   using S = Shape<LOGN>;
+  using R = RingOf<RNS>;
+  using Wd = typename R::Word;
   constexpr int NP = S::NPASS;
   extern __shared__ u64 smem[];
   const int slot = threadIdx.x / S::P, p = threadIdx.x % S::P;
-  u64* buf = smem + slot * S::PADN;
+  Wd* buf = reinterpret_cast<Wd*>(smem + slot * S::PADN);
   const u32 b = blockIdx.x * S::SLOTS + slot;
   const bool active = b < rows * L;
   const u32 j = active ? b / L : 0, i = active ? b % L : 0;
-  u64 x[16];
+  Wd x[16];
 #pragma unroll
   for (int e = 0; e < 16; ++e) {
     const u32 pos = (u32)pass_pos<LOGN, NP - 1>(p, e);
     const u32 k = i * S::N + (rev ? (S::N - 1 - pos) : pos);
     const int w = (active && k < cols) ? (int)W[(size_t)j * rs + (size_t)k * cs] : 0;
-    x[e] = (w < 0) ? rc.q - (u64)(-w) : (u64)w;
+    if constexpr (RNS) {
+      x[e] = make_uint2((w < 0) ? rk.p1 - (u32)(-w) : (u32)w, (w < 0) ? rk.p2 - (u32)(-w) : (u32)w);
+    } else {
+      x[e] = (w < 0) ? rc.q - (u64)(-w) : (u64)w;
+    }
   }
-  ntt_regs<LOGN>(x, p, buf, tw0, twc, rc.q, rc.q2);
+  ntt_regs<LOGN>(x, p, buf, reinterpret_cast<const typename R::Tw*>(tw0v),
+                 reinterpret_cast<const typename R::Tw*>(twcv), make_ring<RNS>(rc, rk, false));
   if (active) {
-    ulonglong2* dst = what + (size_t)b * S::N;
+    if constexpr (RNS) {
+      uint4* dst = reinterpret_cast<uint4*>(whatv) + (size_t)b * S::N;
 #pragma unroll
-    for (int r = 0; r < 16; ++r) {
-      u64 v = reduce_4q(x[r], rc.q, rc.q2);
-      v = reduce_2q(mul_shoup(v, ninv, ninv_p, rc.q), rc.q);
-      dst[what_idx<LOGN>(p, r)] = make_ulonglong2(v, shoup_quotient(v, rc.q));
+      for (int r = 0; r < 16; ++r) {
+        u32 a1 = sub_if32(sub_if32(x[r].x, 2 * rk.p1), rk.p1);
+        u32 a2 = sub_if32(sub_if32(x[r].y, 2 * rk.p2), rk.p2);
+        a1 = sub_if32(mul_shoup32(a1, ninv.n1, ninv.n1p, rk.p1), rk.p1);
+        a2 = sub_if32(mul_shoup32(a2, ninv.n2, ninv.n2p, rk.p2), rk.p2);
+        dst[what_idx<LOGN>(p, r)] = make_uint4(a1, (u32)(((u64)a1 << 32) / rk.p1), a2,
+                                               (u32)(((u64)a2 << 32) / rk.p2));
+      }
+    } else {
+      ulonglong2* dst = reinterpret_cast<ulonglong2*>(whatv) + (size_t)b * S::N;
+#pragma unroll
+      for (int r = 0; r < 16; ++r) {
+        u64 v = reduce_4q(x[r], rc.q, rc.q2);
+        v = reduce_2q(mul_shoup(v, ninv.n64, ninv.n64p, rc.q), rc.q);
+        dst[what_idx<LOGN>(p, r)] = make_ulonglong2(v, shoup_quotient(v, rc.q));
+      }
     }
   }
 }
@@ -131,11 +187,39 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB)
 #ifndef PHE_LWEDOT_MIN_BLOCKS
 #define PHE_LWEDOT_MIN_BLOCKS 3
 #endif
-template <int LOGN, int MODE>
+
+// One thread's share of the body dot product of (token t, row).
+__device__ __forceinline__ void body_partial(const LweJob& J, u32 row, u32 t, int p, int P, int N,
+                                             const RingConst& rc, long long& al, long long& ah) {
+  al = ah = 0;
+  const int8_t* wr = J.wrow + (size_t)row * J.cols;
+  const u64* bt = J.bin + (size_t)t * J.L * (size_t)N;
+  for (u32 kk = p; kk < J.cols; kk += P) {
+    const u64 b = reduce_word(__ldg(&bt[kk]), rc);
+    const int w = __ldg(&wr[kk]);
+    al += (long long)w * (int)(b & 0x3fffffffull);
+    ah += (long long)w * (int)(b >> 30);
+  }
+}
+
+// The body mod q from the block-reduced partial sums.
+__device__ __forceinline__ u64 body_combine(long long ll, long long hl, const RingConst& rc) {
+  const u64 q = rc.q;
+  const u64 vh = (hl < 0) ? q - (u64)(-hl) : (u64)hl;
+  const u64 vl = (ll < 0) ? q - (u64)(-ll) : (u64)ll;
+  const u64 v = reduce_2q(mul_shoup(vh, rc.c30, rc.c30p, q), q) + vl;
+  return reduce_2q(v, q);
+}
+
+template <int LOGN, int MODE, bool RNS>
 __global__ void __launch_bounds__(Shape<LOGN>::TPB, PHE_LWEDOT_MIN_BLOCKS)
-    lwedot_kernel(const LweJobTable jt, RingConst rc, const ulonglong2* __restrict__ tw0,
-                  const ulonglong2* __restrict__ twc) {
+    lwedot_kernel(const LweJobTable jt, RingConst rc, RnsConst rk, const void* __restrict__ tw0v,
+                  const void* __restrict__ twcv) {
+  static_assert(!(RNS && MODE == kOutRing), "client encryption runs in the 64-bit form");
   using S = Shape<LOGN>;
+  using R = RingOf<RNS>;
+  using W = typename R::Word;
+  using Tw = typename R::Tw;
   constexpr int N = S::N;
   constexpr int P = S::P;
   constexpr int NP = S::NPASS;
@@ -145,7 +229,10 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, PHE_LWEDOT_MIN_BLOCKS)
   extern __shared__ u64 smem[];
   __shared__ long long red[2][S::SLOTS][NGRP][2];
   const int slot = threadIdx.x / P, p = threadIdx.x % P;
-  u64* buf = smem + slot * S::PADN;
+  W* buf = reinterpret_cast<W*>(smem + slot * S::PADN);
+  const Tw* tw0 = reinterpret_cast<const Tw*>(tw0v);
+  const Tw* twc = reinterpret_cast<const Tw*>(twcv);
+  const R ring = make_ring<RNS>(rc, rk, true);
   const u64 q = rc.q, q4 = rc.q4;
   const u32 total = jt.prefix[jt.n];
   u32 seq = 0;
@@ -158,45 +245,53 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, PHE_LWEDOT_MIN_BLOCKS)
     const u32 row = local % J.rows;
     const u32 t0 = (local / J.rows) * J.tok_chunk;
     const u32 t1 = min(J.T, t0 + J.tok_chunk);
-    const ulonglong2* wrow = J.what + (size_t)row * J.L * N;
+    const Tw* wrow = reinterpret_cast<const Tw*>(J.what) + (size_t)row * J.L * N;
     const u32 iters = (t1 - t0 + S::SLOTS - 1) / S::SLOTS;
 
     for (u32 it = 0; it < iters; ++it, ++seq) {
       const u32 t = t0 + it * S::SLOTS + slot;
       const bool active = t < t1;
       const int par = seq & 1;
-      u64 x[16];
+      W x[16];
 #pragma unroll
-      for (int r = 0; r < 16; ++r) x[r] = 0;
+      for (int r = 0; r < 16; ++r) {
+        if constexpr (RNS) x[r] = make_uint2(0u, 0u);
+        else x[r] = 0;
+      }
       if (active) {
         const u64* at = J.ahat + (size_t)t * J.L * N;
         for (u32 i = 0; i < J.L; ++i) {
-          const ulonglong2* ap = reinterpret_cast<const ulonglong2*>(at + (size_t)i * N);
-          const ulonglong2* wp = wrow + (size_t)i * N;
+          const Tw* wp = wrow + (size_t)i * N;
+          if constexpr (RNS) {
+            const uint4* ap = reinterpret_cast<const uint4*>(at + (size_t)i * N);
 #pragma unroll
-          for (int r = 0; r < 16; r += 2) {
-            const ulonglong2 av = __ldg(&ap[(r >> 1) * P + p]);
-            const ulonglong2 w0 = __ldg(&wp[what_idx<LOGN>(p, r)]);
-            const ulonglong2 w1 = __ldg(&wp[what_idx<LOGN>(p, r + 1)]);
-            const u64 s0 = x[r] + mul_shoup_lazy(av.x, w0.x, w0.y, q);
-            const u64 s1 = x[r + 1] + mul_shoup_lazy(av.y, w1.x, w1.y, q);
-            x[r] = (s0 >= q4) ? s0 - q4 : s0;
-            x[r + 1] = (s1 >= q4) ? s1 - q4 : s1;
+            for (int r = 0; r < 16; r += 2) {
+              const uint4 av = __ldg(&ap[(r >> 1) * P + p]);  // (a1_r, a2_r, a1_r+1, a2_r+1)
+              const uint4 w0 = __ldg(&wp[what_idx<LOGN>(p, r)]);
+              const uint4 w1 = __ldg(&wp[what_idx<LOGN>(p, r + 1)]);
+              x[r].x = sub_if32(x[r].x + mul_shoup32(av.x, w0.x, w0.y, rk.p1), 2 * rk.p1);
+              x[r].y = sub_if32(x[r].y + mul_shoup32(av.y, w0.z, w0.w, rk.p2), 2 * rk.p2);
+              x[r + 1].x = sub_if32(x[r + 1].x + mul_shoup32(av.z, w1.x, w1.y, rk.p1), 2 * rk.p1);
+              x[r + 1].y = sub_if32(x[r + 1].y + mul_shoup32(av.w, w1.z, w1.w, rk.p2), 2 * rk.p2);
+            }
+          } else {
+            const ulonglong2* ap = reinterpret_cast<const ulonglong2*>(at + (size_t)i * N);
+#pragma unroll
+            for (int r = 0; r < 16; r += 2) {
+              const ulonglong2 av = __ldg(&ap[(r >> 1) * P + p]);
+              const ulonglong2 w0 = __ldg(&wp[what_idx<LOGN>(p, r)]);
+              const ulonglong2 w1 = __ldg(&wp[what_idx<LOGN>(p, r + 1)]);
+              const u64 s0 = x[r] + mul_shoup_lazy(av.x, w0.x, w0.y, q);
+              const u64 s1 = x[r + 1] + mul_shoup_lazy(av.y, w1.x, w1.y, q);
+              x[r] = (s0 >= q4) ? s0 - q4 : s0;
+              x[r + 1] = (s1 >= q4) ? s1 - q4 : s1;
+            }
           }
         }
       }
       if constexpr (BODY) {
         long long al = 0, ah = 0;
-        if (active) {
-          const int8_t* wr = J.wrow + (size_t)row * J.cols;
-          const u64* bt = J.bin + (size_t)t * J.L * N;
-          for (u32 kk = p; kk < J.cols; kk += P) {
-            const u64 b = reduce_word(__ldg(&bt[kk]), rc);
-            const int w = __ldg(&wr[kk]);
-            al += (long long)w * (int)(b & 0x3fffffffull);
-            ah += (long long)w * (int)(b >> 30);
-          }
-        }
+        if (active) body_partial(J, row, t, p, P, N, rc, al, ah);
 #pragma unroll
         for (int off = GW / 2; off > 0; off >>= 1) {
           al += __shfl_xor_sync(0xffffffffu, al, off, GW);
@@ -207,23 +302,20 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, PHE_LWEDOT_MIN_BLOCKS)
           red[par][slot][p / GW][1] = ah;
         }
       }
-      intt_regs<LOGN>(x, p, buf, tw0, twc, q, q4);  // barriers inside also order red[]
+      intt_regs<LOGN>(x, p, buf, tw0, twc, ring);  // barriers inside also order red[]
       if (active) {
-        if constexpr (MODE == kOutSwitched) {
-          uint32_t* out = reinterpret_cast<uint32_t*>(J.out) + ((size_t)t * J.rows + row) * N;
+        if constexpr (MODE == kOutSwitched || MODE == kOutRaw) {
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
             const int pos = pass_pos<LOGN, NP - 1>(p, e);
-            out[N - 1 - pos] = modswitch_word(reduce_4q(x[e], q, rc.q2), rc);
+            u64 c;
+            if constexpr (RNS) c = from_residues(sub_if32(x[e].x, rk.p1), sub_if32(x[e].y, rk.p2), rk);
+            else c = reduce_4q(x[e], q, rc.q2);
+            const size_t o = ((size_t)t * J.rows + row) * N + (N - 1 - pos);
+            if constexpr (MODE == kOutSwitched) reinterpret_cast<uint32_t*>(J.out)[o] = modswitch_word(c, rc);
+            else reinterpret_cast<u64*>(J.out)[o] = c;
           }
-        } else if constexpr (MODE == kOutRaw) {
-          u64* out = reinterpret_cast<u64*>(J.out) + ((size_t)t * J.rows + row) * N;
-#pragma unroll
-          for (int e = 0; e < 16; ++e) {
-            const int pos = pass_pos<LOGN, NP - 1>(p, e);
-            out[N - 1 - pos] = reduce_4q(x[e], q, rc.q2);
-          }
-        } else {
+        } else if constexpr (!RNS) {
           // Ring product in natural order plus E + delta * x_hat: client-side
           // RLWE encryption (one row: the key); `t` runs over token blocks.
           const u32 Le = (J.msg_d + N - 1) / N;
@@ -251,10 +343,7 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, PHE_LWEDOT_MIN_BLOCKS)
               ll += red[par][slot][g][0];
               hl += red[par][slot][g][1];
             }
-            const u64 vh = (hl < 0) ? q - (u64)(-hl) : (u64)hl;
-            const u64 vl = (ll < 0) ? q - (u64)(-ll) : (u64)ll;
-            u64 v = reduce_2q(mul_shoup(vh, rc.c30, rc.c30p, q), q) + vl;
-            v = reduce_2q(v, q);
+            const u64 v = body_combine(ll, hl, rc);
             if constexpr (MODE == kOutSwitched)
               reinterpret_cast<uint32_t*>(J.out_body)[(size_t)t * J.rows + row] = modswitch_word(v, rc);
             else
@@ -303,120 +392,130 @@ static cudaError_t set_smem(F* f, size_t bytes) {
   return cudaFuncSetAttribute(f, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
 }
 
-template <int LOGN>
-static cudaError_t input_ntt_impl(const phe_ctx* c, const NttJob& job, cudaStream_t s) {
-  using S = Shape<LOGN>;
-  const size_t smem = (size_t)S::SLOTS * S::PADN * sizeof(u64);
-  cudaError_t e = set_smem(input_ntt_kernel<LOGN>, smem);
-  if (e != cudaSuccess) return e;
-  const u32 grid = (job.blocks + S::SLOTS - 1) / S::SLOTS;
-  input_ntt_kernel<LOGN><<<grid, S::TPB, smem, s>>>(job, c->rc, c->tab.fwd_0, c->tab.fwd_c);
-  return cudaGetLastError();
+static const void* tw0_of(const phe_ctx* c, bool rns, bool inverse) {
+  const Tables& t = rns ? c->tab32 : c->tab;
+  return inverse ? (const void*)t.inv_0 : (const void*)t.fwd_0;
+}
+static const void* twc_of(const phe_ctx* c, bool rns, bool inverse) {
+  const Tables& t = rns ? c->tab32 : c->tab;
+  return inverse ? (const void*)t.inv_c : (const void*)t.fwd_c;
 }
 
-cudaError_t launch_input_ntt(const phe_ctx* c, const NttJob* jobs, int n, cudaStream_t s) {
+// Calls f(integral_constant<int, LOGN>) for the context's ring degree.
+template <class F>
+static cudaError_t by_logn(int logn, F&& f) {
+  switch (logn) {
+    case 8: return f(std::integral_constant<int, 8>{});
+    case 9: return f(std::integral_constant<int, 9>{});
+    case 10: return f(std::integral_constant<int, 10>{});
+    case 11: return f(std::integral_constant<int, 11>{});
+    case 12: return f(std::integral_constant<int, 12>{});
+    case 13: return f(std::integral_constant<int, 13>{});
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+cudaError_t launch_input_ntt(const phe_ctx* c, const NttJob* jobs, int n, cudaStream_t s, bool force64) {
+  const bool rns = c->rns && !force64;
   for (int i = 0; i < n; ++i) {
     if (jobs[i].blocks == 0) continue;
-    cudaError_t e;
-    switch (c->logn) {
-      case 8: e = input_ntt_impl<8>(c, jobs[i], s); break;
-      case 9: e = input_ntt_impl<9>(c, jobs[i], s); break;
-      case 10: e = input_ntt_impl<10>(c, jobs[i], s); break;
-      case 11: e = input_ntt_impl<11>(c, jobs[i], s); break;
-      case 12: e = input_ntt_impl<12>(c, jobs[i], s); break;
-      case 13: e = input_ntt_impl<13>(c, jobs[i], s); break;
-      default: return cudaErrorInvalidValue;
-    }
+    const NttJob job = jobs[i];
+    cudaError_t e = by_logn(c->logn, [&](auto lg) -> cudaError_t {
+      constexpr int LOGN = decltype(lg)::value;
+      using S = Shape<LOGN>;
+      const size_t smem = (size_t)S::SLOTS * S::PADN * sizeof(u64);
+      const u32 grid = (job.blocks + S::SLOTS - 1) / S::SLOTS;
+      if (rns) {
+        cudaError_t e2 = set_smem(input_ntt_kernel<LOGN, true>, smem);
+        if (e2 != cudaSuccess) return e2;
+        input_ntt_kernel<LOGN, true><<<grid, S::TPB, smem, s>>>(job, c->rc, c->rk, tw0_of(c, true, false),
+                                                                twc_of(c, true, false));
+      } else {
+        cudaError_t e2 = set_smem(input_ntt_kernel<LOGN, false>, smem);
+        if (e2 != cudaSuccess) return e2;
+        input_ntt_kernel<LOGN, false><<<grid, S::TPB, smem, s>>>(job, c->rc, c->rk, tw0_of(c, false, false),
+                                                                 twc_of(c, false, false));
+      }
+      return cudaGetLastError();
+    });
     if (e != cudaSuccess) return e;
   }
   return cudaSuccess;
 }
 
-template <int LOGN>
-static cudaError_t weight_ntt_impl(const phe_ctx* c, const int8_t* W, u32 rows, u32 cols, u32 rs, u32 cs, u32 L,
-                                   int rev, ulonglong2* what, cudaStream_t s) {
-  using S = Shape<LOGN>;
-  const size_t smem = (size_t)S::SLOTS * S::PADN * sizeof(u64);
-  cudaError_t e = set_smem(weight_ntt_kernel<LOGN>, smem);
-  if (e != cudaSuccess) return e;
-  const u32 blocks = rows * L;
-  const u32 grid = (blocks + S::SLOTS - 1) / S::SLOTS;
-  weight_ntt_kernel<LOGN><<<grid, S::TPB, smem, s>>>(W, rows, cols, rs, cs, L, rev, what, c->rc, c->n_inv, c->n_inv_p,
-                                                     c->tab.fwd_0, c->tab.fwd_c);
-  return cudaGetLastError();
-}
-
 cudaError_t launch_weight_ntt(const phe_ctx* c, const int8_t* W, u32 rows, u32 cols, u32 rs, u32 cs, u32 L,
-                              int rev, ulonglong2* what, cudaStream_t s) {
-  switch (c->logn) {
-    case 8: return weight_ntt_impl<8>(c, W, rows, cols, rs, cs, L, rev, what, s);
-    case 9: return weight_ntt_impl<9>(c, W, rows, cols, rs, cs, L, rev, what, s);
-    case 10: return weight_ntt_impl<10>(c, W, rows, cols, rs, cs, L, rev, what, s);
-    case 11: return weight_ntt_impl<11>(c, W, rows, cols, rs, cs, L, rev, what, s);
-    case 12: return weight_ntt_impl<12>(c, W, rows, cols, rs, cs, L, rev, what, s);
-    case 13: return weight_ntt_impl<13>(c, W, rows, cols, rs, cs, L, rev, what, s);
-    default: return cudaErrorInvalidValue;
-  }
+                              int rev, void* what, cudaStream_t s, bool force64) {
+  const bool rns = c->rns && !force64;
+  return by_logn(c->logn, [&](auto lg) -> cudaError_t {
+    constexpr int LOGN = decltype(lg)::value;
+    using S = Shape<LOGN>;
+    const size_t smem = (size_t)S::SLOTS * S::PADN * sizeof(u64);
+    const u32 grid = (rows * L + S::SLOTS - 1) / S::SLOTS;
+    if (rns) {
+      cudaError_t e = set_smem(weight_ntt_kernel<LOGN, true>, smem);
+      if (e != cudaSuccess) return e;
+      weight_ntt_kernel<LOGN, true><<<grid, S::TPB, smem, s>>>(W, rows, cols, rs, cs, L, rev, what, c->rc, c->rk,
+                                                               c->ninv, tw0_of(c, true, false),
+                                                               twc_of(c, true, false));
+    } else {
+      cudaError_t e = set_smem(weight_ntt_kernel<LOGN, false>, smem);
+      if (e != cudaSuccess) return e;
+      weight_ntt_kernel<LOGN, false><<<grid, S::TPB, smem, s>>>(W, rows, cols, rs, cs, L, rev, what, c->rc, c->rk,
+                                                                c->ninv, tw0_of(c, false, false),
+                                                                twc_of(c, false, false));
+    }
+    return cudaGetLastError();
+  });
 }
 
-template <int LOGN, int MODE>
+template <int LOGN, int MODE, bool RNS>
 static cudaError_t lwedot_impl(const phe_ctx* c, const LweJobTable& jt, int grid_limit, cudaStream_t s) {
   using S = Shape<LOGN>;
   const size_t smem = (size_t)S::SLOTS * S::PADN * sizeof(u64);
-  cudaError_t e = set_smem(lwedot_kernel<LOGN, MODE>, smem);
+  cudaError_t e = set_smem(lwedot_kernel<LOGN, MODE, RNS>, smem);
   if (e != cudaSuccess) return e;
   const u32 total = jt.prefix[jt.n];
   if (total == 0) return cudaSuccess;
   u32 grid = total;
   if (grid_limit > 0 && grid > (u32)grid_limit) grid = (u32)grid_limit;
-  lwedot_kernel<LOGN, MODE><<<grid, S::TPB, smem, s>>>(jt, c->rc, c->tab.inv_0, c->tab.inv_c);
+  lwedot_kernel<LOGN, MODE, RNS><<<grid, S::TPB, smem, s>>>(jt, c->rc, c->rk, tw0_of(c, RNS, true),
+                                                            twc_of(c, RNS, true));
   return cudaGetLastError();
 }
 
-template <int LOGN>
-static cudaError_t lwedot_mode(const phe_ctx* c, const LweJobTable& jt, int mode, int grid_limit, cudaStream_t s) {
-  switch (mode) {
-    case kOutSwitched: return lwedot_impl<LOGN, kOutSwitched>(c, jt, grid_limit, s);
-    case kOutRaw: return lwedot_impl<LOGN, kOutRaw>(c, jt, grid_limit, s);
-    case kOutRing: return lwedot_impl<LOGN, kOutRing>(c, jt, grid_limit, s);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-cudaError_t launch_lwedot(const phe_ctx* c, const LweJobTable& jt, int mode, int grid_limit, cudaStream_t s) {
-  switch (c->logn) {
-    case 8: return lwedot_mode<8>(c, jt, mode, grid_limit, s);
-    case 9: return lwedot_mode<9>(c, jt, mode, grid_limit, s);
-    case 10: return lwedot_mode<10>(c, jt, mode, grid_limit, s);
-    case 11: return lwedot_mode<11>(c, jt, mode, grid_limit, s);
-    case 12: return lwedot_mode<12>(c, jt, mode, grid_limit, s);
-    case 13: return lwedot_mode<13>(c, jt, mode, grid_limit, s);
-    default: return cudaErrorInvalidValue;
-  }
-}
-
-template <int LOGN>
-static cudaError_t prepare_impl() {
-  using S = Shape<LOGN>;
-  const size_t smem = (size_t)S::SLOTS * S::PADN * sizeof(u64);
-  cudaError_t e = set_smem(input_ntt_kernel<LOGN>, smem);
-  if (e == cudaSuccess) e = set_smem(weight_ntt_kernel<LOGN>, smem);
-  if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutSwitched>, smem);
-  if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutRaw>, smem);
-  if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutRing>, smem);
-  return e;
+cudaError_t launch_lwedot(const phe_ctx* c, const LweJobTable& jt, int mode, int grid_limit, cudaStream_t s,
+                          bool force64) {
+  const bool rns = c->rns && !force64 && mode != kOutRing;
+  return by_logn(c->logn, [&](auto lg) -> cudaError_t {
+    constexpr int LOGN = decltype(lg)::value;
+    if (rns) {
+      if (mode == kOutSwitched) return lwedot_impl<LOGN, kOutSwitched, true>(c, jt, grid_limit, s);
+      if (mode == kOutRaw) return lwedot_impl<LOGN, kOutRaw, true>(c, jt, grid_limit, s);
+      return cudaErrorInvalidValue;
+    }
+    if (mode == kOutSwitched) return lwedot_impl<LOGN, kOutSwitched, false>(c, jt, grid_limit, s);
+    if (mode == kOutRaw) return lwedot_impl<LOGN, kOutRaw, false>(c, jt, grid_limit, s);
+    if (mode == kOutRing) return lwedot_impl<LOGN, kOutRing, false>(c, jt, grid_limit, s);
+    return cudaErrorInvalidValue;
+  });
 }
 
 cudaError_t prepare_launches(const phe_ctx* c) {
-  switch (c->logn) {
-    case 8: return prepare_impl<8>();
-    case 9: return prepare_impl<9>();
-    case 10: return prepare_impl<10>();
-    case 11: return prepare_impl<11>();
-    case 12: return prepare_impl<12>();
-    case 13: return prepare_impl<13>();
-    default: return cudaErrorInvalidValue;
-  }
+  return by_logn(c->logn, [&](auto lg) -> cudaError_t {
+    constexpr int LOGN = decltype(lg)::value;
+    using S = Shape<LOGN>;
+    const size_t smem = (size_t)S::SLOTS * S::PADN * sizeof(u64);
+    cudaError_t e = set_smem(input_ntt_kernel<LOGN, false>, smem);
+    if (e == cudaSuccess) e = set_smem(input_ntt_kernel<LOGN, true>, smem);
+    if (e == cudaSuccess) e = set_smem(weight_ntt_kernel<LOGN, false>, smem);
+    if (e == cudaSuccess) e = set_smem(weight_ntt_kernel<LOGN, true>, smem);
+    if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutSwitched, false>, smem);
+    if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutRaw, false>, smem);
+    if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutRing, false>, smem);
+    if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutSwitched, true>, smem);
+    if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutRaw, true>, smem);
+    return e;
+  });
 }
 
 cudaError_t launch_expand_masks(const phe_ctx* c, const u64* seeds, u32 n, u64* masks, cudaStream_t s) {

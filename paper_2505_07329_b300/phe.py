@@ -28,7 +28,11 @@ class PheError(RuntimeError):
 
 
 class phe_params(ctypes.Structure):
-    _fields_ = [("N", ctypes.c_uint32), ("log2_qout", ctypes.c_uint32), ("q", ctypes.c_uint64)]
+    _fields_ = [("N", ctypes.c_uint32), ("log2_qout", ctypes.c_uint32), ("q", ctypes.c_uint64),
+                ("rns_p1", ctypes.c_uint32), ("rns_p2", ctypes.c_uint32), ("flags", ctypes.c_uint32)]
+
+
+PHE_CTX_FORCE_U64 = 1
 
 
 class phe_trace_entry(ctypes.Structure):
@@ -172,8 +176,10 @@ def phe_last_error() -> str:
     return lib().phe_last_error().decode()
 
 
-def phe_ctx_create(N: int, q: int, log2_qout: int, device: int = 0):
-    prm = phe_params(N, log2_qout, q)
+def phe_ctx_create(N: int, q: int, log2_qout: int, device: int = 0, rns=None, flags: int = 0):
+    """rns: (p1, p2) when q = p1 * p2 is an RNS modulus of two 30-bit NTT primes."""
+    p1, p2 = rns if rns else (0, 0)
+    prm = phe_params(N, log2_qout, q, p1, p2, flags)
     out = _vp()
     _check(lib().phe_ctx_create(ctypes.byref(prm), device, ctypes.byref(out)))
     return out

@@ -34,6 +34,9 @@ SEED_ARRIVALS = 0x5EED0006
 
 # 2^60 - 2^14 + 1: prime, = 1 mod 2^14, so it carries negacyclic NTTs up to N = 8192.
 Q60 = (1 << 60) - (1 << 14) + 1
+# An RNS ciphertext modulus of the same size: two 30-bit primes = 1 mod 2^14.
+RNS_P1, RNS_P2 = 1073643521, 1073692673
+Q_RNS = RNS_P1 * RNS_P2
 T_PLAIN = 1 << 16          # plaintext modulus t
 LOG2_QOUT = 32             # output modulus q' = 2^32
 SIGMA = 3.2

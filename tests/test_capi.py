@@ -72,3 +72,18 @@ def test_null_arguments_are_rejected(L):
     assert phe.phe_weights_device_bytes(None) == 0
     L.phe_ctx_destroy(None)
     L.phe_weights_free(None)
+
+
+@pytest.mark.parametrize("q,rns,msg", [
+    (synth.Q_RNS + 16384, (synth.RNS_P1, synth.RNS_P2), "q = p1 * p2"),
+    (synth.Q_RNS, (synth.RNS_P1, synth.RNS_P1), "distinct"),
+    (synth.RNS_P1 * 1073709057, (synth.RNS_P1, 1073709057), "p1 and p2 must be prime"),
+    (synth.Q_RNS, None, "not prime"),
+])
+def test_rns_modulus_is_validated(L, q, rns, msg):
+    import sympy
+    assert sympy.isprime(synth.RNS_P1) and sympy.isprime(synth.RNS_P2)
+    with pytest.raises(phe.PheError) as ei:
+        phe.phe_ctx_create(4096, q, 32, 0, rns=rns)
+    assert ei.value.status == phe.PHE_EINVAL
+    assert msg in str(ei.value)
