@@ -306,6 +306,8 @@ phe_status phe_ctx_create(const phe_params* prm, int device, phe_ctx** out) {
   rc.red_mu = (u64)(((u128)1 << 64) / q);
   rc.c30 = (1ull << 30) % q;
   rc.c30p = shoup(rc.c30, q);
+  rc.c60 = (1ull << 60) % q;
+  rc.c60p = shoup(rc.c60, q);
   rc.c64 = (u64)(((u128)1 << 64) % q);
   rc.c64p = shoup(rc.c64, q);
   rc.log2_qout = prm->log2_qout;

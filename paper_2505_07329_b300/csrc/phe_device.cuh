@@ -34,6 +34,8 @@ struct RingConst {
   u64 red_mu;     // floor(2^64 / q): Barrett constant for reducing a 64-bit word
   u64 c30;        // 2^30 mod q (recombines the split body accumulators)
   u64 c30p;       // Shoup quotient of c30
+  u64 c60;        // 2^60 mod q
+  u64 c60p;       // Shoup quotient of c60
   u64 c64;        // 2^64 mod q (reduces 128-bit keystream words of seeded masks)
   u64 c64p;       // Shoup quotient of c64
   u32 ms_s;       // s = floor(log2 q)
@@ -164,10 +166,12 @@ struct Ring2x32 {
 
 // ModulusSwitch q -> 2^k of c in [0, q):
 //   floor((c 2^k + floor(q/2)) / q) mod 2^k   (round half up).
-// X = c 2^k + floor(q/2) < 2^(s+1+k).  With x' = floor(X / 2^s) < 2^(k+1) and
-// mu = floor(2^(64+s)/q), Qt = floor(x' mu / 2^64) satisfies
+// X = c 2^k + floor(q/2) < 2^(s+1+k) + 2^s.  With x' = floor(X / 2^s) <= 2^(k+1)
+// and mu = floor(2^(64+s)/q), Qt = floor(x' mu / 2^64) satisfies
 // floor(X/q) - 2 <= Qt <= floor(X/q); the remainder X - Qt q < 3q < 2^63 is
-// formed in 64-bit arithmetic and corrected at most twice.
+// formed in 64-bit arithmetic and corrected at most twice.  (A variant that
+// forms Qt from two 32-bit wide products and selects measured slower on
+// B300 than the full 64x64 high product.)
 __device__ __forceinline__ u32 modswitch_word(u64 c, const RingConst& rc) {
   const u32 k = rc.log2_qout;
   const u64 lo0 = c << k;

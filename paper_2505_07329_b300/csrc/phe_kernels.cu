@@ -180,9 +180,10 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB)
 //   mask  sum_i A_hat_ti . W_hat_ij in the NTT domain, inverse transform,
 //         coefficient N-1-m to slot m (SampleExtract at N-1), switch;
 //   body  coefficient N-1 of sum_i B_ti * w_hat_ij, i.e. the plain dot
-//         product sum_k W(j,k) B_t[k], exact in two int64 partial sums
-//         (B = Bh 2^30 + Bl; |sum| < 2^14 2^7 2^31 = 2^52 < q), reduced
-//         across the block and switched.
+//         product sum_k W(j,k) B_t[k], exact in three int64 partial sums
+//         (any 64-bit word B = B2 2^60 + B1 2^30 + B0 with B0, B1 < 2^30,
+//         B2 < 16; |sum| < 2^14 2^7 2^30 = 2^51 < q), reduced across the
+//         block and switched.
 // --------------------------------------------------------------------------
 #ifndef PHE_LWEDOT_MIN_BLOCKS
 #define PHE_LWEDOT_MIN_BLOCKS 3
@@ -190,25 +191,28 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB)
 
 // One thread's share of the body dot product of (token t, row).
 __device__ __forceinline__ void body_partial(const LweJob& J, u32 row, u32 t, int p, int P, int N,
-                                             const RingConst& rc, long long& al, long long& ah) {
-  al = ah = 0;
+                                             long long (&acc)[3]) {
+  acc[0] = acc[1] = acc[2] = 0;
   const int8_t* wr = J.wrow + (size_t)row * J.cols;
   const u64* bt = J.bin + (size_t)t * J.L * (size_t)N;
   for (u32 kk = p; kk < J.cols; kk += P) {
-    const u64 b = reduce_word(__ldg(&bt[kk]), rc);
+    const u64 b = __ldg(&bt[kk]);
     const int w = __ldg(&wr[kk]);
-    al += (long long)w * (int)(b & 0x3fffffffull);
-    ah += (long long)w * (int)(b >> 30);
+    acc[0] += (long long)w * (int)(b & 0x3fffffffull);
+    acc[1] += (long long)w * (int)((b >> 30) & 0x3fffffffull);
+    acc[2] += (long long)w * (int)(b >> 60);
   }
 }
 
-// The body mod q from the block-reduced partial sums.
-__device__ __forceinline__ u64 body_combine(long long ll, long long hl, const RingConst& rc) {
+// The body mod q from the block-reduced partial sums S0 + S1 2^30 + S2 2^60.
+__device__ __forceinline__ u64 body_combine(const long long (&S)[3], const RingConst& rc) {
   const u64 q = rc.q;
-  const u64 vh = (hl < 0) ? q - (u64)(-hl) : (u64)hl;
-  const u64 vl = (ll < 0) ? q - (u64)(-ll) : (u64)ll;
-  const u64 v = reduce_2q(mul_shoup(vh, rc.c30, rc.c30p, q), q) + vl;
-  return reduce_2q(v, q);
+  u64 v[3];
+#pragma unroll
+  for (int i = 0; i < 3; ++i) v[i] = (S[i] < 0) ? q - (u64)(-S[i]) : (u64)S[i];
+  const u64 a = reduce_2q(mul_shoup(v[1], rc.c30, rc.c30p, q), q);
+  const u64 b = reduce_2q(mul_shoup(v[2], rc.c60, rc.c60p, q), q);
+  return reduce_2q(reduce_2q(v[0] + a, q) + b, q);
 }
 
 template <int LOGN, int MODE, bool RNS>
@@ -227,7 +231,7 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, PHE_LWEDOT_MIN_BLOCKS)
   constexpr int GW = (P < 32) ? P : 32;   // lanes of one body-reduction group
   constexpr int NGRP = P / GW;            // groups per transform
   extern __shared__ u64 smem[];
-  __shared__ long long red[2][S::SLOTS][NGRP][2];
+  __shared__ long long red[2][S::SLOTS][NGRP][3];
   const int slot = threadIdx.x / P, p = threadIdx.x % P;
   W* buf = reinterpret_cast<W*>(smem + slot * S::PADN);
   const Tw* tw0 = reinterpret_cast<const Tw*>(tw0v);
@@ -290,16 +294,16 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, PHE_LWEDOT_MIN_BLOCKS)
         }
       }
       if constexpr (BODY) {
-        long long al = 0, ah = 0;
-        if (active) body_partial(J, row, t, p, P, N, rc, al, ah);
+        long long acc[3] = {0, 0, 0};
+        if (active) body_partial(J, row, t, p, P, N, acc);
 #pragma unroll
         for (int off = GW / 2; off > 0; off >>= 1) {
-          al += __shfl_xor_sync(0xffffffffu, al, off, GW);
-          ah += __shfl_xor_sync(0xffffffffu, ah, off, GW);
+#pragma unroll
+          for (int i = 0; i < 3; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off, GW);
         }
         if (p % GW == 0) {
-          red[par][slot][p / GW][0] = al;
-          red[par][slot][p / GW][1] = ah;
+#pragma unroll
+          for (int i = 0; i < 3; ++i) red[par][slot][p / GW][i] = acc[i];
         }
       }
       intt_regs<LOGN>(x, p, buf, tw0, twc, ring);  // barriers inside also order red[]
@@ -337,13 +341,13 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, PHE_LWEDOT_MIN_BLOCKS)
         }
         if constexpr (BODY) {
           if (p == 0) {
-            long long hl = 0, ll = 0;
+            long long S3[3] = {0, 0, 0};
 #pragma unroll
             for (int g = 0; g < NGRP; ++g) {
-              ll += red[par][slot][g][0];
-              hl += red[par][slot][g][1];
+#pragma unroll
+              for (int i = 0; i < 3; ++i) S3[i] += red[par][slot][g][i];
             }
-            const u64 v = body_combine(ll, hl, rc);
+            const u64 v = body_combine(S3, rc);
             if constexpr (MODE == kOutSwitched)
               reinterpret_cast<uint32_t*>(J.out_body)[(size_t)t * J.rows + row] = modswitch_word(v, rc);
             else
