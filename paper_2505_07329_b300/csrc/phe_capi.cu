@@ -345,6 +345,17 @@ phe_status phe_ctx_create(const phe_params* prm, int device, phe_ctx** out) {
     k.c32ap = shoup32(k.c32a, p1);
     k.c32b = (u32)((1ull << 32) % p2);
     k.c32bp = shoup32(k.c32b, p2);
+    const u64 two_k = 1ull << prm->log2_qout;
+    k.a1 = (u32)(two_k / p1);
+    k.b1 = (u32)(two_k % p1);
+    k.b1p = shoup32(k.b1, p1);
+    k.a2 = (u32)(two_k / p2);
+    k.b2 = (u32)(two_k % p2);
+    k.b2p = shoup32(k.b2, p2);
+    k.inv_a2 = (u32)((1ull << 32) / p2);
+    k.half1 = (p1 - 1) / 2;
+    k.half2 = (p2 - 1) / 2;
+    k.kmask = (u32)(two_k - 1);
     c->ninv.n1 = (u32)modinv(N, p1);
     c->ninv.n1p = shoup32(c->ninv.n1, p1);
     c->ninv.n2 = (u32)modinv(N, p2);

@@ -312,12 +312,17 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, PHE_LWEDOT_MIN_BLOCKS)
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
             const int pos = pass_pos<LOGN, NP - 1>(p, e);
-            u64 c;
-            if constexpr (RNS) c = from_residues(sub_if32(x[e].x, rk.p1), sub_if32(x[e].y, rk.p2), rk);
-            else c = reduce_4q(x[e], q, rc.q2);
             const size_t o = ((size_t)t * J.rows + row) * N + (N - 1 - pos);
-            if constexpr (MODE == kOutSwitched) reinterpret_cast<uint32_t*>(J.out)[o] = modswitch_word(c, rc);
-            else reinterpret_cast<u64*>(J.out)[o] = c;
+            if constexpr (RNS) {
+              const u32 c1 = sub_if32(x[e].x, rk.p1);
+              const u32 h = crt_digit(c1, sub_if32(x[e].y, rk.p2), rk);
+              if constexpr (MODE == kOutSwitched) reinterpret_cast<uint32_t*>(J.out)[o] = rns_modswitch(c1, h, rk);
+              else reinterpret_cast<u64*>(J.out)[o] = (u64)c1 + (u64)rk.p1 * h;
+            } else {
+              const u64 c = reduce_4q(x[e], q, rc.q2);
+              if constexpr (MODE == kOutSwitched) reinterpret_cast<uint32_t*>(J.out)[o] = modswitch_word(c, rc);
+              else reinterpret_cast<u64*>(J.out)[o] = c;
+            }
           }
         } else if constexpr (!RNS) {
           // Ring product in natural order plus E + delta * x_hat: client-side

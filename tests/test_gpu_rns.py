@@ -52,6 +52,26 @@ def test_rns_form_equals_u64_form(ctxs, N):
         assert np.array_equal(a[0], b[0]) and np.array_equal(a[1], b[1])
 
 
+@pytest.mark.parametrize("k", [31, 26, 1])
+def test_rns_switch_to_other_output_moduli(ctxs, k):
+    # the RNS epilogue switches from the CRT digits in 32-bit arithmetic;
+    # compare with the 64-bit form's switch (itself checked against the oracle)
+    N, d_in, d_out, T = 1024, 1100, 33, 7
+    W = synth.weights(d_out, d_in, seed=k)
+    A = synth.uniform_words((T, 2, N), Q, 100 + k)
+    B = synth.uniform_words((T, 2, N), Q, 200 + k)
+    got = []
+    for force64 in (False, True):
+        ctx = ctxs(N, force64, k)
+        w = phe.phe_weights_upload(ctx, W, phe.PHE_DIR_FWD_BIT)
+        try:
+            got.append(gpu_matmul(ctx, w, phe.PHE_FWD, A, B, d_out))
+        finally:
+            phe.phe_weights_free(w)
+    assert np.array_equal(got[0][0], got[1][0]) and np.array_equal(got[0][1], got[1][1])
+    assert int(got[0][0].max()) < 2 ** k
+
+
 def test_rns_matches_oracle_and_decrypts(orc, ctxs):
     N, d_in, d_out, T = 1024, 1500, 24, 6
     L = synth.blocks(d_in, N)
