@@ -15,6 +15,9 @@ Functions and the passages they follow:
   modswitch                               ModulusSwitch q -> 2^k           Sec. 3.2 / 4.3.1
   rlwe_encrypt, lwe_phase, decode         RLWE / LWE definitions           Sec. 3.1
   expand_mask, chacha20_block             mask from a seed (PRNG read as ChaCha20, RFC 8439)  Sec. 3.1
+  gadget, decompose                       Decomp (read as TFHE's approximate signed gadget)  Sec. 3.2
+  ksk_encrypt, keyswitch, rotate          KeySwitching, Rotate             Sec. 3.2
+  pack, pack_coeffs                       sum_j Rotate(KeySwitching(LWE_j), j)   Eq. (pack_rotate)
 
 Parity status: every function above is pinned by tests/test_oracle_pins.py
 (closed forms, library routines, brute force, exact noise identity).
@@ -87,6 +90,19 @@ def lib():
             L.oracle_chacha20_block.argtypes = [_u32p, ctypes.c_uint32, _u32p, _u32p]
             L.oracle_expand_mask.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, _u64p]
             L.oracle_num_threads.restype = ctypes.c_int
+            L.oracle_gadget.restype = ctypes.c_uint64
+            L.oracle_gadget.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32]
+            L.oracle_decompose.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, _i64p]
+            L.oracle_ksk_encrypt.argtypes = [_u64p, _i64p, _i64p, ctypes.c_uint32, _i64p, ctypes.c_uint32,
+                                             ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, _u64p]
+            L.oracle_keyswitch.argtypes = [_u64p, ctypes.c_uint64, ctypes.c_uint32, _u64p, _u64p, ctypes.c_uint32,
+                                           ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, _u64p, _u64p]
+            L.oracle_rotate.argtypes = [_u64p, ctypes.c_uint32, ctypes.c_uint32, ctypes.c_uint64, _u64p]
+            L.oracle_pack.argtypes = [_u64p, _u64p, ctypes.c_uint32, ctypes.c_uint32, _u64p, _u64p, ctypes.c_uint32,
+                                      ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, _u64p, _u64p]
+            L.oracle_pack_coeffs.argtypes = [_u64p, _u64p, ctypes.c_uint32, ctypes.c_uint32, _u64p, _u64p,
+                                             ctypes.c_uint32, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32,
+                                             _u32p, ctypes.c_uint32, _u64p, _u64p]
             _lib = L
     return _lib
 
@@ -294,6 +310,71 @@ def expand_masks(seeds, N: int, q: int) -> np.ndarray:
     for idx in np.ndindex(seeds.shape):
         out[idx] = expand_mask(int(seeds[idx]), N, q)
     return out
+
+
+# --- output packing ------------------------------------------------------------
+
+def gadget(q: int, base_log: int, l: int) -> int:
+    return int(lib().oracle_gadget(q, base_log, l))
+
+
+def decompose(a: int, q: int, base_log: int, ell: int) -> np.ndarray:
+    d = np.zeros(ell, dtype=np.int64)
+    lib().oracle_decompose(a, q, base_log, ell, _p(d, _i64p))
+    return d
+
+
+def ksk_encrypt(KA, E, s, S2, q: int, base_log: int, ell: int) -> np.ndarray:
+    """KB [n][ell][N] of the key-switching key s -> S2 with masks KA and noise E."""
+    KA, E, s, S2 = _u64(KA), _i64(E), _i64(s), _i64(S2)
+    n, N = s.shape[0], S2.shape[0]
+    assert KA.shape == (n, ell, N) and E.shape == (n, ell, N)
+    KB = np.zeros((n, ell, N), dtype=np.uint64)
+    lib().oracle_ksk_encrypt(_p(KA, _u64p), _p(E, _i64p), _p(s, _i64p), n, _p(S2, _i64p), N, q, base_log, ell,
+                             _p(KB, _u64p))
+    return KB
+
+
+def keyswitch(a, b: int, KA, KB, q: int, base_log: int, ell: int):
+    a, KA, KB = _u64(a), _u64(KA), _u64(KB)
+    n, N = a.shape[0], KA.shape[2]
+    A_out = np.zeros(N, dtype=np.uint64)
+    B_out = np.zeros(N, dtype=np.uint64)
+    lib().oracle_keyswitch(_p(a, _u64p), b, n, _p(KA, _u64p), _p(KB, _u64p), N, q, base_log, ell,
+                           _p(A_out, _u64p), _p(B_out, _u64p))
+    return A_out, B_out
+
+
+def rotate(P, k: int, q: int) -> np.ndarray:
+    P = _u64(P)
+    out = np.zeros_like(P)
+    lib().oracle_rotate(_p(P, _u64p), P.shape[0], k, q, _p(out, _u64p))
+    return out
+
+
+def pack(a, b, KA, KB, q: int, base_log: int, ell: int):
+    """(A, B) = sum_j Rotate(KeySwitching((a_j, b_j)), j) for a: [m][n], b: [m]."""
+    a, b, KA, KB = _u64(a), _u64(b), _u64(KA), _u64(KB)
+    m, n = a.shape
+    N = KA.shape[2]
+    A_out = np.zeros(N, dtype=np.uint64)
+    B_out = np.zeros(N, dtype=np.uint64)
+    lib().oracle_pack(_p(a, _u64p), _p(b, _u64p), m, n, _p(KA, _u64p), _p(KB, _u64p), N, q, base_log, ell,
+                      _p(A_out, _u64p), _p(B_out, _u64p))
+    return A_out, B_out
+
+
+def pack_coeffs(a, b, KA, KB, q: int, base_log: int, ell: int, rs):
+    """Coefficients rs of the packed (A, B), evaluated one by one."""
+    a, b, KA, KB = _u64(a), _u64(b), _u64(KA), _u64(KB)
+    rs = np.ascontiguousarray(np.asarray(rs, dtype=np.uint32))
+    m, n = a.shape
+    N = KA.shape[2]
+    A_out = np.zeros(rs.shape[0], dtype=np.uint64)
+    B_out = np.zeros(rs.shape[0], dtype=np.uint64)
+    lib().oracle_pack_coeffs(_p(a, _u64p), _p(b, _u64p), m, n, _p(KA, _u64p), _p(KB, _u64p), N, q, base_log, ell,
+                             _p(rs, _u32p), rs.shape[0], _p(A_out, _u64p), _p(B_out, _u64p))
+    return A_out, B_out
 
 
 def num_threads() -> int:

@@ -23,6 +23,8 @@
  *   - seeded mask generation ("Mask Generation via PRNG") ... Sec. 3.1; the PRNG
  *     is not named by the paper; this oracle reads it as the ChaCha20 block
  *     function of RFC 8439 (see oracle_expand_mask).
+ *   - Decomp, KeySwitching, Rotate ........................... Sec. 3.2
+ *   - output packing sum_j Rotate(KeySwitching(LWE_j), j) ..... Eq. (pack_rotate), Sec. 4.3.1
  *
  * Parity pins (closed forms, library routines, brute force) live in tests/.
  */
@@ -402,6 +404,159 @@ void oracle_expand_mask(uint64_t seed, uint32_t N, uint64_t q, uint64_t* A) {
         u128 v = (u128)w[0] | ((u128)w[1] << 32) | ((u128)w[2] << 64) | ((u128)w[3] << 96);
         A[m] = (uint64_t)(v % q);
     }
+}
+
+/* ------------------------------------------------------------------------ */
+/* Output packing: KeySwitching and Rotate (Sec. 3.2), Eq. (pack_rotate).     */
+/* ------------------------------------------------------------------------ */
+
+/* The paper takes Decomp from TFHE without fixing it; this oracle reads it as
+ * the approximate signed gadget decomposition with base B = 2^base_log and
+ * ell levels (base_log * ell <= 62):
+ *   a~ = ModulusSwitch of a from q to B^ell (the same rounding as above),
+ *   digits d_0 (most significant) .. d_{ell-1} in [-B/2, B/2) with
+ *   sum_l d_l B^(ell-1-l) = a~ (mod B^ell),
+ * and the matching gadget g_l = round(q / B^(l+1)) (ties up), so that
+ * sum_l d_l g_l = a (mod q) up to q/(2 B^ell) + ell B/4. */
+uint64_t oracle_gadget(uint64_t q, uint32_t base_log, uint32_t l) {
+    u128 den = (u128)1 << (base_log * (l + 1));
+    return (uint64_t)(((u128)q + den / 2) / den);
+}
+
+void oracle_decompose(uint64_t a, uint64_t q, uint32_t base_log, uint32_t ell, int64_t* d) {
+    uint64_t v = oracle_modswitch(a, q, base_log * ell);
+    const uint64_t B = (uint64_t)1 << base_log;
+    for (int l = (int)ell - 1; l >= 0; --l) {
+        int64_t r = (int64_t)(v & (B - 1));
+        v >>= base_log;
+        if (r >= (int64_t)(B / 2)) {  /* signed digit: borrow from the next level */
+            r -= (int64_t)B;
+            v += 1;
+        }
+        d[l] = r;
+    }
+    /* a carry out of d_0 is a multiple of B^ell, i.e. of q after scaling: dropped */
+}
+
+/* Key-switching key (client side, test only): KSK_{i,l} is an RLWE encryption
+ * under S2 of the constant polynomial s_i g_l:
+ *   KB_{i,l} = KA_{i,l} * S2 + E_{i,l} + s_i g_l X^0   (mod q).
+ * KA, E, KB are [n][ell][N]; s has n entries (the LWE key), S2 N (the target key). */
+void oracle_ksk_encrypt(const uint64_t* KA, const int64_t* E, const int64_t* s, uint32_t n, const int64_t* S2,
+                        uint32_t N, uint64_t q, uint32_t base_log, uint32_t ell, uint64_t* KB) {
+    for (uint32_t i = 0; i < n; ++i) {
+        for (uint32_t l = 0; l < ell; ++l) {
+            const size_t o = ((size_t)i * ell + l) * N;
+            negacyclic_mul_small(KA + o, S2, KB + o, N, q);
+            for (uint32_t k = 0; k < N; ++k) KB[o + k] = mod_add(KB[o + k], mod_i128((i128)E[o + k], q), q);
+            const uint64_t msg = mod_mul(mod_i128((i128)s[i], q), oracle_gadget(q, base_log, l) % q, q);
+            KB[o] = mod_add(KB[o], msg, q);
+        }
+    }
+}
+
+/* KeySwitching of one LWE ciphertext (a, b) of dimension n (Sec. 3.2):
+ *   (A', B') = (0, b) - sum_i Decomp(a_i) . KSK_i
+ *            = (-sum_{i,l} d_{i,l} KA_{i,l},  b X^0 - sum_{i,l} d_{i,l} KB_{i,l}). */
+void oracle_keyswitch(const uint64_t* a, uint64_t b, uint32_t n, const uint64_t* KA, const uint64_t* KB, uint32_t N,
+                      uint64_t q, uint32_t base_log, uint32_t ell, uint64_t* A_out, uint64_t* B_out) {
+    int64_t* d = (int64_t*)malloc(sizeof(int64_t) * ell);
+    for (uint32_t k = 0; k < N; ++k) {
+        A_out[k] = 0;
+        B_out[k] = 0;
+    }
+    B_out[0] = b % q;
+    for (uint32_t i = 0; i < n; ++i) {
+        oracle_decompose(a[i], q, base_log, ell, d);
+        for (uint32_t l = 0; l < ell; ++l) {
+            const size_t o = ((size_t)i * ell + l) * N;
+            const uint64_t dq = mod_i128((i128)d[l], q);
+            for (uint32_t k = 0; k < N; ++k) {
+                A_out[k] = mod_sub(A_out[k], mod_mul(dq, KA[o + k], q), q);
+                B_out[k] = mod_sub(B_out[k], mod_mul(dq, KB[o + k], q), q);
+            }
+        }
+    }
+    free(d);
+}
+
+/* Rotate (Sec. 3.2): P X^k in R_q.  For 0 <= k < N coefficient r of the result
+ * is P_{r-k} when r >= k and -P_{r-k+N} when r < k; X^N = -1 covers N <= k < 2N. */
+void oracle_rotate(const uint64_t* P, uint32_t N, uint32_t k, uint64_t q, uint64_t* out) {
+    const int negate_all = (k >= N);
+    if (negate_all) k -= N;
+    for (uint32_t r = 0; r < N; ++r) {
+        uint64_t v = (r >= k) ? P[r - k] % q : mod_sub(0, P[r - k + N] % q, q);
+        out[r] = negate_all ? mod_sub(0, v, q) : v;
+    }
+}
+
+/* Eq. (pack_rotate) before its ModulusSwitch: m <= N LWE ciphertexts
+ * (a_j, b_j) of dimension n become one RLWE ciphertext
+ *   (A, B) = sum_{j<m} Rotate(KeySwitching(LWE_j), j)      (mod q),
+ * so that coefficient j of its message is the message of LWE_j.
+ * a: [m][n], b: [m]; KA, KB: [n][ell][N]. */
+void oracle_pack(const uint64_t* a, const uint64_t* b, uint32_t m, uint32_t n, const uint64_t* KA, const uint64_t* KB,
+                 uint32_t N, uint64_t q, uint32_t base_log, uint32_t ell, uint64_t* A_out, uint64_t* B_out) {
+    uint64_t* ka = (uint64_t*)malloc(sizeof(uint64_t) * N);
+    uint64_t* kb = (uint64_t*)malloc(sizeof(uint64_t) * N);
+    uint64_t* ra = (uint64_t*)malloc(sizeof(uint64_t) * N);
+    uint64_t* rb = (uint64_t*)malloc(sizeof(uint64_t) * N);
+    for (uint32_t k = 0; k < N; ++k) {
+        A_out[k] = 0;
+        B_out[k] = 0;
+    }
+    for (uint32_t j = 0; j < m; ++j) {
+        oracle_keyswitch(a + (size_t)j * n, b[j], n, KA, KB, N, q, base_log, ell, ka, kb);
+        oracle_rotate(ka, N, j, q, ra);
+        oracle_rotate(kb, N, j, q, rb);
+        for (uint32_t k = 0; k < N; ++k) {
+            A_out[k] = mod_add(A_out[k], ra[k], q);
+            B_out[k] = mod_add(B_out[k], rb[k], q);
+        }
+    }
+    free(ka);
+    free(kb);
+    free(ra);
+    free(rb);
+}
+
+/* The same sum evaluated one coefficient at a time, for sampled checks at
+ * sizes where oracle_pack is too slow.  Coefficient r of Rotate(P, j) is
+ * P_{r-j} (r >= j) or -P_{r-j+N} (r < j), and coefficient c of
+ * KeySwitching(LWE_j) is [c = 0] b_j - sum_{i,l} d_{i,l}(a_j[i]) K_{i,l}[c]. */
+void oracle_pack_coeffs(const uint64_t* a, const uint64_t* b, uint32_t m, uint32_t n, const uint64_t* KA,
+                        const uint64_t* KB, uint32_t N, uint64_t q, uint32_t base_log, uint32_t ell,
+                        const uint32_t* rs, uint32_t n_rs, uint64_t* A_out, uint64_t* B_out) {
+    int64_t* D = (int64_t*)malloc(sizeof(int64_t) * (size_t)m * n * ell);
+    for (size_t ji = 0; ji < (size_t)m * n; ++ji) oracle_decompose(a[ji], q, base_log, ell, D + ji * ell);
+#pragma omp parallel for schedule(dynamic, 1)
+    for (uint32_t x = 0; x < n_rs; ++x) {
+        const uint32_t r = rs[x];
+        uint64_t accA = 0, accB = 0;
+        for (uint32_t j = 0; j < m; ++j) {
+            const int wrapped = r < j;
+            const uint32_t c = wrapped ? r + N - j : r - j;
+            uint64_t ca = 0, cb = (c == 0) ? b[j] % q : 0;
+            for (uint32_t i = 0; i < n; ++i) {
+                for (uint32_t l = 0; l < ell; ++l) {
+                    const uint64_t dq = mod_i128((i128)D[((size_t)j * n + i) * ell + l], q);
+                    const size_t o = ((size_t)i * ell + l) * N + c;
+                    ca = mod_sub(ca, mod_mul(dq, KA[o], q), q);
+                    cb = mod_sub(cb, mod_mul(dq, KB[o], q), q);
+                }
+            }
+            if (wrapped) {
+                ca = mod_sub(0, ca, q);
+                cb = mod_sub(0, cb, q);
+            }
+            accA = mod_add(accA, ca, q);
+            accB = mod_add(accB, cb, q);
+        }
+        A_out[x] = accA;
+        B_out[x] = accB;
+    }
+    free(D);
 }
 
 int oracle_num_threads(void) {
