@@ -37,13 +37,14 @@ sys.path.insert(0, ROOT)
 import synth  # noqa: E402
 
 METRIC = "encrypted W·[x] tokens/s per Llama-1B layer; p50/p99 latency; % of roofline"
-# DRAM bytes (read + write) per lwedot_kernel launch, measured with ncu on the
-# 14 products of one 32-token chunk of the layer workload (mean over the 14),
-# with the algorithmic bytes of the same launches.  Valid only for the kernel
-# sources the counters were taken on (hash of phe_kernels.cu + phe_device.cuh).
-TRAFFIC_KERNEL_HASH = "f44c15b967e04afd"
-TRAFFIC_BYTES_PER_LAUNCH = 2138.8e6
-TRAFFIC_ALG_BYTES_PER_LAUNCH = 1895.5e6
+# DRAM bytes (read + write) of one lwedot_kernel launch of the batched form
+# (128 tokens x all 14 products of the layer workload, RNS modulus), measured
+# with ncu, and the algorithmic bytes of that launch.  Valid only for the
+# kernel sources the counters were taken on (hash of phe_kernels.cu +
+# phe_device.cuh).
+TRAFFIC_KERNEL_HASH = "71035676985d25fb"
+TRAFFIC_BYTES_PER_LAUNCH = 96444.6e6
+TRAFFIC_ALG_BYTES_PER_LAUNCH = 95891.8e6
 
 
 def kernel_source_hash() -> str:
@@ -255,7 +256,7 @@ def workload_config(wl, args, form):
             "description": wl.description, "tokens_per_gpu": args.tokens or wl.tokens,
             "N": wl.ring.N, "q": qdesc, "q_out": f"2^{wl.ring.log2_qout}",
             "projections": [f"{n} {di}->{do}" for n, di, do in wl.projections],
-            "directions": list(wl.directions), "form": form, "token_chunk": args.chunk,
+            "directions": list(wl.directions), "form": form, "plain_call_tokens": args.chunk,
             "l2": "inputs larger than L2 (encrypted inputs and encoded weights are several GB)"}
 
 
@@ -431,8 +432,8 @@ def main():
     modmuls = modmuls_per_token(wl) * T * args.steps
     achieved = modmuls / (kernel_ms / 1e3) / 1e9 if kernel_ms else None
     peak = alu_peak_gmodmul(args.modulus)
-    traffic_ok = (kernel_source_hash() == TRAFFIC_KERNEL_HASH and wl.name == "layer" and chunk == 32
-                  and args.form == "plain")
+    traffic_ok = (kernel_source_hash() == TRAFFIC_KERNEL_HASH and wl.name == "layer" and bchunk == 128
+                  and args.form == "batched" and args.modulus == "rns" and T % bchunk == 0)
     roof = {"bound": "alu", "unit": "Gmodmul/s", "achieved": achieved, "peak": peak,
             "frac": (achieved / peak) if achieved and peak else None,
             "traffic": TRAFFIC_BYTES_PER_LAUNCH if traffic_ok else None,
@@ -486,8 +487,9 @@ def main():
     if rank == 0 and world == 1 and not args.no_cpu:
         cpu = oracle_tokens_per_s(wl, args.cpu_seconds)
 
-    form_desc = ("batched: one autotuned plan per token chunk over all 14 products (one persistent lwedot launch, "
-                 "CUDA graph replay)" if args.form == "batched"
+    form_desc = ("batched: one autotuned plan per token chunk over all 14 products (one lwedot launch over "
+                 "every tile of the chunk, persistent when the autotuner picks it; CUDA graph replay)"
+                 if args.form == "batched"
                  else "plain per-call (one phe_matmul per projection and token chunk)")
     calls = trace.get("phe_plan_graph") if args.form == "batched" else trace.get("phe_matmul")
     calls = calls or {}

@@ -246,8 +246,12 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, PHE_LWEDOT_MIN_BLOCKS)
     while (tile >= jt.prefix[k + 1]) ++k;
     const LweJob& J = jt.j[k];
     const u32 local = tile - jt.prefix[k];
-    const u32 row = local % J.rows;
-    const u32 t0 = (local / J.rows) * J.tok_chunk;
+    // The token chunks of one row are adjacent tiles: CTAs resident at the
+    // same time share W_hat_j through L2, so a launch reads W_hat from HBM
+    // about once however small the token chunk.
+    const u32 nch = (J.T + J.tok_chunk - 1) / J.tok_chunk;
+    const u32 row = local / nch;
+    const u32 t0 = (local % nch) * J.tok_chunk;
     const u32 t1 = min(J.T, t0 + J.tok_chunk);
     const Tw* wrow = reinterpret_cast<const Tw*>(J.what) + (size_t)row * J.L * N;
     const u32 iters = (t1 - t0 + S::SLOTS - 1) / S::SLOTS;
