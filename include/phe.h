@@ -320,6 +320,69 @@ phe_status phe_server_stats(phe_server* srv, phe_serving_stats* out);
 /* Drains the admitted and waiting requests, then stops the worker. */
 void phe_server_destroy(phe_server* srv);
 
+/* ------------------------------------------------------------------------
+ * Output packing (Sec. 3.2 KeySwitching and Rotate; Eq. (pack_rotate); the
+ * key-switching products as matrix products, Eq. (gpu_keyswitch), Sec. 4.5)
+ *
+ * The LWE outputs of rows gN .. gN+m-1 of a token (m = min(N, rows - gN))
+ * become one RLWE ciphertext
+ *     RLWE_g = ModulusSwitch( sum_{j<m} Rotate(KeySwitching(LWE_{gN+j}), j) ),
+ * whose message coefficient j is the message of output row gN+j (zero for
+ * j >= m).  This replaces rows*(N+1) words per token by G*2N,
+ * G = ceil(rows/N).
+ *
+ * KeySwitching of (a, b) under the LWE key s (dimension n = N: the RLWE key's
+ * coefficients, as SampleExtract leaves them) to the RLWE key S' is
+ *     (A', B') = (0, b) - sum_{i<n} sum_{l<ell} d_l(a_i) KSK_{i,l},
+ * with Decomp read as the approximate signed gadget decomposition: a~ is the
+ * ModulusSwitch of a to B^ell (B = 2^base_log), d_0 .. d_{ell-1} are its
+ * signed base-B digits in [-B/2, B/2) (d_0 most significant), and KSK_{i,l}
+ * encrypts the constant polynomial s_i round(q / B^(l+1)) under S'.
+ * ------------------------------------------------------------------------ */
+typedef struct phe_ksk phe_ksk;
+
+/* Copies a key-switching key to the device and precomputes its NTT form
+ * (-N^-1 NTT(KSK) with Shoup quotients; 2*n*ell*N*16 bytes).
+ *   h_ka, h_kb  host [n][ell][N] uint64: KSK_{i,l} = (h_ka[i][l], h_kb[i][l]),
+ *               words mod q (larger words are reduced); caller keeps them.
+ *   n           LWE dimension; must equal N.
+ *   base_log, ell  1 <= ell <= 4, 1 <= base_log <= 30, base_log*ell <= 32.
+ * Synchronous.  Errors: PHE_EINVAL (shape or parameters), PHE_ENOMEM,
+ * PHE_ECUDA. */
+phe_status phe_ksk_upload(phe_ctx* ctx, const uint64_t* h_ka, const uint64_t* h_kb, uint32_t n, uint32_t base_log,
+                          uint32_t ell, phe_ksk** out);
+void phe_ksk_free(phe_ksk* k);
+uint64_t phe_ksk_device_bytes(const phe_ksk* k);
+
+/* Packs T x rows given LWE ciphertexts of dimension N.
+ *   d_lwe_mask  [T][rows][N] uint64 mod q (as phe_matmul writes with PHE_OUT_RAW)
+ *   d_lwe_body  [T][rows]    uint64 mod q
+ *   d_out_a, d_out_b  [T][G][N]: uint32 words mod 2^log2_qout (PHE_OUT_SWITCHED)
+ *               or uint64 mod q (PHE_OUT_RAW); RLWE_g of token t at (t*G + g)*N.
+ * Allocates its scratch (at most 2 GiB of digit rows at a time) on `stream`
+ * with cudaMallocAsync.  Errors: PHE_EINVAL (handles, flags, T*G > 2^24),
+ * PHE_ENOMEM, PHE_ECUDA. */
+phe_status phe_pack(phe_ctx* ctx, const phe_ksk* k, uint32_t T, uint32_t rows, const uint64_t* d_lwe_mask,
+                     const uint64_t* d_lwe_body, void* d_out_a, void* d_out_b, uint32_t flags, void* stream);
+
+/* phe_matmul followed by phe_pack, token chunk by token chunk (the raw LWE
+ * outputs of a chunk stay in a scratch buffer of at most 2 GiB): the paper's
+ * whole server path, Eq. (LWEdot) then Eq. (pack_rotate).  Inputs as
+ * phe_matmul; outputs as phe_pack with rows of direction `dir`. */
+phe_status phe_matmul_packed(phe_ctx* ctx, const phe_weights* w, const phe_ksk* k, int dir, uint32_t T,
+                             const uint64_t* d_in_mask, const uint64_t* d_in_body, void* d_out_a, void* d_out_b,
+                             uint32_t flags, void* stream);
+
+/* phe_matmul_packed with HOST buffers, `tok_chunk` tokens at a time (0
+ * selects 8): inputs host->device, the packed path, packed outputs
+ * device->host, double-buffered on two streams.  h_* have the layouts of the
+ * device buffers above; page-locked host memory makes the copies
+ * asynchronous.  Blocking: returns after the last result has reached the
+ * host.  Errors: as phe_matmul_packed. */
+phe_status phe_matmul_packed_host(phe_ctx* ctx, const phe_weights* w, const phe_ksk* k, int dir, uint32_t T,
+                                  const uint64_t* h_in_mask, const uint64_t* h_in_body, void* h_out_a,
+                                  void* h_out_b, uint32_t flags, uint32_t tok_chunk, void* stream);
+
 /* Size of the fixed device scratch array used by phe_matmul_noalloc. */
 #define PHE_NOALLOC_MAX_SCRATCH_BYTES (16u << 20)
 

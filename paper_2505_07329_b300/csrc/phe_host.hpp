@@ -48,11 +48,14 @@ enum OutMode : int { kOutSwitched = 0, kOutRaw = 1, kOutRing = 2 };
 
 // Kernel names for tracing; kKCall brackets a whole phe_matmul call.
 enum KernelId : int {
-  kKInputNtt = 0, kKLwedot, kKModswitch, kKWeightNtt, kKExpand, kKCall, kKPlan, kKGraph, kKCount
+  kKInputNtt = 0, kKLwedot, kKModswitch, kKWeightNtt, kKExpand, kKCall, kKPlan, kKGraph,
+  kKPackDecompose, kKPackMac, kKPackFinish, kKPackCall, kKCount
 };
 inline const char* kernel_name(int k) {
   static const char* names[kKCount] = {"input_ntt_kernel", "lwedot_kernel", "modswitch_kernel", "weight_ntt_kernel",
-                                       "expand_masks_kernel", "phe_matmul", "phe_plan_run", "phe_plan_graph"};
+                                       "expand_masks_kernel", "phe_matmul", "phe_plan_run", "phe_plan_graph",
+                                       "pack_decompose_kernel", "pack_mac_kernel", "pack_finish_kernel",
+                                       "phe_pack"};
   return (k >= 0 && k < kKCount) ? names[k] : "?";
 }
 struct TraceRec {

@@ -1,0 +1,631 @@
+// Output packing (Sec. 3.2 KeySwitching and Rotate, Eq. (pack_rotate)):
+// the m <= N LWE outputs (a_j, b_j) of a group of rows become one RLWE
+// ciphertext sum_j Rotate(KeySwitching(LWE_j), j), then ModulusSwitch.
+//
+// KeySwitching is linear in the digits of the masks and Rotate by j is the
+// product with X^j, so the packed mask is
+//   A = - sum_{i,l} D_il(X) KA_il(X),   D_il(X) = sum_j d_l(a_j[i]) X^j,
+// and B = sum_j b_j X^j - sum_{i,l} D_il(X) KB_il(X): n*ell negacyclic
+// products with the key-switching key instead of m*n*ell scalar-polynomial
+// products.  Kernels:
+//   pack_decompose_kernel  digits d_l(a_j[i]) of the masks, transposed so
+//                          that D_il is a row over j (natural order, mod q)
+//   input_ntt_kernel       D_il -> NTT domain, in place
+//   pack_mac_kernel        per NTT slot: sum over (i,l) of D_hat * KSK_hat
+//                          (the key carries -N^-1 and Shoup quotients)
+//   pack_finish_kernel     inverse NTT of A_hat and B_hat, + b_j X^j, switch
+//   ksk_finish_kernel      upload: NTT(KSK) -> -N^-1 NTT(KSK) with quotients
+#include <algorithm>
+#include <cstdarg>
+#include <cstdio>
+#include <new>
+#include <vector>
+
+#include "phe_host.hpp"
+
+using phe::u32;
+using phe::u64;
+
+struct phe_ksk {
+  phe_ctx* ctx = nullptr;
+  uint32_t n = 0, base_log = 0, ell = 0;
+  void* khat = nullptr;  // [n*ell][2][N] entries of 16 bytes (A then B), A_hat slot order
+  uint64_t bytes = 0;
+};
+
+namespace phe {
+
+// Signed gadget digits of a (Sec. 3.2 Decomp, read as the approximate signed
+// decomposition of TFHE): a~ = ModulusSwitch of a from q to B^ell, then
+// base-B digits d_0 (most significant) .. d_{ell-1} in [-B/2, B/2); a carry
+// out of d_0 is a multiple of B^ell and is dropped.  rcK is the context's
+// constants with log2_qout = base_log * ell (<= 32).
+template <int ELL>
+__device__ __forceinline__ void gadget_digits(u64 a, const RingConst& rcK, u32 base_log, int (&d)[ELL]) {
+  u32 v = modswitch_word(a, rcK);
+  const u32 B = 1u << base_log, half = B >> 1, mask = B - 1;
+#pragma unroll
+  for (int l = ELL - 1; l >= 0; --l) {
+    int r = (int)(v & mask);
+    v = (base_log < 32) ? (v >> base_log) : 0u;
+    if ((u32)r >= half) {
+      r -= (int)B;
+      v += 1u;
+    }
+    d[l] = r;
+  }
+}
+
+// Masks [T][rows][N] (mod q) -> digit rows D[u][i*ell + l][j] of the units
+// u_base + u, unit = t*G + g,
+// holding d_l(a_{gN+j}[i]) mod q for gN + j < rows and 0 past the last row.
+// A 32x32 tile of (j, i) goes through shared memory so that both the load
+// (along i) and the store (along j) are coalesced.
+template <int ELL>
+__global__ void __launch_bounds__(256)
+    pack_decompose_kernel(const u64* __restrict__ mask, u32 rows, u32 N, u32 G, u32 u_base, u32 base_log,
+                          RingConst rcK, u64* __restrict__ D) {
+  __shared__ int tile[ELL][32][33];
+  const u32 u = blockIdx.z;  // unit within the chunk; D holds the chunk's units
+  const u32 t = (u_base + u) / G, g = (u_base + u) % G;
+  const u32 i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+  const u32 tx = threadIdx.x, ty = threadIdx.y;
+  for (u32 k = ty; k < 32; k += 8) {
+    const u32 j = j0 + k, row = g * N + j;
+    int d[ELL];
+    if (row < rows) {
+      gadget_digits<ELL>(reduce_word(mask[((size_t)t * rows + row) * N + i0 + tx], rcK), rcK, base_log, d);
+    } else {
+#pragma unroll
+      for (int l = 0; l < ELL; ++l) d[l] = 0;
+    }
+#pragma unroll
+    for (int l = 0; l < ELL; ++l) tile[l][tx][k] = d[l];
+  }
+  __syncthreads();
+  const u64 q = rcK.q;
+  for (u32 k = ty; k < 32; k += 8) {
+    const u32 i = i0 + k;
+#pragma unroll
+    for (int l = 0; l < ELL; ++l) {
+      const int v = tile[l][k][tx];
+      D[(((size_t)u * N + i) * ELL + l) * N + j0 + tx] = (v < 0) ? q - (u64)(-v) : (u64)v;
+    }
+  }
+}
+
+// Key upload: NTT(KSK) words in A_hat slot order -> -N^-1 NTT(KSK), fully
+// reduced, with Shoup quotients: (k1, k1', k2, k2') (RNS) or (k, k') mod q.
+template <bool RNS>
+__global__ void ksk_finish_kernel(const u64* __restrict__ src, void* __restrict__ dst, size_t n, RingConst rc,
+                                  RnsConst rk, NInv ninv) {
+  for (size_t idx = (size_t)blockIdx.x * blockDim.x + threadIdx.x; idx < n; idx += (size_t)gridDim.x * blockDim.x) {
+    if constexpr (RNS) {
+      const uint2 x = reinterpret_cast<const uint2*>(src)[idx];
+      u32 a1 = sub_if32(sub_if32(x.x, 2 * rk.p1), rk.p1);
+      u32 a2 = sub_if32(sub_if32(x.y, 2 * rk.p2), rk.p2);
+      a1 = sub_if32(mul_shoup32(a1, ninv.n1, ninv.n1p, rk.p1), rk.p1);
+      a2 = sub_if32(mul_shoup32(a2, ninv.n2, ninv.n2p, rk.p2), rk.p2);
+      a1 = a1 ? rk.p1 - a1 : 0u;
+      a2 = a2 ? rk.p2 - a2 : 0u;
+      reinterpret_cast<uint4*>(dst)[idx] =
+          make_uint4(a1, (u32)(((u64)a1 << 32) / rk.p1), a2, (u32)(((u64)a2 << 32) / rk.p2));
+    } else {
+      u64 v = reduce_4q(src[idx], rc.q, rc.q2);
+      v = reduce_2q(mul_shoup(v, ninv.n64, ninv.n64p, rc.q), rc.q);
+      v = v ? rc.q - v : 0ull;
+      u64 rem = v, quo = 0;  // floor(v 2^64 / q) by long division
+      for (int b = 0; b < 64; ++b) {
+        rem <<= 1;
+        quo <<= 1;
+        if (rem >= rc.q) {
+          rem -= rc.q;
+          quo |= 1ull;
+        }
+      }
+      reinterpret_cast<ulonglong2*>(dst)[idx] = make_ulonglong2(v, quo);
+    }
+  }
+}
+
+// a mod p for a < 2^43 (a sum of at most 2^12 lazy products below 2p).
+__device__ __forceinline__ u32 reduce_acc32(u64 a, u32 p, u32 c32, u32 c32p) {
+  u32 lo = (u32)a;
+  lo = (lo >= 4 * p) ? lo - 4 * p : lo;
+  lo = sub_if32(sub_if32(lo, 2 * p), p);
+  const u32 hi = sub_if32(mul_shoup32((u32)(a >> 32), c32, c32p, p), p);
+  return sub_if32(lo + hi, p);
+}
+
+// Per NTT slot s and unit u: P_hat[u][c][s] = sum_{r < n*ell} D_hat[u][r][s] K_hat[r][c][s]
+// for c = 0 (A) and 1 (B).  A block covers 256 slots of UB units, so each key
+// entry loaded serves UB units.
+template <bool RNS, int UB>
+__global__ void __launch_bounds__(256)
+    pack_mac_kernel(const u64* __restrict__ Dhat, const void* __restrict__ khatv, u32 nr, u32 N, u32 units,
+                    u64* __restrict__ Phat, RingConst rc, RnsConst rk) {
+  const u32 s = blockIdx.x * blockDim.x + threadIdx.x;
+  const u32 u0 = blockIdx.y * UB;
+  if (s >= N) return;
+  const int nu = (int)min((u32)UB, units - u0);
+  if constexpr (RNS) {
+    const uint4* kh = reinterpret_cast<const uint4*>(khatv);
+    u64 acc[UB][4];
+#pragma unroll
+    for (int k = 0; k < UB; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0;
+#pragma unroll 2
+    for (u32 r = 0; r < nr; ++r) {
+      const uint4 ka = __ldg(&kh[((size_t)r * 2) * N + s]);
+      const uint4 kb = __ldg(&kh[((size_t)r * 2 + 1) * N + s]);
+#pragma unroll
+      for (int k = 0; k < UB; ++k) {
+        if (k < nu) {
+          const uint2 d = __ldg(reinterpret_cast<const uint2*>(Dhat) + ((size_t)(u0 + k) * nr + r) * N + s);
+          acc[k][0] += mul_shoup32(d.x, ka.x, ka.y, rk.p1);
+          acc[k][1] += mul_shoup32(d.y, ka.z, ka.w, rk.p2);
+          acc[k][2] += mul_shoup32(d.x, kb.x, kb.y, rk.p1);
+          acc[k][3] += mul_shoup32(d.y, kb.z, kb.w, rk.p2);
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < UB; ++k) {
+      if (k < nu) {
+        uint2* out = reinterpret_cast<uint2*>(Phat) + (size_t)(u0 + k) * 2 * N + s;
+        out[0] = make_uint2(reduce_acc32(acc[k][0], rk.p1, rk.c32a, rk.c32ap),
+                            reduce_acc32(acc[k][1], rk.p2, rk.c32b, rk.c32bp));
+        out[N] = make_uint2(reduce_acc32(acc[k][2], rk.p1, rk.c32a, rk.c32ap),
+                            reduce_acc32(acc[k][3], rk.p2, rk.c32b, rk.c32bp));
+      }
+    }
+  } else {
+    const ulonglong2* kh = reinterpret_cast<const ulonglong2*>(khatv);
+    const u64 q = rc.q, q4 = rc.q4;
+    u64 acc[UB][2];
+#pragma unroll
+    for (int k = 0; k < UB; ++k) acc[k][0] = acc[k][1] = 0;
+#pragma unroll 2
+    for (u32 r = 0; r < nr; ++r) {
+      const ulonglong2 ka = __ldg(&kh[((size_t)r * 2) * N + s]);
+      const ulonglong2 kb = __ldg(&kh[((size_t)r * 2 + 1) * N + s]);
+#pragma unroll
+      for (int k = 0; k < UB; ++k) {
+        if (k < nu) {
+          const u64 d = __ldg(&Dhat[((size_t)(u0 + k) * nr + r) * N + s]);
+          const u64 a = acc[k][0] + mul_shoup_lazy(d, ka.x, ka.y, q);  // each term < 4q, sum < 8q
+          const u64 b = acc[k][1] + mul_shoup_lazy(d, kb.x, kb.y, q);
+          acc[k][0] = (a >= q4) ? a - q4 : a;
+          acc[k][1] = (b >= q4) ? b - q4 : b;
+        }
+      }
+    }
+#pragma unroll
+    for (int k = 0; k < UB; ++k) {
+      if (k < nu) {
+        u64* out = Phat + (size_t)(u0 + k) * 2 * N + s;
+        out[0] = reduce_4q(acc[k][0], q, rc.q2);
+        out[N] = reduce_4q(acc[k][1], q, rc.q2);
+      }
+    }
+  }
+}
+
+// Inverse transform of P_hat[u][c] (c = 0: A, c = 1: B), + b_{gN+m} at
+// coefficient m of B for the group's rows, then the switch (or raw words).
+// Block b = u*2 + c of the chunk; u_base is the chunk's first unit.
+template <int LOGN, bool RNS, int MODE>
+__global__ void __launch_bounds__(Shape<LOGN>::TPB)
+    pack_finish_kernel(const u64* __restrict__ Phat, const u64* __restrict__ body, u32 rows, u32 G, u32 u_base,
+                       u32 units, void* __restrict__ out_a, void* __restrict__ out_b, RingConst rc, RnsConst rk,
+                       const void* __restrict__ tw0v, const void* __restrict__ twcv) {
+  using S = Shape<LOGN>;
+  using R = std::conditional_t<RNS, Ring2x32, Ring64>;
+  using W = typename R::Word;
+  using Tw = typename R::Tw;
+  constexpr int N = S::N;
+  constexpr int P = S::P;
+  constexpr int NP = S::NPASS;
+  extern __shared__ u64 smem[];
+  const int slot = threadIdx.x / P, p = threadIdx.x % P;
+  W* buf = reinterpret_cast<W*>(smem + slot * S::PADN);
+  const u32 b = blockIdx.x * S::SLOTS + slot;
+  const bool active = b < 2 * units;
+  W x[16];
+#pragma unroll
+  for (int r = 0; r < 16; ++r) {
+    if constexpr (RNS) x[r] = make_uint2(0u, 0u);
+    else x[r] = 0;
+  }
+  if (active) {
+    // words (r, r+1) of thread p sit together, as the input transform wrote them
+    if constexpr (RNS) {
+      const uint4* ap = reinterpret_cast<const uint4*>(Phat + (size_t)b * N);
+#pragma unroll
+      for (int r = 0; r < 16; r += 2) {
+        const uint4 v = ap[(r >> 1) * P + p];
+        x[r] = make_uint2(v.x, v.y);
+        x[r + 1] = make_uint2(v.z, v.w);
+      }
+    } else {
+      const ulonglong2* ap = reinterpret_cast<const ulonglong2*>(Phat + (size_t)b * N);
+#pragma unroll
+      for (int r = 0; r < 16; r += 2) {
+        const ulonglong2 v = ap[(r >> 1) * P + p];
+        x[r] = v.x;
+        x[r + 1] = v.y;
+      }
+    }
+  }
+  if constexpr (RNS) {
+    intt_regs<LOGN>(x, p, buf, reinterpret_cast<const Tw*>(tw0v), reinterpret_cast<const Tw*>(twcv),
+                    Ring2x32{rk.p1, rk.p2});
+  } else {
+    intt_regs<LOGN>(x, p, buf, reinterpret_cast<const Tw*>(tw0v), reinterpret_cast<const Tw*>(twcv),
+                    Ring64{rc.q, rc.q4});
+  }
+  if (!active) return;
+  const u32 u = u_base + b / 2, comp = b % 2;
+  const u32 t = u / G, g = u % G;
+  void* out = comp ? out_b : out_a;
+#pragma unroll
+  for (int e = 0; e < 16; ++e) {
+    const u32 pos = (u32)pass_pos<LOGN, NP - 1>(p, e);
+    const u32 row = g * N + pos;
+    const bool add_body = comp == 1 && row < rows;
+    const size_t o = (size_t)u * N + pos;
+    if constexpr (RNS) {
+      u32 c1 = sub_if32(x[e].x, rk.p1), c2 = sub_if32(x[e].y, rk.p2);
+      if (add_body) {
+        const uint2 rb = to_residues(reduce_word(body[(size_t)t * rows + row], rc), rk);
+        c1 = sub_if32(sub_if32(c1 + rb.x, 2 * rk.p1), rk.p1);
+        c2 = sub_if32(sub_if32(c2 + rb.y, 2 * rk.p2), rk.p2);
+      }
+      const u32 h = crt_digit(c1, c2, rk);
+      if constexpr (MODE == kOutSwitched) reinterpret_cast<u32*>(out)[o] = rns_modswitch(c1, h, rk);
+      else reinterpret_cast<u64*>(out)[o] = (u64)c1 + (u64)rk.p1 * h;
+    } else {
+      u64 c = reduce_4q(x[e], rc.q, rc.q2);
+      if (add_body) c = reduce_2q(c + reduce_word(body[(size_t)t * rows + row], rc), rc.q);
+      if constexpr (MODE == kOutSwitched) reinterpret_cast<u32*>(out)[o] = modswitch_word(c, rc);
+      else reinterpret_cast<u64*>(out)[o] = c;
+    }
+  }
+}
+
+}  // namespace phe
+
+// --------------------------------------------------------------------------
+// Host side
+// --------------------------------------------------------------------------
+namespace {
+
+using phe::Span;
+
+phe_status fail(phe_status s, const char* fmt, ...) {
+  char buf[384];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  phe::set_last_error(buf);
+  return s;
+}
+
+phe_status cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) return fail(PHE_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(PHE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
+
+struct DeviceGuard {
+  int prev = -1;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(int dev) {
+    err = cudaGetDevice(&prev);
+    if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    if (prev >= 0) cudaSetDevice(prev);
+  }
+};
+
+constexpr int kMacUnits = 8;                        // units per pack_mac_kernel block
+constexpr uint64_t kPackScratchBytes = 2ull << 30;  // digit rows in flight per phe_pack chunk
+
+cudaError_t launch_decompose(const phe_ctx* c, const phe_ksk* k, const u64* mask, u32 rows, u32 G, u32 u_base,
+                             u32 cu, u64* D, cudaStream_t s) {
+  const u32 N = c->prm.N;
+  phe::RingConst rcK = c->rc;
+  rcK.log2_qout = k->base_log * k->ell;
+  const dim3 grid(N / 32, N / 32, cu), block(32, 8);
+  switch (k->ell) {
+    case 1: phe::pack_decompose_kernel<1><<<grid, block, 0, s>>>(mask, rows, N, G, u_base, k->base_log, rcK, D); break;
+    case 2: phe::pack_decompose_kernel<2><<<grid, block, 0, s>>>(mask, rows, N, G, u_base, k->base_log, rcK, D); break;
+    case 3: phe::pack_decompose_kernel<3><<<grid, block, 0, s>>>(mask, rows, N, G, u_base, k->base_log, rcK, D); break;
+    default: phe::pack_decompose_kernel<4><<<grid, block, 0, s>>>(mask, rows, N, G, u_base, k->base_log, rcK, D); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_mac(const phe_ctx* c, const phe_ksk* k, const u64* Dhat, u32 cu, u64* Phat, cudaStream_t s) {
+  const u32 N = c->prm.N, nr = k->n * k->ell;
+  const dim3 grid(N / 256, (cu + kMacUnits - 1) / kMacUnits);
+  if (c->rns) phe::pack_mac_kernel<true, kMacUnits><<<grid, 256, 0, s>>>(Dhat, k->khat, nr, N, cu, Phat, c->rc, c->rk);
+  else phe::pack_mac_kernel<false, kMacUnits><<<grid, 256, 0, s>>>(Dhat, k->khat, nr, N, cu, Phat, c->rc, c->rk);
+  return cudaGetLastError();
+}
+
+template <int LOGN, bool RNS, int MODE>
+cudaError_t finish_one(const phe_ctx* c, const u64* Phat, const u64* body, u32 rows, u32 G, u32 u_base, u32 cu,
+                       void* oa, void* ob, cudaStream_t s) {
+  using S = phe::Shape<LOGN>;
+  const size_t smem = phe::lwedot_smem(LOGN);
+  auto kern = phe::pack_finish_kernel<LOGN, RNS, MODE>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const phe::Tables& tab = RNS ? c->tab32 : c->tab;
+  const u32 blocks = (2 * cu + S::SLOTS - 1) / S::SLOTS;
+  kern<<<blocks, S::TPB, smem, s>>>(Phat, body, rows, G, u_base, cu, oa, ob, c->rc, c->rk, tab.inv_0, tab.inv_c);
+  return cudaGetLastError();
+}
+
+template <int LOGN>
+cudaError_t finish_by_form(const phe_ctx* c, int mode, const u64* Phat, const u64* body, u32 rows, u32 G, u32 u_base,
+                           u32 cu, void* oa, void* ob, cudaStream_t s) {
+  if (c->rns) {
+    return mode == phe::kOutRaw ? finish_one<LOGN, true, phe::kOutRaw>(c, Phat, body, rows, G, u_base, cu, oa, ob, s)
+                                : finish_one<LOGN, true, phe::kOutSwitched>(c, Phat, body, rows, G, u_base, cu, oa, ob, s);
+  }
+  return mode == phe::kOutRaw ? finish_one<LOGN, false, phe::kOutRaw>(c, Phat, body, rows, G, u_base, cu, oa, ob, s)
+                              : finish_one<LOGN, false, phe::kOutSwitched>(c, Phat, body, rows, G, u_base, cu, oa, ob, s);
+}
+
+cudaError_t launch_finish(const phe_ctx* c, int mode, const u64* Phat, const u64* body, u32 rows, u32 G, u32 u_base,
+                          u32 cu, void* oa, void* ob, cudaStream_t s) {
+  switch (c->logn) {
+    case 8: return finish_by_form<8>(c, mode, Phat, body, rows, G, u_base, cu, oa, ob, s);
+    case 9: return finish_by_form<9>(c, mode, Phat, body, rows, G, u_base, cu, oa, ob, s);
+    case 10: return finish_by_form<10>(c, mode, Phat, body, rows, G, u_base, cu, oa, ob, s);
+    case 11: return finish_by_form<11>(c, mode, Phat, body, rows, G, u_base, cu, oa, ob, s);
+    case 12: return finish_by_form<12>(c, mode, Phat, body, rows, G, u_base, cu, oa, ob, s);
+    case 13: return finish_by_form<13>(c, mode, Phat, body, rows, G, u_base, cu, oa, ob, s);
+    default: return cudaErrorInvalidValue;
+  }
+}
+
+// The packing of T x rows LWE ciphertexts on `s`, in chunks of units.
+cudaError_t pack_device(phe_ctx* c, const phe_ksk* k, u32 T, u32 rows, const u64* mask, const u64* body, void* oa,
+                        void* ob, int mode, cudaStream_t s) {
+  const u32 N = c->prm.N, nr = k->n * k->ell;
+  const u32 G = (rows + N - 1) / N;
+  const u64 units = (u64)T * G;
+  const u64 unit_bytes = (u64)nr * N * sizeof(u64);
+  const u32 per = (u32)std::max<u64>(1, std::min<u64>(units, kPackScratchBytes / unit_bytes));
+  Span call(c, phe::kKPackCall, s);
+  u64* D = nullptr;
+  u64* Phat = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&D, (size_t)per * unit_bytes, s);
+  if (e != cudaSuccess) return e;
+  e = cudaMallocAsync((void**)&Phat, (size_t)per * 2 * N * sizeof(u64), s);
+  for (u64 u0 = 0; u0 < units && e == cudaSuccess; u0 += per) {
+    const u32 cu = (u32)std::min<u64>(per, units - u0);
+    {
+      Span sp(c, phe::kKPackDecompose, s);
+      e = launch_decompose(c, k, mask, rows, G, (u32)u0, cu, D, s);
+    }
+    if (e == cudaSuccess) {
+      Span sp(c, phe::kKInputNtt, s);
+      phe::NttJob nj{D, D, cu * nr, nullptr};
+      e = phe::launch_input_ntt(c, &nj, 1, s);
+    }
+    if (e == cudaSuccess) {
+      Span sp(c, phe::kKPackMac, s);
+      e = launch_mac(c, k, D, cu, Phat, s);
+    }
+    if (e == cudaSuccess) {
+      Span sp(c, phe::kKPackFinish, s);
+      e = launch_finish(c, mode, Phat, body, rows, G, (u32)u0, cu, oa, ob, s);
+    }
+  }
+  cudaError_t f1 = Phat ? cudaFreeAsync(Phat, s) : cudaSuccess;
+  cudaError_t f2 = cudaFreeAsync(D, s);
+  if (e != cudaSuccess) return e;
+  return f1 != cudaSuccess ? f1 : f2;
+}
+
+phe_status check_ksk(const phe_ctx* c, const phe_ksk* k, const char* who) {
+  if (!c || !k) return fail(PHE_EINVAL, "%s: null handle", who);
+  if (k->ctx != c) return fail(PHE_EINVAL, "%s: key-switching key belongs to another context", who);
+  return PHE_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+phe_status phe_ksk_upload(phe_ctx* c, const uint64_t* h_ka, const uint64_t* h_kb, uint32_t n, uint32_t base_log,
+                          uint32_t ell, phe_ksk** out) {
+  if (!c || !h_ka || !h_kb || !out) return fail(PHE_EINVAL, "phe_ksk_upload: null argument");
+  *out = nullptr;
+  const u32 N = c->prm.N;
+  if (n != N) return fail(PHE_EINVAL, "phe_ksk_upload: n=%u must equal N=%u (LWE outputs of dimension N)", n, N);
+  if (ell < 1 || ell > 4 || base_log < 1 || base_log > 30 || base_log * ell > 32)
+    return fail(PHE_EINVAL, "phe_ksk_upload: base_log=%u ell=%u (need 1<=ell<=4, 1<=base_log<=30, product<=32)",
+                base_log, ell);
+  DeviceGuard g(c->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  phe_ksk* k = new (std::nothrow) phe_ksk;
+  if (!k) return fail(PHE_ENOMEM, "phe_ksk_upload: host allocation");
+  k->ctx = c;
+  k->n = n;
+  k->base_log = base_log;
+  k->ell = ell;
+  const size_t nr = (size_t)n * ell, words = nr * 2 * N;
+  k->bytes = words * 16;
+  u64* tmp = nullptr;
+  cudaError_t e = cudaMalloc((void**)&tmp, words * sizeof(u64));
+  if (e == cudaSuccess) e = cudaMalloc(&k->khat, k->bytes);
+  // rows r = i*ell + l of KA and KB interleaved: tmp[r][0] = KA_r, tmp[r][1] = KB_r
+  if (e == cudaSuccess)
+    e = cudaMemcpy2D(tmp, 2 * N * sizeof(u64), h_ka, N * sizeof(u64), N * sizeof(u64), nr, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess)
+    e = cudaMemcpy2D(tmp + N, 2 * N * sizeof(u64), h_kb, N * sizeof(u64), N * sizeof(u64), nr,
+                     cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) {
+    phe::NttJob nj{tmp, tmp, (u32)(nr * 2), nullptr};
+    e = phe::launch_input_ntt(c, &nj, 1, 0);
+  }
+  if (e == cudaSuccess) {
+    const int blocks = (int)std::min<size_t>((words + 255) / 256, (size_t)c->num_sms * 8);
+    if (c->rns) phe::ksk_finish_kernel<true><<<blocks, 256>>>(tmp, k->khat, words, c->rc, c->rk, c->ninv);
+    else phe::ksk_finish_kernel<false><<<blocks, 256>>>(tmp, k->khat, words, c->rc, c->rk, c->ninv);
+    e = cudaGetLastError();
+  }
+  if (e == cudaSuccess) e = cudaDeviceSynchronize();
+  if (tmp) cudaFree(tmp);
+  if (e != cudaSuccess) {
+    if (k->khat) cudaFree(k->khat);
+    delete k;
+    return cuda_fail(e, "phe_ksk_upload");
+  }
+  *out = k;
+  return PHE_OK;
+}
+
+void phe_ksk_free(phe_ksk* k) {
+  if (!k) return;
+  DeviceGuard g(k->ctx->device);
+  if (k->khat) cudaFree(k->khat);
+  delete k;
+}
+
+uint64_t phe_ksk_device_bytes(const phe_ksk* k) { return k ? k->bytes : 0; }
+
+phe_status phe_pack(phe_ctx* c, const phe_ksk* k, uint32_t T, uint32_t rows, const uint64_t* d_lwe_mask,
+                    const uint64_t* d_lwe_body, void* d_out_a, void* d_out_b, uint32_t flags, void* stream) {
+  phe_status st = check_ksk(c, k, "phe_pack");
+  if (st != PHE_OK) return st;
+  if (flags != PHE_OUT_SWITCHED && flags != PHE_OUT_RAW) return fail(PHE_EINVAL, "phe_pack: flags=%u", flags);
+  if (T == 0 || rows == 0) return PHE_OK;
+  if (!d_lwe_mask || !d_lwe_body || !d_out_a || !d_out_b) return fail(PHE_EINVAL, "phe_pack: null buffer");
+  const u32 G = (rows + c->prm.N - 1) / c->prm.N;
+  if ((u64)T * G > (1u << 24)) return fail(PHE_EINVAL, "phe_pack: T*ceil(rows/N)=%llu exceeds 2^24",
+                                           (unsigned long long)((u64)T * G));
+  DeviceGuard g(c->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  cudaError_t e = pack_device(c, k, T, rows, reinterpret_cast<const u64*>(d_lwe_mask),
+                              reinterpret_cast<const u64*>(d_lwe_body), d_out_a, d_out_b,
+                              flags == PHE_OUT_RAW ? phe::kOutRaw : phe::kOutSwitched, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "phe_pack");
+  return PHE_OK;
+}
+
+phe_status phe_matmul_packed(phe_ctx* c, const phe_weights* w, const phe_ksk* k, int dir, uint32_t T,
+                             const uint64_t* d_in_mask, const uint64_t* d_in_body, void* d_out_a, void* d_out_b,
+                             uint32_t flags, void* stream) {
+  phe_status st = check_ksk(c, k, "phe_matmul_packed");
+  if (st != PHE_OK) return st;
+  uint32_t rows = 0, cols = 0, L = 0;
+  if (!w || w->ctx != c) return fail(PHE_EINVAL, "phe_matmul_packed: weights missing or of another context");
+  if ((st = phe_weights_shape(w, dir, &rows, &cols, &L)) != PHE_OK) return st;
+  if (flags != PHE_OUT_SWITCHED && flags != PHE_OUT_RAW)
+    return fail(PHE_EINVAL, "phe_matmul_packed: flags=%u", flags);
+  if (T == 0) return PHE_OK;
+  if (!d_in_mask || !d_in_body || !d_out_a || !d_out_b) return fail(PHE_EINVAL, "phe_matmul_packed: null buffer");
+  const u32 N = c->prm.N, G = (rows + N - 1) / N;
+  DeviceGuard g(c->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  cudaStream_t s = (cudaStream_t)stream;
+  // raw LWE outputs of a chunk of tokens, then their packing
+  const u64 tok_bytes = (u64)rows * (N + 1) * sizeof(u64);
+  const u32 per = (u32)std::max<u64>(1, std::min<u64>(T, kPackScratchBytes / tok_bytes));
+  const size_t osz = flags == PHE_OUT_RAW ? sizeof(u64) : sizeof(u32);
+  u64* raw = nullptr;
+  cudaError_t e = cudaMallocAsync((void**)&raw, (size_t)per * tok_bytes, s);
+  if (e != cudaSuccess) return cuda_fail(e, "phe_matmul_packed: scratch");
+  u64* raw_body = raw + (size_t)per * rows * N;
+  for (u32 t0 = 0; t0 < T && st == PHE_OK; t0 += per) {
+    const u32 tn = std::min(per, T - t0);
+    const size_t in_off = (size_t)t0 * L * N, out_off = (size_t)t0 * G * N * osz;
+    st = phe_matmul(c, w, dir, tn, d_in_mask + in_off, d_in_body + in_off, raw, raw_body, PHE_OUT_RAW, stream);
+    if (st == PHE_OK)
+      st = phe_pack(c, k, tn, rows, reinterpret_cast<const uint64_t*>(raw),
+                    reinterpret_cast<const uint64_t*>(raw_body), static_cast<char*>(d_out_a) + out_off,
+                    static_cast<char*>(d_out_b) + out_off, flags, stream);
+  }
+  e = cudaFreeAsync(raw, s);
+  if (st != PHE_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "phe_matmul_packed: free");
+  return PHE_OK;
+}
+
+phe_status phe_matmul_packed_host(phe_ctx* c, const phe_weights* w, const phe_ksk* k, int dir, uint32_t T,
+                                  const uint64_t* h_in_mask, const uint64_t* h_in_body, void* h_out_a,
+                                  void* h_out_b, uint32_t flags, uint32_t tok_chunk, void* stream) {
+  phe_status st = check_ksk(c, k, "phe_matmul_packed_host");
+  if (st != PHE_OK) return st;
+  uint32_t rows = 0, cols = 0, L = 0;
+  if (!w || w->ctx != c) return fail(PHE_EINVAL, "phe_matmul_packed_host: weights missing or of another context");
+  if ((st = phe_weights_shape(w, dir, &rows, &cols, &L)) != PHE_OK) return st;
+  if (flags != PHE_OUT_SWITCHED && flags != PHE_OUT_RAW)
+    return fail(PHE_EINVAL, "phe_matmul_packed_host: flags=%u", flags);
+  if (T == 0) return PHE_OK;
+  if (!h_in_mask || !h_in_body || !h_out_a || !h_out_b) return fail(PHE_EINVAL, "phe_matmul_packed_host: null buffer");
+  DeviceGuard g(c->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  const u32 N = c->prm.N, G = (rows + N - 1) / N;
+  const size_t osz = flags == PHE_OUT_RAW ? sizeof(u64) : sizeof(u32);
+  const size_t in_tok = (size_t)L * N * sizeof(u64), out_tok = (size_t)G * N * osz;
+  const u32 tc = std::max(1u, std::min(tok_chunk ? tok_chunk : 8u, T));
+  cudaStream_t caller = (cudaStream_t)stream;
+  cudaError_t e = cudaSuccess;
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i)
+    if (!c->side[i]) e = cudaStreamCreateWithFlags(&c->side[i], cudaStreamNonBlocking);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaStreamCreate");
+  cudaEvent_t ev = nullptr;
+  if ((e = cudaEventCreateWithFlags(&ev, cudaEventDisableTiming)) != cudaSuccess) return cuda_fail(e, "cudaEventCreate");
+  e = cudaEventRecord(ev, caller);
+  for (int i = 0; i < 2 && e == cudaSuccess; ++i) e = cudaStreamWaitEvent(c->side[i], ev, 0);
+  // two buffer sets on the context's two side streams: the copies of one
+  // chunk overlap the kernels of the next
+  struct Buf { u64 *a = nullptr, *b = nullptr; char *oa = nullptr, *ob = nullptr; } buf[2];
+  const u32 nchunks = (T + tc - 1) / tc;
+  for (int i = 0; i < 2 && i < (int)nchunks && e == cudaSuccess; ++i) {
+    cudaStream_t s = c->side[i];
+    if ((e = cudaMallocAsync((void**)&buf[i].a, tc * in_tok, s)) != cudaSuccess) break;
+    if ((e = cudaMallocAsync((void**)&buf[i].b, tc * in_tok, s)) != cudaSuccess) break;
+    if ((e = cudaMallocAsync((void**)&buf[i].oa, tc * out_tok, s)) != cudaSuccess) break;
+    e = cudaMallocAsync((void**)&buf[i].ob, tc * out_tok, s);
+  }
+  for (u32 n = 0; n < nchunks && e == cudaSuccess && st == PHE_OK; ++n) {
+    const u32 t0 = n * tc, tn = std::min(tc, T - t0);
+    cudaStream_t s = c->side[n % 2];
+    Buf& B = buf[n % 2];
+    if ((e = cudaMemcpyAsync(B.a, reinterpret_cast<const char*>(h_in_mask) + t0 * in_tok, tn * in_tok,
+                             cudaMemcpyHostToDevice, s)) != cudaSuccess) break;
+    if ((e = cudaMemcpyAsync(B.b, reinterpret_cast<const char*>(h_in_body) + t0 * in_tok, tn * in_tok,
+                             cudaMemcpyHostToDevice, s)) != cudaSuccess) break;
+    st = phe_matmul_packed(c, w, k, dir, tn, reinterpret_cast<const uint64_t*>(B.a),
+                           reinterpret_cast<const uint64_t*>(B.b), B.oa, B.ob, flags, s);
+    if (st != PHE_OK) break;
+    if ((e = cudaMemcpyAsync(static_cast<char*>(h_out_a) + t0 * out_tok, B.oa, tn * out_tok, cudaMemcpyDeviceToHost,
+                             s)) != cudaSuccess) break;
+    e = cudaMemcpyAsync(static_cast<char*>(h_out_b) + t0 * out_tok, B.ob, tn * out_tok, cudaMemcpyDeviceToHost, s);
+  }
+  for (int i = 0; i < 2; ++i) {
+    cudaStream_t s = c->side[i];
+    if (buf[i].a) cudaFreeAsync(buf[i].a, s);
+    if (buf[i].b) cudaFreeAsync(buf[i].b, s);
+    if (buf[i].oa) cudaFreeAsync(buf[i].oa, s);
+    if (buf[i].ob) cudaFreeAsync(buf[i].ob, s);
+    cudaError_t e2 = cudaStreamSynchronize(s);
+    if (e == cudaSuccess) e = e2;
+  }
+  cudaEventDestroy(ev);
+  if (st != PHE_OK) return st;
+  if (e != cudaSuccess) return cuda_fail(e, "phe_matmul_packed_host");
+  return PHE_OK;
+}
+
+}  // extern "C"

@@ -115,6 +115,12 @@ SIGNATURES = {
     "phe_server_destroy": (None, [_vp]),
     "phe_matmul_seeded": (_i32, [_vp, _vp, _i32, _u32, _vp, _vp, _vp, _vp, _u32, _vp]),
     "phe_expand_masks": (_i32, [_vp, _vp, _u32, _vp, _vp]),
+    "phe_ksk_upload": (_i32, [_vp, _vp, _vp, _u32, _u32, _u32, ctypes.POINTER(_vp)]),
+    "phe_ksk_free": (None, [_vp]),
+    "phe_ksk_device_bytes": (_u64, [_vp]),
+    "phe_pack": (_i32, [_vp, _vp, _u32, _u32, _vp, _vp, _vp, _vp, _u32, _vp]),
+    "phe_matmul_packed": (_i32, [_vp, _vp, _vp, _i32, _u32, _vp, _vp, _vp, _vp, _u32, _vp]),
+    "phe_matmul_packed_host": (_i32, [_vp, _vp, _vp, _i32, _u32, _vp, _vp, _vp, _vp, _u32, _u32, _vp]),
 }
 
 _lib = None
@@ -372,3 +378,42 @@ def phe_matmul_seeded(ctx, w, direction: int, T: int, in_seeds, in_body, out_mas
 
 def phe_expand_masks(ctx, seeds, n: int, masks, stream=None) -> None:
     _check(lib().phe_expand_masks(ctx, _dptr(seeds), n, _dptr(masks), _stream(stream)))
+
+
+def phe_ksk_upload(ctx, KA, KB, base_log: int, ell: int):
+    """KA, KB: host uint64 arrays [n][ell][N] (the key-switching key, words mod q)."""
+    import numpy as np
+    KA = np.ascontiguousarray(np.asarray(KA, dtype=np.uint64))
+    KB = np.ascontiguousarray(np.asarray(KB, dtype=np.uint64))
+    if KA.shape != KB.shape or KA.ndim != 3 or KA.shape[1] != ell:
+        raise ValueError(f"KA/KB must both be [n][{ell}][N], got {KA.shape} and {KB.shape}")
+    out = _vp()
+    _check(lib().phe_ksk_upload(ctx, KA.ctypes.data, KB.ctypes.data, KA.shape[0], base_log, ell,
+                                ctypes.byref(out)))
+    return out
+
+
+def phe_ksk_free(k) -> None:
+    lib().phe_ksk_free(k)
+
+
+def phe_ksk_device_bytes(k) -> int:
+    return int(lib().phe_ksk_device_bytes(k))
+
+
+def phe_pack(ctx, k, T: int, rows: int, lwe_mask, lwe_body, out_a, out_b, flags: int = PHE_OUT_SWITCHED,
+             stream=None) -> None:
+    _check(lib().phe_pack(ctx, k, T, rows, _dptr(lwe_mask), _dptr(lwe_body), _dptr(out_a), _dptr(out_b), flags,
+                          _stream(stream)))
+
+
+def phe_matmul_packed(ctx, w, k, direction: int, T: int, in_mask, in_body, out_a, out_b,
+                      flags: int = PHE_OUT_SWITCHED, stream=None) -> None:
+    _check(lib().phe_matmul_packed(ctx, w, k, direction, T, _dptr(in_mask), _dptr(in_body), _dptr(out_a),
+                                   _dptr(out_b), flags, _stream(stream)))
+
+
+def phe_matmul_packed_host(ctx, w, k, direction: int, T: int, h_in_mask, h_in_body, h_out_a, h_out_b,
+                           flags: int = PHE_OUT_SWITCHED, tok_chunk: int = 8, stream=None) -> None:
+    _check(lib().phe_matmul_packed_host(ctx, w, k, direction, T, _hptr(h_in_mask), _hptr(h_in_body),
+                                        _hptr(h_out_a), _hptr(h_out_b), flags, tok_chunk, _stream(stream)))

@@ -70,8 +70,13 @@ def test_null_arguments_are_rejected(L):
     assert L.phe_modswitch(None, None, None, 0, None) == phe.PHE_EINVAL
     assert L.phe_weights_upload(None, None, 1, 1, 1, None, None) == phe.PHE_EINVAL
     assert phe.phe_weights_device_bytes(None) == 0
+    assert L.phe_ksk_upload(None, None, None, 0, 26, 1, None) == phe.PHE_EINVAL
+    assert L.phe_pack(None, None, 1, 1, None, None, None, None, 0, None) == phe.PHE_EINVAL
+    assert L.phe_matmul_packed(None, None, None, 0, 1, None, None, None, None, 0, None) == phe.PHE_EINVAL
+    assert phe.phe_ksk_device_bytes(None) == 0
     L.phe_ctx_destroy(None)
     L.phe_weights_free(None)
+    L.phe_ksk_free(None)
 
 
 @pytest.mark.parametrize("q,rns,msg", [

@@ -1,0 +1,210 @@
+"""GPU: output packing (Sec. 3.2 KeySwitching and Rotate, Eq. (pack_rotate))
+against the oracle, bit for bit.
+
+  - phe_pack on given LWE ciphertexts equals the oracle's packing sum
+    (raw words mod q, and after the switch), for both moduli, several gadget
+    shapes, ragged row groups and several tokens;
+  - at N = 4096, sampled coefficients of full-size packs match the oracle's
+    coefficient-by-coefficient evaluation;
+  - phe_matmul_packed on real encryptions equals the oracle composition
+    Eq. (LWEdot) -> packing -> switch, and decrypts to (W x) mod t;
+  - token chunking inside phe_matmul_packed does not change the result.
+"""
+import numpy as np
+import pytest
+
+import synth
+from paper_2505_07329_b300 import phe
+from tests.gpu_helpers import to_dev_u64
+
+pytestmark = pytest.mark.gpu
+
+MODULI = {"prime": (synth.Q60, None), "rns": (synth.Q_RNS, (synth.RNS_P1, synth.RNS_P2))}
+
+
+@pytest.fixture(scope="module")
+def ctxs():
+    from paper_2505_07329_b300 import build
+    build.build()
+    made = {}
+
+    def get(N, modulus):
+        key = (N, modulus)
+        if key not in made:
+            q, rns = MODULI[modulus]
+            made[key] = phe.phe_ctx_create(N, q, 32, 0, rns=rns)
+        return made[key]
+    yield get
+    for c in made.values():
+        phe.phe_ctx_destroy(c)
+
+
+def _rng(seed):
+    return np.random.Generator(np.random.PCG64(seed))
+
+
+def _gpu_pack(ctx, k, masks, bodies, N, flags):
+    import torch
+    T, rows = bodies.shape
+    G = (rows + N - 1) // N
+    odt = torch.int64 if flags == phe.PHE_OUT_RAW else torch.int32
+    oa = torch.empty((T, G, N), dtype=odt, device="cuda")
+    ob = torch.empty((T, G, N), dtype=odt, device="cuda")
+    phe.phe_pack(ctx, k, T, rows, to_dev_u64(masks), to_dev_u64(bodies), oa, ob, flags)
+    torch.cuda.synchronize()
+    if flags == phe.PHE_OUT_RAW:
+        return oa.cpu().numpy().view(np.uint64), ob.cpu().numpy().view(np.uint64)
+    return (oa.cpu().numpy().view(np.uint32).astype(np.uint64), ob.cpu().numpy().view(np.uint32).astype(np.uint64))
+
+
+@pytest.mark.parametrize("modulus,base_log,ell", [("rns", 26, 1), ("prime", 26, 1), ("rns", 13, 2),
+                                                  ("prime", 10, 3), ("rns", 8, 4)])
+def test_pack_matches_oracle(orc, ctxs, modulus, base_log, ell):
+    N, T, rows = 256, 2, 300          # two row groups per token, the second ragged (44 rows)
+    q = MODULI[modulus][0]
+    ctx = ctxs(N, modulus)
+    g = _rng(100 + ell)
+    KA = g.integers(0, q, (N, ell, N), dtype=np.uint64)
+    KB = g.integers(0, q, (N, ell, N), dtype=np.uint64)
+    masks = g.integers(0, q, (T, rows, N), dtype=np.uint64)
+    bodies = g.integers(0, q, (T, rows), dtype=np.uint64)
+    masks[0, 0, :4] = [0, q - 1, q // 2, (q + 1) // 2]   # switch edges
+    k = phe.phe_ksk_upload(ctx, KA, KB, base_log, ell)
+    try:
+        raw_a, raw_b = _gpu_pack(ctx, k, masks, bodies, N, phe.PHE_OUT_RAW)
+        sw_a, sw_b = _gpu_pack(ctx, k, masks, bodies, N, phe.PHE_OUT_SWITCHED)
+    finally:
+        phe.phe_ksk_free(k)
+    for t in range(T):
+        for grp in range(2):
+            a = masks[t, grp * N:(grp + 1) * N]
+            b = bodies[t, grp * N:(grp + 1) * N]
+            ea, eb = orc.pack_coeffs(a, b, KA, KB, q, base_log, ell, np.arange(N))
+            assert np.array_equal(raw_a[t, grp], ea) and np.array_equal(raw_b[t, grp], eb), (t, grp)
+            assert np.array_equal(sw_a[t, grp], orc.modswitch(ea, q, 32))
+            assert np.array_equal(sw_b[t, grp], orc.modswitch(eb, q, 32))
+
+
+@pytest.mark.parametrize("modulus", ["rns", "prime"])
+def test_pack_full_size_sampled(orc, ctxs, modulus):
+    N, T, rows = 4096, 2, 4096 + 100
+    q = MODULI[modulus][0]
+    ctx = ctxs(N, modulus)
+    g = _rng(7)
+    KA = g.integers(0, q, (N, 1, N), dtype=np.uint64)
+    KB = g.integers(0, q, (N, 1, N), dtype=np.uint64)
+    masks = g.integers(0, q, (T, rows, N), dtype=np.uint64)
+    bodies = g.integers(0, q, (T, rows), dtype=np.uint64)
+    k = phe.phe_ksk_upload(ctx, KA, KB, 26, 1)
+    try:
+        ga, gb = _gpu_pack(ctx, k, masks, bodies, N, phe.PHE_OUT_SWITCHED)
+    finally:
+        phe.phe_ksk_free(k)
+    rs = np.array([0, 1, 99, 100, 2047, 4095])
+    for t, grp in [(0, 0), (1, 1)]:
+        a = masks[t, grp * N:(grp + 1) * N]
+        b = bodies[t, grp * N:(grp + 1) * N]
+        ea, eb = orc.pack_coeffs(a, b, KA, KB, q, 26, 1, rs)
+        assert np.array_equal(ga[t, grp, rs], orc.modswitch(ea, q, 32)), (t, grp)
+        assert np.array_equal(gb[t, grp, rs], orc.modswitch(eb, q, 32)), (t, grp)
+
+
+def _encrypted_inputs(orc, N, T, d, q, seed):
+    g = _rng(seed)
+    S = g.integers(-1, 2, N)
+    L = synth.blocks(d, N)
+    A = g.integers(0, q, (T, L, N), dtype=np.uint64)
+    E = np.rint(g.normal(0, synth.SIGMA, (T, L, N))).astype(np.int64)
+    X = g.integers(-127, 128, (T, d)).astype(np.int8)
+    B = orc.encrypt_vectors(A, S, E, X, q, q // synth.T_PLAIN)
+    return S, A, B, X
+
+
+@pytest.mark.parametrize("modulus", ["rns", "prime"])
+@pytest.mark.parametrize("direction", [phe.PHE_FWD, phe.PHE_BWD])
+def test_matmul_packed_end_to_end(orc, ctxs, modulus, direction):
+    import torch
+    N, T, t = 256, 3, synth.T_PLAIN
+    q = MODULI[modulus][0]
+    ctx = ctxs(N, modulus)
+    W = synth.weights(300, 290, seed=21)          # fwd: 300 rows (2 groups) of 290; bwd: 290 rows of 300
+    Wd = W if direction == phe.PHE_FWD else np.ascontiguousarray(W.T)
+    rows, cols = Wd.shape
+    S, A, B, X = _encrypted_inputs(orc, N, T, cols, q, 22 + direction)
+    g = _rng(23)
+    KA = g.integers(0, q, (N, 1, N), dtype=np.uint64)
+    E = np.rint(g.normal(0, synth.SIGMA, (N, 1, N))).astype(np.int64)
+    KB = orc.ksk_encrypt(KA, E, S, S, q, 26, 1)
+    w = phe.phe_weights_upload(ctx, W)
+    k = phe.phe_ksk_upload(ctx, KA, KB, 26, 1)
+    G = (rows + N - 1) // N
+    try:
+        oa = torch.empty((T, G, N), dtype=torch.int32, device="cuda")
+        ob = torch.empty((T, G, N), dtype=torch.int32, device="cuda")
+        phe.phe_matmul_packed(ctx, w, k, direction, T, to_dev_u64(A), to_dev_u64(B), oa, ob)
+        torch.cuda.synchronize()
+    finally:
+        phe.phe_ksk_free(k)
+        phe.phe_weights_free(w)
+    ga = oa.cpu().numpy().view(np.uint32).astype(np.uint64)
+    gb = ob.cpu().numpy().view(np.uint32).astype(np.uint64)
+    la, lb = orc.lwedot_all(Wd, A, B, q)
+    y = X.astype(np.int64) @ Wd.astype(np.int64).T
+    Sq = np.array([s % (1 << 32) for s in S.tolist()], dtype=np.uint64)
+    for tok in range(T):
+        for grp in range(G):
+            m = min(N, rows - grp * N)
+            ea, eb = orc.pack_coeffs(la[tok, grp * N:grp * N + m], lb[tok, grp * N:grp * N + m], KA, KB, q, 26, 1,
+                                     np.arange(N))
+            assert np.array_equal(ga[tok, grp], orc.modswitch(ea, q, 32)), (tok, grp)
+            assert np.array_equal(gb[tok, grp], orc.modswitch(eb, q, 32)), (tok, grp)
+            AS = orc.negacyclic_mul(ga[tok, grp], Sq, 1 << 32)
+            ph = [(int(bv) - int(av)) % (1 << 32) for bv, av in zip(gb[tok, grp], AS)]
+            got = [orc.decode(v, 1 << 32, t) for v in ph]
+            want = [((int(v) + t // 2) % t) - t // 2 for v in y[tok, grp * N:grp * N + m]] + [0] * (N - m)
+            assert got == want, (tok, grp)
+
+
+def test_matmul_packed_token_chunks_agree(ctxs):
+    # 8192 raw rows x (N + 1) words x 8 B = 268 MB per token: the 2 GiB
+    # scratch holds 8 tokens, so 11 tokens run as two chunks.
+    import torch
+    N, T = 4096, 11
+    ctx = ctxs(N, "rns")
+    q = synth.Q_RNS
+    W = synth.weights(8192, 2048, seed=31)
+    g = _rng(32)
+    KA = g.integers(0, q, (N, 1, N), dtype=np.uint64)
+    KB = g.integers(0, q, (N, 1, N), dtype=np.uint64)
+    A = torch.tensor(g.integers(0, q, (T, 1, N), dtype=np.uint64).view(np.int64), device="cuda")
+    B = torch.tensor(g.integers(0, q, (T, 1, N), dtype=np.uint64).view(np.int64), device="cuda")
+    w = phe.phe_weights_upload(ctx, W, phe.PHE_DIR_FWD_BIT)
+    k = phe.phe_ksk_upload(ctx, KA, KB, 26, 1)
+    try:
+        oa = torch.empty((T, 2, N), dtype=torch.int32, device="cuda")
+        ob = torch.empty_like(oa)
+        phe.phe_matmul_packed(ctx, w, k, phe.PHE_FWD, T, A, B, oa, ob)
+        ra = torch.empty_like(oa)
+        rb = torch.empty_like(oa)
+        raw_m = torch.empty((1, 8192, N), dtype=torch.int64, device="cuda")
+        raw_b = torch.empty((1, 8192), dtype=torch.int64, device="cuda")
+        for tok in range(T):   # one token at a time, through the two public steps
+            phe.phe_matmul(ctx, w, phe.PHE_FWD, 1, A[tok:tok + 1], B[tok:tok + 1], raw_m, raw_b, phe.PHE_OUT_RAW)
+            phe.phe_pack(ctx, k, 1, 8192, raw_m, raw_b, ra[tok:tok + 1], rb[tok:tok + 1])
+        torch.cuda.synchronize()
+    finally:
+        phe.phe_ksk_free(k)
+        phe.phe_weights_free(w)
+    assert torch.equal(oa, ra) and torch.equal(ob, rb)
+
+
+def test_ksk_upload_rejects_bad_shapes(ctxs):
+    ctx = ctxs(256, "rns")
+    K = np.zeros((256, 1, 256), dtype=np.uint64)
+    for base_log, ell in [(0, 1), (31, 1), (17, 2), (8, 5)]:
+        with pytest.raises(phe.PheError) as ei:
+            phe.phe_ksk_upload(ctx, np.zeros((256, ell, 256), np.uint64), np.zeros((256, ell, 256), np.uint64),
+                               base_log, ell)
+        assert ei.value.status == phe.PHE_EINVAL
+    with pytest.raises(phe.PheError):
+        phe.phe_ksk_upload(ctx, K[:128], K[:128], 26, 1)   # n != N
