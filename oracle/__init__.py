@@ -18,6 +18,8 @@ Functions and the passages they follow:
   gadget, decompose                       Decomp (read as TFHE's approximate signed gadget)  Sec. 3.2
   ksk_encrypt, keyswitch, rotate          KeySwitching, Rotate             Sec. 3.2
   pack, pack_coeffs                       sum_j Rotate(KeySwitching(LWE_j), j)   Eq. (pack_rotate)
+  wire_bytes, pack_bits, unpack_bits,     bit-packed wire records          Sec. 4.4, Sec. 4.5
+  wire_input_record
 
 Parity status: every function above is pinned by tests/test_oracle_pins.py
 (closed forms, library routines, brute force, exact noise identity).
@@ -42,6 +44,7 @@ _u64p = ctypes.POINTER(ctypes.c_uint64)
 _i64p = ctypes.POINTER(ctypes.c_int64)
 _u32p = ctypes.POINTER(ctypes.c_uint32)
 _i8p = ctypes.POINTER(ctypes.c_int8)
+_u8p = ctypes.POINTER(ctypes.c_uint8)
 
 
 def build(force: bool = False) -> str:
@@ -90,6 +93,11 @@ def lib():
             L.oracle_chacha20_block.argtypes = [_u32p, ctypes.c_uint32, _u32p, _u32p]
             L.oracle_expand_mask.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint64, _u64p]
             L.oracle_num_threads.restype = ctypes.c_int
+            L.oracle_wire_bytes.restype = ctypes.c_uint64
+            L.oracle_wire_bytes.argtypes = [ctypes.c_uint64, ctypes.c_uint32]
+            L.oracle_pack_bits.argtypes = [_u64p, ctypes.c_uint64, ctypes.c_uint32, _u8p]
+            L.oracle_unpack_bits.argtypes = [_u8p, ctypes.c_uint64, ctypes.c_uint32, _u64p]
+            L.oracle_wire_input_record.argtypes = [ctypes.c_uint64, _u64p, ctypes.c_uint32, ctypes.c_uint32, _u8p]
             L.oracle_gadget.restype = ctypes.c_uint64
             L.oracle_gadget.argtypes = [ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32]
             L.oracle_decompose.argtypes = [ctypes.c_uint64, ctypes.c_uint64, ctypes.c_uint32, ctypes.c_uint32, _i64p]
@@ -375,6 +383,33 @@ def pack_coeffs(a, b, KA, KB, q: int, base_log: int, ell: int, rs):
     lib().oracle_pack_coeffs(_p(a, _u64p), _p(b, _u64p), m, n, _p(KA, _u64p), _p(KB, _u64p), N, q, base_log, ell,
                              _p(rs, _u32p), rs.shape[0], _p(A_out, _u64p), _p(B_out, _u64p))
     return A_out, B_out
+
+
+# --- wire format ----------------------------------------------------------------
+
+def wire_bytes(fields: int, bits: int) -> int:
+    return int(lib().oracle_wire_bytes(fields, bits))
+
+
+def pack_bits(v, bits: int) -> np.ndarray:
+    v = _u64(v).ravel()
+    out = np.zeros(wire_bytes(v.shape[0], bits), dtype=np.uint8)
+    lib().oracle_pack_bits(_p(v, _u64p), v.shape[0], bits, _p(out, _u8p))
+    return out
+
+
+def unpack_bits(data, n: int, bits: int) -> np.ndarray:
+    data = np.ascontiguousarray(np.asarray(data, dtype=np.uint8))
+    v = np.zeros(n, dtype=np.uint64)
+    lib().oracle_unpack_bits(_p(data, _u8p), n, bits, _p(v, _u64p))
+    return v
+
+
+def wire_input_record(seed: int, B, bits_q: int) -> np.ndarray:
+    B = _u64(B)
+    out = np.zeros(8 + wire_bytes(B.shape[0], bits_q), dtype=np.uint8)
+    lib().oracle_wire_input_record(seed, _p(B, _u64p), B.shape[0], bits_q, _p(out, _u8p))
+    return out
 
 
 def num_threads() -> int:

@@ -25,6 +25,7 @@
  *     function of RFC 8439 (see oracle_expand_mask).
  *   - Decomp, KeySwitching, Rotate ........................... Sec. 3.2
  *   - output packing sum_j Rotate(KeySwitching(LWE_j), j) ..... Eq. (pack_rotate), Sec. 4.3.1
+ *   - wire records: seed + bit-packed body in, bit-packed results out  Sec. 4.4, Sec. 4.5
  *
  * Parity pins (closed forms, library routines, brute force) live in tests/.
  */
@@ -557,6 +558,47 @@ void oracle_pack_coeffs(const uint64_t* a, const uint64_t* b, uint32_t m, uint32
         B_out[x] = accB;
     }
     free(D);
+}
+
+/* ------------------------------------------------------------------------ */
+/* Wire format (Sec. 4.4 sizes; Sec. 4.5: the result is "packed into a bit-  */
+/* vector").  A record is a little-endian bit stream: field m of width `bits` */
+/* occupies stream bits m*bits .. m*bits+bits-1, and stream bit j is bit     */
+/* j mod 8 of byte j/8.  Records are padded with zero bits to a multiple of  */
+/* 32 bits (the sizes printed in Sec. 4.4 need no padding).                  */
+/* ------------------------------------------------------------------------ */
+
+uint64_t oracle_wire_bytes(uint64_t fields, uint32_t bits) { return ((fields * bits + 31) / 32) * 4; }
+
+void oracle_pack_bits(const uint64_t* v, uint64_t n, uint32_t bits, uint8_t* out) {
+    const uint64_t nbytes = oracle_wire_bytes(n, bits);
+    for (uint64_t i = 0; i < nbytes; ++i) out[i] = 0;
+    for (uint64_t m = 0; m < n; ++m) {
+        for (uint32_t b = 0; b < bits; ++b) {
+            const uint64_t j = m * bits + b;
+            if ((v[m] >> b) & 1u) out[j / 8] |= (uint8_t)(1u << (j % 8));
+        }
+    }
+}
+
+void oracle_unpack_bits(const uint8_t* in, uint64_t n, uint32_t bits, uint64_t* v) {
+    for (uint64_t m = 0; m < n; ++m) {
+        uint64_t x = 0;
+        for (uint32_t b = 0; b < bits; ++b) {
+            const uint64_t j = m * bits + b;
+            if ((in[j / 8] >> (j % 8)) & 1u) x |= (uint64_t)1 << b;
+        }
+        v[m] = x;
+    }
+}
+
+/* Input record of one RLWE block as the client sends it (Sec. 3.1 "Mask
+ * Generation via PRNG", Sec. 4.4 input size): the 8-byte seed (little
+ * endian), then the N body coefficients at bits_q = ceil(log2 q) bits each.
+ * Size 8 + wire_bytes(N, bits_q); N = 2048, q = 2^39 gives 8 + 9984. */
+void oracle_wire_input_record(uint64_t seed, const uint64_t* B, uint32_t N, uint32_t bits_q, uint8_t* out) {
+    for (int i = 0; i < 8; ++i) out[i] = (uint8_t)(seed >> (8 * i));
+    oracle_pack_bits(B, N, bits_q, out + 8);
 }
 
 int oracle_num_threads(void) {
