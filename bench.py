@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--tokens", type=int, default=0, help="override tokens per GPU (0 = the workload's)")
     ap.add_argument("--e2e-tokens", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--packed-tokens", type=int, default=16,
+                    help="tokens of the packed-output measurement (Eq. (pack_rotate) after each product; 0 = skip)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--modulus", choices=["rns", "prime"], default="rns",
@@ -475,6 +477,11 @@ def main():
     if not args.no_e2e:
         e2e = measure_e2e(phe, ctx, weights, wl, mm, keys, inputs, args.e2e_tokens, stream)
 
+    packed = None
+    if args.packed_tokens > 0:
+        packed = measure_packed(phe, ctx, weights, wl, mm, keys, inputs, S, q, min(args.packed_tokens, T), stream,
+                                gen, dev)
+
     serving = None
     if args.serve_requests > 0 and wl.name == "layer":
         # release the batched plans' scratch first; the server allocates per chunk
@@ -508,6 +515,7 @@ def main():
                                "call_tokens": bchunk if args.form == "batched" else chunk},
                 "other_form": other,
                 "serving": serving,
+                "packed": packed,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
                 "kernels": {k: {"launches": v["launches"], "total_ms": v["total_ms"]} for k, v in trace.items()},
                 "clocks": clk, "sanity_decrypt": check}
@@ -658,6 +666,120 @@ def measure_e2e(phe, ctx, weights, wl, mm, keys, inputs, tokens, stream):
             "tokens_per_step": tokens,
             "note": "host-buffer C-ABI call; every result word of the layer's 14 products returns to pinned host "
                     "memory (output explosion without the paper's keyswitch packing)"}
+
+
+def _negacyclic_small(a, s, mod):
+    """a * s in Z_mod[X]/(X^N + 1) for a small signed s (client-side decryption)."""
+    a = a.astype(np.int64)
+    acc = np.zeros(a.shape[0], dtype=np.int64)
+    for k in np.nonzero(s)[0]:
+        rolled = np.roll(a, k)
+        rolled[:k] *= -1
+        acc += int(s[k]) * rolled   # |acc| < N 2^32: no overflow
+    return acc % mod
+
+
+def client_ksk(phe, ctx, S, N, q, base_log, gen, dev):
+    """Client side of the packing: KSK_i = RLWE_S(s_i round(q / 2^base_log)),
+    i < N, for the LWE key s = S (what SampleExtract leaves) and one gadget
+    level, made with the library's client encryption helper; host arrays
+    [N][1][N]."""
+    import torch
+    g0 = (q + (1 << (base_log - 1))) >> base_log
+    KA = torch.randint(0, q, (N, 1, N), device=dev, generator=gen, dtype=torch.int64)
+    E = torch.round(torch.randn((N, 1, N), device=dev, generator=gen) * synth.SIGMA).to(torch.int32)
+    X = torch.zeros((N, N), dtype=torch.int8, device=dev)
+    X[:, 0] = S
+    KB = torch.empty_like(KA)
+    phe.phe_client_encrypt(ctx, N, N, KA, S, E, X, g0, KB)
+    torch.cuda.synchronize()
+    return KA.cpu().numpy().view(np.uint64), KB.cpu().numpy().view(np.uint64)
+
+
+def measure_packed(phe, ctx, weights, wl, mm, keys, inputs, S, q, tokens, stream, gen, dev):
+    """The whole server path of the paper, Eq. (LWEdot) then the packing of
+    Eq. (pack_rotate) and the switch: every product of the layer through
+    phe_matmul_packed on `tokens` resident tokens (device-timed), then the
+    same through the host-buffer call phe_matmul_packed_host (wall-clock,
+    copies included).  Decomp: one level of base 2^26."""
+    import torch
+    N = wl.ring.N
+    base_log = 26
+    KA, KB = client_ksk(phe, ctx, S, N, q, base_log, gen, dev)
+    k = phe.phe_ksk_upload(ctx, KA, KB, base_log, 1)
+    del KA, KB
+    try:
+        outs = []
+        for (pi, name, d, rows, cols, L) in mm:
+            G = (rows + N - 1) // N
+            outs.append((torch.empty((tokens, G, N), dtype=torch.int32, device=dev),
+                         torch.empty((tokens, G, N), dtype=torch.int32, device=dev)))
+
+        def step():
+            for n, (pi, name, d, rows, cols, L) in enumerate(mm):
+                A, B, _ = inputs[keys[(pi, d)][0]]
+                phe.phe_matmul_packed(ctx, weights[pi], k, phe.PHE_FWD if d == "fwd" else phe.PHE_BWD, tokens,
+                                      A[:tokens], B[:tokens], outs[n][0], outs[n][1], phe.PHE_OUT_SWITCHED, stream)
+
+        step()
+        torch.cuda.synchronize()
+        phe.phe_trace_enable(ctx, True)
+        phe.phe_trace_read(ctx)
+        steps = 2
+        a = torch.cuda.Event(enable_timing=True)
+        b = torch.cuda.Event(enable_timing=True)
+        a.record(stream)
+        for _ in range(steps):
+            step()
+        b.record(stream)
+        torch.cuda.synchronize()
+        ms = a.elapsed_time(b)
+        tr = phe.phe_trace_read(ctx)
+        phe.phe_trace_enable(ctx, False)
+        kern = {n: round(v["total_ms"] / steps / tokens, 4) for n, v in tr.items()
+                if n.endswith("_kernel")}
+        # client-side check: RLWE of the first product, first token, first group
+        pi, name, d, rows, cols, L = mm[0]
+        _, _, X = inputs[keys[(pi, d)][0]]
+        W = synth.weights(wl.projections[pi][2], wl.projections[pi][1], seed=synth.SEED_W + pi)
+        Wd = W if d == "fwd" else W.T
+        y = Wd[:min(rows, N)].astype(np.int64) @ X[0].cpu().numpy().astype(np.int64)
+        pa = outs[0][0][0, 0].cpu().numpy().view(np.uint32)
+        pb = outs[0][1][0, 0].cpu().numpy().view(np.uint32).astype(np.int64)
+        ph = (pb - _negacyclic_small(pa, S.cpu().numpy().astype(np.int64), 1 << 32)) % (1 << 32)
+        t = synth.T_PLAIN
+        dec = ((ph * t + (1 << 31)) >> 32) % t
+        ok = int(np.sum((dec[:y.shape[0]] - y) % t == 0))
+        zero = int(np.sum(dec[y.shape[0]:] == 0))
+        out_bytes = sum(2 * ((rows + N - 1) // N) * N * 4 for (_, _, _, rows, _, _) in mm)
+        # end to end with host buffers
+        host_in = {key: (A[:tokens].cpu().pin_memory(), B[:tokens].cpu().pin_memory())
+                   for key, (A, B, X) in inputs.items()}
+        houts = [(torch.empty(o[0].shape, dtype=torch.int32).pin_memory(),
+                  torch.empty(o[1].shape, dtype=torch.int32).pin_memory()) for o in outs]
+
+        def host_step():
+            for n, (pi, name, d, rows, cols, L) in enumerate(mm):
+                hA, hB = host_in[keys[(pi, d)][0]]
+                phe.phe_matmul_packed_host(ctx, weights[pi], k, phe.PHE_FWD if d == "fwd" else phe.PHE_BWD, tokens,
+                                           hA, hB, houts[n][0], houts[n][1], phe.PHE_OUT_SWITCHED, 8, stream)
+
+        host_step()
+        t0 = time.perf_counter()
+        for _ in range(steps):
+            host_step()
+        torch.cuda.synchronize()
+        dt = time.perf_counter() - t0
+        h2d = sum(2 * tokens * L * N * 8 for (_, _, _, _, _, L) in mm)
+    finally:
+        phe.phe_ksk_free(k)
+    return {"value": tokens * steps / (ms / 1e3), "unit": "tokens/s", "tokens": tokens,
+            "ms_per_token": ms / steps / tokens, "kernel_ms_per_token": kern,
+            "ksk": {"base_log": base_log, "ell": 1, "device_bytes": 2 * N * N * 16},
+            "out_bytes_per_token": out_bytes, "unpacked_out_bytes_per_token": out_bytes_per_token(wl),
+            "sanity_decrypt": f"{ok}/{y.shape[0]} coefficients, {zero}/{N - y.shape[0]} unused zero",
+            "e2e": {"value": tokens * steps / dt, "unit": "tokens/s", "h2d_bytes_per_step": h2d,
+                    "d2h_bytes_per_step": out_bytes * tokens, "tokens_per_step": tokens}}
 
 
 if __name__ == "__main__":

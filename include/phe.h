@@ -61,14 +61,24 @@ typedef struct phe_weights phe_weights;
 /* Ring and switch parameters (Sec. 3.1 RLWE ciphertexts over
  * R_q = Z_q[X]/(X^N+1); Sec. 3.2 ModulusSwitch q -> q_out).
  *   N          ring degree, a power of two in [256, 8192]
- *   q          ciphertext modulus, 2^53 < q < 2^61, either
- *                - a prime with q = 1 (mod 2N) (e.g. 2^60 - 2^14 + 1;
+ *   q          ciphertext modulus: either
+ *                - a prime 2^53 < q < 2^61 with q = 1 (mod 2N) (e.g. 2^60 - 2^14 + 1;
  *                  rns_p1 = rns_p2 = 0), or
- *                - an RNS modulus q = rns_p1 * rns_p2 of two distinct primes
+ *                - an RNS modulus 2^53 < q = rns_p1 * rns_p2 < 2^61 of two distinct primes
  *                  below 2^30, each = 1 (mod 2N) (e.g. 1073643521 *
  *                  1073692673); the hot path then runs on 32-bit residues
- *                  and returns to q by the CRT before the switch
- *   log2_qout  k of the output modulus q' = 2^k, 1 <= k <= 32
+ *                  and returns to q by the CRT before the switch, or
+ *                - a power of two q = 2^K, 8 <= K <= 62, with rns_p1, rns_p2
+ *                  as above (the paper's parameter set, Table cryptoparams in
+ *                  Sec. 4.4: K = 39, N = 2048, q_out = 2^26).  Products run
+ *                  exactly in Z through the residues mod rns_p1 * rns_p2
+ *                  (masks lifted to [-2^(K-1), 2^(K-1))), then are reduced
+ *                  mod 2^K; this needs N * 127 * 2^(K-1) * L < p1 p2 / 2 for
+ *                  the weights' block count L (checked at upload), and the
+ *                  switch is a rounding shift (ties up).  No 64-bit form,
+ *                  client encryption or packing for such a q
+ *                  (PHE_EUNSUPPORTED)
+ *   log2_qout  k of the output modulus q' = 2^k, 1 <= k <= 32 (k < K for q = 2^K)
  *   flags      PHE_CTX_FORCE_U64: with an RNS modulus, run the 64-bit form
  *              anyway (the results are identical; for cross-checks) */
 typedef struct phe_params {

@@ -262,14 +262,25 @@ phe_status phe_ctx_create(const phe_params* prm, int device, phe_ctx** out) {
   if (N < (1u << phe::kMinLogN) || N > (1u << phe::kMaxLogN) || (N & (N - 1)))
     return fail(PHE_EINVAL, "N=%u must be a power of two in [256, 8192]", N);
   const u64 q = prm->q;
-  if (q <= (1ull << 53) || q >= (1ull << 61))
-    return fail(PHE_EINVAL, "q=%llu must satisfy 2^53 < q < 2^61", (unsigned long long)q);
-  if ((q - 1) % (2ull * N) != 0)
-    return fail(PHE_EINVAL, "q=%llu is not 1 mod 2N=%u", (unsigned long long)q, 2 * N);
   const bool rns_modulus = prm->rns_p1 || prm->rns_p2;
   const u32 p1 = std::min(prm->rns_p1, prm->rns_p2), p2 = std::max(prm->rns_p1, prm->rns_p2);
+  // q = 2^k (the paper's parameter set): computed exactly through p1 p2
+  const bool pow2 = q != 0 && (q & (q - 1)) == 0;
+  if (pow2) {
+    const u32 k = (u32)floor_log2(q);
+    if (!rns_modulus) return fail(PHE_EINVAL, "q=2^%u needs rns_p1, rns_p2 (the modulus the products run in)", k);
+    if (k < 8 || k > 62) return fail(PHE_EINVAL, "q=2^%u: need 8 <= k <= 62", k);
+    if (prm->log2_qout < 1 || prm->log2_qout >= k)
+      return fail(PHE_EINVAL, "q=2^%u: log2_qout=%u must be in [1, %u)", k, prm->log2_qout, k);
+    if (prm->flags & PHE_CTX_FORCE_U64) return fail(PHE_EINVAL, "q=2^%u has no 64-bit form", k);
+  } else {
+    if (q <= (1ull << 53) || q >= (1ull << 61))
+      return fail(PHE_EINVAL, "q=%llu must satisfy 2^53 < q < 2^61", (unsigned long long)q);
+    if ((q - 1) % (2ull * N) != 0)
+      return fail(PHE_EINVAL, "q=%llu is not 1 mod 2N=%u", (unsigned long long)q, 2 * N);
+  }
   if (rns_modulus) {
-    if (!p1 || p1 == p2 || p2 >= (1u << 30) || (u64)p1 * p2 != q)
+    if (!p1 || p1 == p2 || p2 >= (1u << 30) || (!pow2 && (u64)p1 * p2 != q))
       return fail(PHE_EINVAL, "RNS modulus: need q = p1 * p2 with distinct p1, p2 < 2^30");
     if (!is_prime(p1) || !is_prime(p2)) return fail(PHE_EINVAL, "RNS modulus: p1 and p2 must be prime");
     if ((p1 - 1) % (2u * N) != 0 || (p2 - 1) % (2u * N) != 0)
@@ -277,6 +288,13 @@ phe_status phe_ctx_create(const phe_params* prm, int device, phe_ctx** out) {
   } else if (!is_prime(q)) {
     return fail(PHE_EINVAL, "q=%llu is not prime (give rns_p1, rns_p2 for an RNS modulus)",
                 (unsigned long long)q);
+  }
+  if (pow2) {
+    // one block of products must stay below (p1 p2)/2 in magnitude: N 127 2^(k-1)
+    const u128 bound = (u128)N * 127 * (q / 2);
+    if (2 * bound >= (u128)p1 * p2)
+      return fail(PHE_EINVAL, "q=%llu: N*127*q/2 must be below p1*p2/2 for exact products",
+                  (unsigned long long)q);
   }
   if (prm->log2_qout < 1 || prm->log2_qout > 32) return fail(PHE_EINVAL, "log2_qout=%u not in [1, 32]", prm->log2_qout);
   if (prm->flags & ~PHE_CTX_FORCE_U64) return fail(PHE_EINVAL, "flags=%u", prm->flags);
@@ -302,7 +320,7 @@ phe_status phe_ctx_create(const phe_params* prm, int device, phe_ctx** out) {
   rc.q4 = 4 * q;
   rc.half_q = q / 2;
   rc.ms_s = (u32)floor_log2(q);
-  rc.ms_mu = (u64)(((u128)1 << (64 + rc.ms_s)) / q);
+  rc.ms_mu = pow2 ? 0 : (u64)(((u128)1 << (64 + rc.ms_s)) / q);  // the power-of-two switch is a shift
   rc.red_mu = (u64)(((u128)1 << 64) / q);
   rc.c30 = (1ull << 30) % q;
   rc.c30p = shoup(rc.c30, q);
@@ -311,10 +329,13 @@ phe_status phe_ctx_create(const phe_params* prm, int device, phe_ctx** out) {
   rc.c64 = (u64)(((u128)1 << 64) % q);
   rc.c64p = shoup(rc.c64, q);
   rc.log2_qout = prm->log2_qout;
-  c->n_inv = modinv(N, q);
-  c->n_inv_p = shoup(c->n_inv, q);
-  c->ninv.n64 = c->n_inv;
-  c->ninv.n64p = c->n_inv_p;
+  c->pow2 = pow2;
+  if (!pow2) {
+    c->n_inv = modinv(N, q);
+    c->n_inv_p = shoup(c->n_inv, q);
+    c->ninv.n64 = c->n_inv;
+    c->ninv.n64p = c->n_inv_p;
+  }
 
   // Primitive 2N-th root of unity mod q: directly for a prime q; for q = p1 p2
   // the CRT combination of the two primes' roots (its order is 2N in both).
@@ -324,13 +345,14 @@ phe_status phe_ctx_create(const phe_params* prm, int device, phe_ctx** out) {
     psi1 = (u32)primitive_root_2n(p1, N);
     psi2 = (u32)primitive_root_2n(p2, N);
     if (!psi1 || !psi2) { delete c; return fail(PHE_EINVAL, "no primitive 2N-th root of unity mod p1 or p2"); }
-    psi = crt2(psi1, p1, psi2, p2);
+    if (!pow2) psi = crt2(psi1, p1, psi2, p2);
   } else {
     psi = primitive_root_2n(q, N);
   }
-  if (!psi) { delete c; return fail(PHE_EINVAL, "no primitive 2N-th root of unity found for q"); }
+  if (!psi && !pow2) { delete c; return fail(PHE_EINVAL, "no primitive 2N-th root of unity found for q"); }
 
-  phe_status st = build_tables(c, [&](u32 br, bool inverse) -> ulonglong2 {
+  // 64-bit tables mod q (none for q = 2^k: everything runs through p1 p2)
+  phe_status st = pow2 ? PHE_OK : build_tables(c, [&](u32 br, bool inverse) -> ulonglong2 {
     const u64 root = inverse ? modinv(psi, q) : psi;
     const u64 a = powmod(root, br, q);
     return make_ulonglong2(a, shoup(a, q));
@@ -356,6 +378,13 @@ phe_status phe_ctx_create(const phe_params* prm, int device, phe_ctx** out) {
     k.half1 = (p1 - 1) / 2;
     k.half2 = (p2 - 1) / 2;
     k.kmask = (u32)(two_k - 1);
+    if (pow2) {
+      k.p2k = (u32)floor_log2(q);
+      k.p2shift = k.p2k - prm->log2_qout;
+      k.Q = (u64)p1 * p2;
+      k.Qhalf = k.Q / 2;
+      k.lift = k.Q - q;
+    }
     c->ninv.n1 = (u32)modinv(N, p1);
     c->ninv.n1p = shoup32(c->ninv.n1, p1);
     c->ninv.n2 = (u32)modinv(N, p2);
@@ -404,6 +433,18 @@ phe_status phe_weights_upload(phe_ctx* c, const int8_t* h_W, uint32_t d_out, uin
   if (d_out < 1 || d_in < 1 || d_out > 16384 || d_in > 16384)
     return fail(PHE_EINVAL, "weights %ux%u: dimensions must be in [1, 16384]", d_out, d_in);
   if (dirs == 0 || (dirs & ~3u)) return fail(PHE_EINVAL, "dirs=%u must be a non-empty subset of {FWD, BWD}", dirs);
+  if (c->pow2) {
+    // every product sum_i A_i w_hat_ij must stay an exact integer below p1 p2 / 2
+    const u32 N0 = c->prm.N;
+    for (int dir = 0; dir < 2; ++dir) {
+      if (!(dirs & (1u << dir))) continue;
+      const u32 cols = dir == PHE_FWD ? d_in : d_out;
+      const u64 L = (cols + N0 - 1) / N0;
+      if (2 * ((u128)L * N0 * 127 * (c->prm.q / 2)) >= (u128)c->rk.Q)
+        return fail(PHE_EINVAL, "weights %ux%u: %llu blocks exceed the exact range of p1*p2 for q=2^%u", d_out,
+                    d_in, (unsigned long long)L, c->rk.p2k);
+    }
+  }
   DeviceGuard g(c->device);
   if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
@@ -645,6 +686,8 @@ phe_status phe_modswitch(phe_ctx* c, const uint64_t* d_in, uint32_t* d_out, size
 phe_status phe_client_encrypt(phe_ctx* c, uint32_t T, uint32_t d, const uint64_t* d_A, const int8_t* d_S,
                               const int32_t* d_E, const int8_t* d_x, uint64_t delta, uint64_t* d_B, void* stream) {
   if (!c) return fail(PHE_EINVAL, "phe_client_encrypt: null context");
+  if (c->pow2) return fail(PHE_EUNSUPPORTED, "phe_client_encrypt: no NTT mod q = 2^%u (encrypt on the client)",
+                           c->rk.p2k);
   if (T == 0) return PHE_OK;
   if (d < 1 || d > 16384) return fail(PHE_EINVAL, "phe_client_encrypt: d=%u not in [1, 16384]", d);
   if (!d_A || !d_S || !d_E || !d_x || !d_B) return fail(PHE_EINVAL, "phe_client_encrypt: null buffer");

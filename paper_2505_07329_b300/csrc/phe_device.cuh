@@ -128,6 +128,12 @@ struct RnsConst {
   u32 inv_a2;         // floor(2^32 / p2)
   u32 half1, half2;   // (p1 - 1)/2, (p2 - 1)/2
   u32 kmask;          // 2^k - 1
+  // A power-of-two ciphertext modulus q = 2^p2k computed through p1 p2: the
+  // products are exact integers below (p1 p2)/2 in magnitude, so the centred
+  // CRT value reduced mod 2^p2k is the product mod q (p2k = 0: q = p1 p2).
+  u32 p2k, p2shift;   // log2 q and log2 q - k
+  u64 Q, Qhalf;       // p1 p2 and floor(p1 p2 / 2)
+  u64 lift;           // p1 p2 - 2^p2k: centred lift of a word in [2^(p2k-1), 2^p2k)
 };
 
 // A word of [0, 2^61) to its residues (mod p1, mod p2).
@@ -176,6 +182,24 @@ __device__ __forceinline__ u32 rns_modswitch(u32 c1, u32 h, const RnsConst& k) {
   if (n >= k.p2) { n -= k.p2; ++t; }
   if (n >= k.p2) ++t;
   return (a + G + t) & k.kmask;
+}
+
+// Power-of-two q (RnsConst::p2k > 0).  Input word -> residues of its centred
+// lift: a mod 2^p2k in [-2^(p2k-1), 2^(p2k-1)), represented mod p1 p2.
+__device__ __forceinline__ uint2 pow2_residues(u64 a_mod_q, const RnsConst& k) {
+  const u64 v = (a_mod_q >> (k.p2k - 1)) ? a_mod_q + k.lift : a_mod_q;
+  return to_residues(v, k);
+}
+// CRT digits (c1, h) of an exact product -> its value mod 2^p2k: the centred
+// representative of c = c1 + p1 h, taken mod 2^64 (2^p2k divides 2^64).
+__device__ __forceinline__ u64 pow2_from_crt(u32 c1, u32 h, const RnsConst& k) {
+  u64 c = (u64)c1 + (u64)k.p1 * h;
+  if (c > k.Qhalf) c -= k.Q;  // wraps: the two's complement of a negative value
+  return c & ((1ull << k.p2k) - 1);
+}
+// ModulusSwitch 2^p2k -> 2^k: floor((v + 2^(p2k-k-1)) / 2^(p2k-k)) mod 2^k.
+__device__ __forceinline__ u32 pow2_modswitch(u64 v, const RnsConst& k) {
+  return (u32)((v + (1ull << (k.p2shift - 1))) >> k.p2shift) & k.kmask;
 }
 
 // Arithmetic policies of the NTT passes.

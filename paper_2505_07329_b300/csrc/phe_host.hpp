@@ -44,7 +44,7 @@ struct NttJob {             // forward transform of T*L input blocks
   const u64* seeds = nullptr;  // [blocks] 64-bit seeds: masks expanded on the fly
 };
 
-enum OutMode : int { kOutSwitched = 0, kOutRaw = 1, kOutRing = 2 };
+enum OutMode : int { kOutSwitched = 0, kOutRaw = 1, kOutRing = 2, kPow2 = 4 /* flag: q = 2^k via the RNS form */ };
 
 // Kernel names for tracing; kKCall brackets a whole phe_matmul call.
 enum KernelId : int {
@@ -94,7 +94,8 @@ struct phe_ctx {
   phe::u64 n_inv = 0, n_inv_p = 0;  // N^-1 mod q and its Shoup quotient
   phe::NInv ninv{};
   phe::Tables tab;        // 64-bit form (every context)
-  bool rns = false;       // hot path in the RNS form (q = p1 p2)
+  bool rns = false;       // hot path in the RNS form (q = p1 p2, or q = 2^k computed through p1 p2)
+  bool pow2 = false;      // q = 2^k: exact products through p1 p2, reduced mod 2^k (RnsConst::p2k)
   phe::RnsConst rk{};
   phe::Tables tab32;      // RNS form (RNS contexts)
   int num_sms = 0;

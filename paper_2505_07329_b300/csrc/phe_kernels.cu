@@ -42,10 +42,11 @@ __device__ __forceinline__ RingOf<RNS> make_ring(const RingConst& rc, const RnsC
 // --------------------------------------------------------------------------
 // Forward transform of input masks: [blocks][N] natural -> A_hat layout.
 // --------------------------------------------------------------------------
-template <int LOGN, bool RNS>
+template <int LOGN, bool RNS, bool P2 = false>
 __global__ void __launch_bounds__(Shape<LOGN>::TPB)
     input_ntt_kernel(NttJob job, RingConst rc, RnsConst rk, const void* __restrict__ tw0v,
                      const void* __restrict__ twcv) {
+  static_assert(RNS || !P2, "a power-of-two q runs in the RNS form");
   using S = Shape<LOGN>;
   using R = RingOf<RNS>;
   using W = typename R::Word;
@@ -81,7 +82,8 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB)
   W x[16];
 #pragma unroll
   for (int e = 0; e < 16; ++e) {
-    if constexpr (RNS) x[e] = to_residues(v[e], rk);
+    if constexpr (P2) x[e] = pow2_residues(v[e], rk);
+    else if constexpr (RNS) x[e] = to_residues(v[e], rk);
     else x[e] = v[e];
   }
   ntt_regs<LOGN>(x, p, buf, reinterpret_cast<const typename R::Tw*>(tw0v),
@@ -219,7 +221,10 @@ template <int LOGN, int MODE, bool RNS>
 __global__ void __launch_bounds__(Shape<LOGN>::TPB, PHE_LWEDOT_MIN_BLOCKS)
     lwedot_kernel(const LweJobTable jt, RingConst rc, RnsConst rk, const void* __restrict__ tw0v,
                   const void* __restrict__ twcv) {
-  static_assert(!(RNS && MODE == kOutRing), "client encryption runs in the 64-bit form");
+  constexpr int OUT = MODE & 3;                 // kOutSwitched, kOutRaw or kOutRing
+  constexpr bool P2 = (MODE & kPow2) != 0;      // power-of-two q through the RNS modulus
+  static_assert(!(RNS && OUT == kOutRing), "client encryption runs in the 64-bit form");
+  static_assert(RNS || !P2, "a power-of-two q runs in the RNS form");
   using S = Shape<LOGN>;
   using R = RingOf<RNS>;
   using W = typename R::Word;
@@ -227,7 +232,7 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, PHE_LWEDOT_MIN_BLOCKS)
   constexpr int N = S::N;
   constexpr int P = S::P;
   constexpr int NP = S::NPASS;
-  constexpr bool BODY = MODE != kOutRing;
+  constexpr bool BODY = OUT != kOutRing;
   constexpr int GW = (P < 32) ? P : 32;   // lanes of one body-reduction group
   constexpr int NGRP = P / GW;            // groups per transform
   extern __shared__ u64 smem[];
@@ -312,19 +317,24 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, PHE_LWEDOT_MIN_BLOCKS)
       }
       intt_regs<LOGN>(x, p, buf, tw0, twc, ring);  // barriers inside also order red[]
       if (active) {
-        if constexpr (MODE == kOutSwitched || MODE == kOutRaw) {
+        if constexpr (OUT == kOutSwitched || OUT == kOutRaw) {
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
             const int pos = pass_pos<LOGN, NP - 1>(p, e);
             const size_t o = ((size_t)t * J.rows + row) * N + (N - 1 - pos);
-            if constexpr (RNS) {
+            if constexpr (P2) {
+              const u32 c1 = sub_if32(x[e].x, rk.p1);
+              const u64 v = pow2_from_crt(c1, crt_digit(c1, sub_if32(x[e].y, rk.p2), rk), rk);
+              if constexpr (OUT == kOutSwitched) reinterpret_cast<uint32_t*>(J.out)[o] = pow2_modswitch(v, rk);
+              else reinterpret_cast<u64*>(J.out)[o] = v;
+            } else if constexpr (RNS) {
               const u32 c1 = sub_if32(x[e].x, rk.p1);
               const u32 h = crt_digit(c1, sub_if32(x[e].y, rk.p2), rk);
-              if constexpr (MODE == kOutSwitched) reinterpret_cast<uint32_t*>(J.out)[o] = rns_modswitch(c1, h, rk);
+              if constexpr (OUT == kOutSwitched) reinterpret_cast<uint32_t*>(J.out)[o] = rns_modswitch(c1, h, rk);
               else reinterpret_cast<u64*>(J.out)[o] = (u64)c1 + (u64)rk.p1 * h;
             } else {
               const u64 c = reduce_4q(x[e], q, rc.q2);
-              if constexpr (MODE == kOutSwitched) reinterpret_cast<uint32_t*>(J.out)[o] = modswitch_word(c, rc);
+              if constexpr (OUT == kOutSwitched) reinterpret_cast<uint32_t*>(J.out)[o] = modswitch_word(c, rc);
               else reinterpret_cast<u64*>(J.out)[o] = c;
             }
           }
@@ -356,11 +366,20 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, PHE_LWEDOT_MIN_BLOCKS)
 #pragma unroll
               for (int i = 0; i < 3; ++i) S3[i] += red[par][slot][g][i];
             }
-            const u64 v = body_combine(S3, rc);
-            if constexpr (MODE == kOutSwitched)
-              reinterpret_cast<uint32_t*>(J.out_body)[(size_t)t * J.rows + row] = modswitch_word(v, rc);
-            else
-              reinterpret_cast<u64*>(J.out_body)[(size_t)t * J.rows + row] = v;
+            if constexpr (P2) {
+              // S0 + S1 2^30 + S2 2^60 mod 2^64 is exact mod q = 2^p2k
+              const u64 v = ((u64)S3[0] + ((u64)S3[1] << 30) + ((u64)S3[2] << 60)) & (rc.q - 1);
+              if constexpr (OUT == kOutSwitched)
+                reinterpret_cast<uint32_t*>(J.out_body)[(size_t)t * J.rows + row] = pow2_modswitch(v, rk);
+              else
+                reinterpret_cast<u64*>(J.out_body)[(size_t)t * J.rows + row] = v;
+            } else {
+              const u64 v = body_combine(S3, rc);
+              if constexpr (OUT == kOutSwitched)
+                reinterpret_cast<uint32_t*>(J.out_body)[(size_t)t * J.rows + row] = modswitch_word(v, rc);
+              else
+                reinterpret_cast<u64*>(J.out_body)[(size_t)t * J.rows + row] = v;
+            }
           }
         }
       }
@@ -384,9 +403,10 @@ __global__ void expand_masks_kernel(const u64* __restrict__ seeds, u32 n, u32 N,
   }
 }
 
-__global__ void modswitch_kernel(const u64* __restrict__ in, uint32_t* __restrict__ out, size_t n, RingConst rc) {
+__global__ void modswitch_kernel(const u64* __restrict__ in, uint32_t* __restrict__ out, size_t n, RingConst rc,
+                                 RnsConst rk) {
   for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    out[i] = modswitch_word(reduce_word(in[i], rc), rc);
+    out[i] = rk.p2k ? pow2_modswitch(reduce_word(in[i], rc), rk) : modswitch_word(reduce_word(in[i], rc), rc);
 }
 
 // --------------------------------------------------------------------------
@@ -438,7 +458,12 @@ cudaError_t launch_input_ntt(const phe_ctx* c, const NttJob* jobs, int n, cudaSt
       using S = Shape<LOGN>;
       const size_t smem = (size_t)S::SLOTS * S::PADN * sizeof(u64);
       const u32 grid = (job.blocks + S::SLOTS - 1) / S::SLOTS;
-      if (rns) {
+      if (rns && c->pow2) {
+        cudaError_t e2 = set_smem(input_ntt_kernel<LOGN, true, true>, smem);
+        if (e2 != cudaSuccess) return e2;
+        input_ntt_kernel<LOGN, true, true><<<grid, S::TPB, smem, s>>>(job, c->rc, c->rk, tw0_of(c, true, false),
+                                                                      twc_of(c, true, false));
+      } else if (rns) {
         cudaError_t e2 = set_smem(input_ntt_kernel<LOGN, true>, smem);
         if (e2 != cudaSuccess) return e2;
         input_ntt_kernel<LOGN, true><<<grid, S::TPB, smem, s>>>(job, c->rc, c->rk, tw0_of(c, true, false),
@@ -501,6 +526,11 @@ cudaError_t launch_lwedot(const phe_ctx* c, const LweJobTable& jt, int mode, int
   const bool rns = c->rns && !force64 && mode != kOutRing;
   return by_logn(c->logn, [&](auto lg) -> cudaError_t {
     constexpr int LOGN = decltype(lg)::value;
+    if (rns && c->pow2) {
+      if (mode == kOutSwitched) return lwedot_impl<LOGN, kOutSwitched | kPow2, true>(c, jt, grid_limit, s);
+      if (mode == kOutRaw) return lwedot_impl<LOGN, kOutRaw | kPow2, true>(c, jt, grid_limit, s);
+      return cudaErrorInvalidValue;
+    }
     if (rns) {
       if (mode == kOutSwitched) return lwedot_impl<LOGN, kOutSwitched, true>(c, jt, grid_limit, s);
       if (mode == kOutRaw) return lwedot_impl<LOGN, kOutRaw, true>(c, jt, grid_limit, s);
@@ -527,6 +557,9 @@ cudaError_t prepare_launches(const phe_ctx* c) {
     if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutRing, false>, smem);
     if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutSwitched, true>, smem);
     if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutRaw, true>, smem);
+    if (e == cudaSuccess) e = set_smem(input_ntt_kernel<LOGN, true, true>, smem);
+    if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutSwitched | kPow2, true>, smem);
+    if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutRaw | kPow2, true>, smem);
     return e;
   });
 }
@@ -546,7 +579,7 @@ cudaError_t launch_modswitch(const phe_ctx* c, const u64* in, uint32_t* out, siz
   size_t blocks = (n + 255) / 256;
   const size_t cap = (size_t)c->num_sms * 16;
   if (blocks > cap) blocks = cap;
-  modswitch_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, out, n, c->rc);
+  modswitch_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, out, n, c->rc, c->rk);
   return cudaGetLastError();
 }
 

@@ -137,31 +137,36 @@ __device__ __forceinline__ u32 reduce_acc32(u64 a, u32 p, u32 c32, u32 c32p) {
   return sub_if32(lo + hi, p);
 }
 
-// Per NTT slot s and unit u: P_hat[u][c][s] = sum_{r < n*ell} D_hat[u][r][s] K_hat[r][c][s]
-// for c = 0 (A) and 1 (B).  A block covers 256 slots of UB units, so each key
-// entry loaded serves UB units.
+// Per NTT slot s, unit u and segment g of the contraction:
+//   P_hat[g][u][c][s] = sum_{r in segment g} D_hat[u][r][s] K_hat[r][c][s]   (c = 0: A, 1: B),
+// fully reduced.  A block covers 256 slots, one segment and UB units, so each
+// key entry it loads serves UB units; the segments (a split of the n*ell
+// contraction) give enough blocks to fill the GPU and are summed by the
+// finishing kernel.
 template <bool RNS, int UB>
 __global__ void __launch_bounds__(256)
-    pack_mac_kernel(const u64* __restrict__ Dhat, const void* __restrict__ khatv, u32 nr, u32 N, u32 units,
+    pack_mac_kernel(const u64* __restrict__ Dhat, const void* __restrict__ khatv, u32 nr, u32 rseg, u32 N, u32 units,
                     u64* __restrict__ Phat, RingConst rc, RnsConst rk) {
   const u32 s = blockIdx.x * blockDim.x + threadIdx.x;
-  const u32 u0 = blockIdx.y * UB;
+  const u32 seg = blockIdx.y, u0 = blockIdx.z * UB;
   if (s >= N) return;
   const int nu = (int)min((u32)UB, units - u0);
+  const u32 r0 = seg * rseg, r1 = min(nr, r0 + rseg);
+  u64* part = Phat + (size_t)seg * units * 2 * N;
   if constexpr (RNS) {
     const uint4* kh = reinterpret_cast<const uint4*>(khatv);
     u64 acc[UB][4];
 #pragma unroll
     for (int k = 0; k < UB; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0;
 #pragma unroll 2
-    for (u32 r = 0; r < nr; ++r) {
+    for (u32 r = r0; r < r1; ++r) {
       const uint4 ka = __ldg(&kh[((size_t)r * 2) * N + s]);
       const uint4 kb = __ldg(&kh[((size_t)r * 2 + 1) * N + s]);
 #pragma unroll
       for (int k = 0; k < UB; ++k) {
         if (k < nu) {
           const uint2 d = __ldg(reinterpret_cast<const uint2*>(Dhat) + ((size_t)(u0 + k) * nr + r) * N + s);
-          acc[k][0] += mul_shoup32(d.x, ka.x, ka.y, rk.p1);
+          acc[k][0] += mul_shoup32(d.x, ka.x, ka.y, rk.p1);  // each < 2p: 2^12 of them stay below 2^43
           acc[k][1] += mul_shoup32(d.y, ka.z, ka.w, rk.p2);
           acc[k][2] += mul_shoup32(d.x, kb.x, kb.y, rk.p1);
           acc[k][3] += mul_shoup32(d.y, kb.z, kb.w, rk.p2);
@@ -171,7 +176,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int k = 0; k < UB; ++k) {
       if (k < nu) {
-        uint2* out = reinterpret_cast<uint2*>(Phat) + (size_t)(u0 + k) * 2 * N + s;
+        uint2* out = reinterpret_cast<uint2*>(part) + (size_t)(u0 + k) * 2 * N + s;
         out[0] = make_uint2(reduce_acc32(acc[k][0], rk.p1, rk.c32a, rk.c32ap),
                             reduce_acc32(acc[k][1], rk.p2, rk.c32b, rk.c32bp));
         out[N] = make_uint2(reduce_acc32(acc[k][2], rk.p1, rk.c32a, rk.c32ap),
@@ -185,7 +190,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int k = 0; k < UB; ++k) acc[k][0] = acc[k][1] = 0;
 #pragma unroll 2
-    for (u32 r = 0; r < nr; ++r) {
+    for (u32 r = r0; r < r1; ++r) {
       const ulonglong2 ka = __ldg(&kh[((size_t)r * 2) * N + s]);
       const ulonglong2 kb = __ldg(&kh[((size_t)r * 2 + 1) * N + s]);
 #pragma unroll
@@ -202,7 +207,7 @@ __global__ void __launch_bounds__(256)
 #pragma unroll
     for (int k = 0; k < UB; ++k) {
       if (k < nu) {
-        u64* out = Phat + (size_t)(u0 + k) * 2 * N + s;
+        u64* out = part + (size_t)(u0 + k) * 2 * N + s;
         out[0] = reduce_4q(acc[k][0], q, rc.q2);
         out[N] = reduce_4q(acc[k][1], q, rc.q2);
       }
@@ -215,9 +220,9 @@ __global__ void __launch_bounds__(256)
 // Block b = u*2 + c of the chunk; u_base is the chunk's first unit.
 template <int LOGN, bool RNS, int MODE>
 __global__ void __launch_bounds__(Shape<LOGN>::TPB)
-    pack_finish_kernel(const u64* __restrict__ Phat, const u64* __restrict__ body, u32 rows, u32 G, u32 u_base,
-                       u32 units, void* __restrict__ out_a, void* __restrict__ out_b, RingConst rc, RnsConst rk,
-                       const void* __restrict__ tw0v, const void* __restrict__ twcv) {
+    pack_finish_kernel(const u64* __restrict__ Phat, u32 nseg, const u64* __restrict__ body, u32 rows, u32 G,
+                       u32 u_base, u32 units, void* __restrict__ out_a, void* __restrict__ out_b, RingConst rc,
+                       RnsConst rk, const void* __restrict__ tw0v, const void* __restrict__ twcv) {
   using S = Shape<LOGN>;
   using R = std::conditional_t<RNS, Ring2x32, Ring64>;
   using W = typename R::Word;
@@ -237,22 +242,26 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB)
     else x[r] = 0;
   }
   if (active) {
-    // words (r, r+1) of thread p sit together, as the input transform wrote them
-    if constexpr (RNS) {
-      const uint4* ap = reinterpret_cast<const uint4*>(Phat + (size_t)b * N);
+    // the segments' partial sums, words (r, r+1) of thread p together as the
+    // input transform laid them out
+    for (u32 g = 0; g < nseg; ++g) {
+      const u64* part = Phat + ((size_t)g * units * 2 + b) * N;
+      if constexpr (RNS) {
+        const uint4* ap = reinterpret_cast<const uint4*>(part);
 #pragma unroll
-      for (int r = 0; r < 16; r += 2) {
-        const uint4 v = ap[(r >> 1) * P + p];
-        x[r] = make_uint2(v.x, v.y);
-        x[r + 1] = make_uint2(v.z, v.w);
-      }
-    } else {
-      const ulonglong2* ap = reinterpret_cast<const ulonglong2*>(Phat + (size_t)b * N);
+        for (int r = 0; r < 16; r += 2) {
+          const uint4 v = ap[(r >> 1) * P + p];
+          x[r] = make_uint2(sub_if32(x[r].x + v.x, rk.p1), sub_if32(x[r].y + v.y, rk.p2));
+          x[r + 1] = make_uint2(sub_if32(x[r + 1].x + v.z, rk.p1), sub_if32(x[r + 1].y + v.w, rk.p2));
+        }
+      } else {
+        const ulonglong2* ap = reinterpret_cast<const ulonglong2*>(part);
 #pragma unroll
-      for (int r = 0; r < 16; r += 2) {
-        const ulonglong2 v = ap[(r >> 1) * P + p];
-        x[r] = v.x;
-        x[r + 1] = v.y;
+        for (int r = 0; r < 16; r += 2) {
+          const ulonglong2 v = ap[(r >> 1) * P + p];
+          x[r] = reduce_2q(x[r] + v.x, rc.q);
+          x[r + 1] = reduce_2q(x[r + 1] + v.y, rc.q);
+        }
       }
     }
   }
@@ -346,17 +355,30 @@ cudaError_t launch_decompose(const phe_ctx* c, const phe_ksk* k, const u64* mask
   return cudaGetLastError();
 }
 
-cudaError_t launch_mac(const phe_ctx* c, const phe_ksk* k, const u64* Dhat, u32 cu, u64* Phat, cudaStream_t s) {
+// Segments of the n*ell contraction for a chunk of `cu` units: enough blocks
+// for about four per SM, each segment at least 16 rows long.
+u32 mac_segments(const phe_ctx* c, const phe_ksk* k, u32 cu) {
+  const u32 nr = k->n * k->ell;
+  const u32 base = (c->prm.N / 256) * ((cu + kMacUnits - 1) / kMacUnits);
+  const u32 want = (4u * (u32)c->num_sms + base - 1) / base;
+  return std::max(1u, std::min(want, nr / 16));
+}
+
+cudaError_t launch_mac(const phe_ctx* c, const phe_ksk* k, const u64* Dhat, u32 cu, u32 nseg, u64* Phat,
+                       cudaStream_t s) {
   const u32 N = c->prm.N, nr = k->n * k->ell;
-  const dim3 grid(N / 256, (cu + kMacUnits - 1) / kMacUnits);
-  if (c->rns) phe::pack_mac_kernel<true, kMacUnits><<<grid, 256, 0, s>>>(Dhat, k->khat, nr, N, cu, Phat, c->rc, c->rk);
-  else phe::pack_mac_kernel<false, kMacUnits><<<grid, 256, 0, s>>>(Dhat, k->khat, nr, N, cu, Phat, c->rc, c->rk);
+  const u32 rseg = (nr + nseg - 1) / nseg;
+  const dim3 grid(N / 256, nseg, (cu + kMacUnits - 1) / kMacUnits);
+  if (c->rns)
+    phe::pack_mac_kernel<true, kMacUnits><<<grid, 256, 0, s>>>(Dhat, k->khat, nr, rseg, N, cu, Phat, c->rc, c->rk);
+  else
+    phe::pack_mac_kernel<false, kMacUnits><<<grid, 256, 0, s>>>(Dhat, k->khat, nr, rseg, N, cu, Phat, c->rc, c->rk);
   return cudaGetLastError();
 }
 
 template <int LOGN, bool RNS, int MODE>
-cudaError_t finish_one(const phe_ctx* c, const u64* Phat, const u64* body, u32 rows, u32 G, u32 u_base, u32 cu,
-                       void* oa, void* ob, cudaStream_t s) {
+cudaError_t finish_one(const phe_ctx* c, const u64* Phat, u32 nseg, const u64* body, u32 rows, u32 G, u32 u_base,
+                       u32 cu, void* oa, void* ob, cudaStream_t s) {
   using S = phe::Shape<LOGN>;
   const size_t smem = phe::lwedot_smem(LOGN);
   auto kern = phe::pack_finish_kernel<LOGN, RNS, MODE>;
@@ -366,30 +388,31 @@ cudaError_t finish_one(const phe_ctx* c, const u64* Phat, const u64* body, u32 r
   }
   const phe::Tables& tab = RNS ? c->tab32 : c->tab;
   const u32 blocks = (2 * cu + S::SLOTS - 1) / S::SLOTS;
-  kern<<<blocks, S::TPB, smem, s>>>(Phat, body, rows, G, u_base, cu, oa, ob, c->rc, c->rk, tab.inv_0, tab.inv_c);
+  kern<<<blocks, S::TPB, smem, s>>>(Phat, nseg, body, rows, G, u_base, cu, oa, ob, c->rc, c->rk, tab.inv_0,
+                                    tab.inv_c);
   return cudaGetLastError();
 }
 
 template <int LOGN>
-cudaError_t finish_by_form(const phe_ctx* c, int mode, const u64* Phat, const u64* body, u32 rows, u32 G, u32 u_base,
-                           u32 cu, void* oa, void* ob, cudaStream_t s) {
+cudaError_t finish_by_form(const phe_ctx* c, int mode, const u64* Phat, u32 nseg, const u64* body, u32 rows, u32 G,
+                           u32 u_base, u32 cu, void* oa, void* ob, cudaStream_t s) {
   if (c->rns) {
-    return mode == phe::kOutRaw ? finish_one<LOGN, true, phe::kOutRaw>(c, Phat, body, rows, G, u_base, cu, oa, ob, s)
-                                : finish_one<LOGN, true, phe::kOutSwitched>(c, Phat, body, rows, G, u_base, cu, oa, ob, s);
+    return mode == phe::kOutRaw ? finish_one<LOGN, true, phe::kOutRaw>(c, Phat, nseg, body, rows, G, u_base, cu, oa, ob, s)
+                                : finish_one<LOGN, true, phe::kOutSwitched>(c, Phat, nseg, body, rows, G, u_base, cu, oa, ob, s);
   }
-  return mode == phe::kOutRaw ? finish_one<LOGN, false, phe::kOutRaw>(c, Phat, body, rows, G, u_base, cu, oa, ob, s)
-                              : finish_one<LOGN, false, phe::kOutSwitched>(c, Phat, body, rows, G, u_base, cu, oa, ob, s);
+  return mode == phe::kOutRaw ? finish_one<LOGN, false, phe::kOutRaw>(c, Phat, nseg, body, rows, G, u_base, cu, oa, ob, s)
+                              : finish_one<LOGN, false, phe::kOutSwitched>(c, Phat, nseg, body, rows, G, u_base, cu, oa, ob, s);
 }
 
-cudaError_t launch_finish(const phe_ctx* c, int mode, const u64* Phat, const u64* body, u32 rows, u32 G, u32 u_base,
-                          u32 cu, void* oa, void* ob, cudaStream_t s) {
+cudaError_t launch_finish(const phe_ctx* c, int mode, const u64* Phat, u32 nseg, const u64* body, u32 rows, u32 G,
+                          u32 u_base, u32 cu, void* oa, void* ob, cudaStream_t s) {
   switch (c->logn) {
-    case 8: return finish_by_form<8>(c, mode, Phat, body, rows, G, u_base, cu, oa, ob, s);
-    case 9: return finish_by_form<9>(c, mode, Phat, body, rows, G, u_base, cu, oa, ob, s);
-    case 10: return finish_by_form<10>(c, mode, Phat, body, rows, G, u_base, cu, oa, ob, s);
-    case 11: return finish_by_form<11>(c, mode, Phat, body, rows, G, u_base, cu, oa, ob, s);
-    case 12: return finish_by_form<12>(c, mode, Phat, body, rows, G, u_base, cu, oa, ob, s);
-    case 13: return finish_by_form<13>(c, mode, Phat, body, rows, G, u_base, cu, oa, ob, s);
+    case 8: return finish_by_form<8>(c, mode, Phat, nseg, body, rows, G, u_base, cu, oa, ob, s);
+    case 9: return finish_by_form<9>(c, mode, Phat, nseg, body, rows, G, u_base, cu, oa, ob, s);
+    case 10: return finish_by_form<10>(c, mode, Phat, nseg, body, rows, G, u_base, cu, oa, ob, s);
+    case 11: return finish_by_form<11>(c, mode, Phat, nseg, body, rows, G, u_base, cu, oa, ob, s);
+    case 12: return finish_by_form<12>(c, mode, Phat, nseg, body, rows, G, u_base, cu, oa, ob, s);
+    case 13: return finish_by_form<13>(c, mode, Phat, nseg, body, rows, G, u_base, cu, oa, ob, s);
     default: return cudaErrorInvalidValue;
   }
 }
@@ -407,7 +430,8 @@ cudaError_t pack_device(phe_ctx* c, const phe_ksk* k, u32 T, u32 rows, const u64
   u64* Phat = nullptr;
   cudaError_t e = cudaMallocAsync((void**)&D, (size_t)per * unit_bytes, s);
   if (e != cudaSuccess) return e;
-  e = cudaMallocAsync((void**)&Phat, (size_t)per * 2 * N * sizeof(u64), s);
+  const u32 nseg_max = mac_segments(c, k, 1);  // the smallest chunk needs the most segments
+  e = cudaMallocAsync((void**)&Phat, (size_t)nseg_max * per * 2 * N * sizeof(u64), s);
   for (u64 u0 = 0; u0 < units && e == cudaSuccess; u0 += per) {
     const u32 cu = (u32)std::min<u64>(per, units - u0);
     {
@@ -419,13 +443,14 @@ cudaError_t pack_device(phe_ctx* c, const phe_ksk* k, u32 T, u32 rows, const u64
       phe::NttJob nj{D, D, cu * nr, nullptr};
       e = phe::launch_input_ntt(c, &nj, 1, s);
     }
+    const u32 nseg = mac_segments(c, k, cu);
     if (e == cudaSuccess) {
       Span sp(c, phe::kKPackMac, s);
-      e = launch_mac(c, k, D, cu, Phat, s);
+      e = launch_mac(c, k, D, cu, nseg, Phat, s);
     }
     if (e == cudaSuccess) {
       Span sp(c, phe::kKPackFinish, s);
-      e = launch_finish(c, mode, Phat, body, rows, G, (u32)u0, cu, oa, ob, s);
+      e = launch_finish(c, mode, Phat, nseg, body, rows, G, (u32)u0, cu, oa, ob, s);
     }
   }
   cudaError_t f1 = Phat ? cudaFreeAsync(Phat, s) : cudaSuccess;
@@ -448,6 +473,7 @@ phe_status phe_ksk_upload(phe_ctx* c, const uint64_t* h_ka, const uint64_t* h_kb
                           uint32_t ell, phe_ksk** out) {
   if (!c || !h_ka || !h_kb || !out) return fail(PHE_EINVAL, "phe_ksk_upload: null argument");
   *out = nullptr;
+  if (c->pow2) return fail(PHE_EUNSUPPORTED, "phe_ksk_upload: packing needs an NTT-friendly q (not 2^%u)", c->rk.p2k);
   const u32 N = c->prm.N;
   if (n != N) return fail(PHE_EINVAL, "phe_ksk_upload: n=%u must equal N=%u (LWE outputs of dimension N)", n, N);
   if (ell < 1 || ell > 4 || base_log < 1 || base_log > 30 || base_log * ell > 32)

@@ -92,3 +92,20 @@ def test_rns_modulus_is_validated(L, q, rns, msg):
         phe.phe_ctx_create(4096, q, 32, 0, rns=rns)
     assert ei.value.status == phe.PHE_EINVAL
     assert msg in str(ei.value)
+
+
+@pytest.mark.parametrize("N,q,k,rns,flags,msg", [
+    (2048, 1 << 39, 26, None, 0, "needs rns_p1"),
+    (2048, 1 << 39, 39, (synth.RNS_P1, synth.RNS_P2), 0, "log2_qout"),
+    (2048, 1 << 39, 26, (synth.RNS_P1, synth.RNS_P2), 1, "no 64-bit form"),
+    (2048, 1 << 45, 26, (synth.RNS_P1, synth.RNS_P2), 0, "exact products"),
+    (2048, 1 << 4, 2, (synth.RNS_P1, synth.RNS_P2), 0, "8 <= k"),
+])
+def test_power_of_two_modulus_is_validated(L, N, q, k, rns, flags, msg):
+    """q = 2^K (the paper's parameter set) runs through p1 p2 and needs the
+    exact-range condition N * 127 * 2^(K-1) < p1 p2 / 2 (2^45 at N = 2048
+    breaks it; 2^39 keeps it with L up to 4)."""
+    with pytest.raises(phe.PheError) as ei:
+        phe.phe_ctx_create(N, q, k, 0, rns=rns, flags=flags)
+    assert ei.value.status == phe.PHE_EINVAL
+    assert msg in str(ei.value)

@@ -208,3 +208,32 @@ def test_ksk_upload_rejects_bad_shapes(ctxs):
         assert ei.value.status == phe.PHE_EINVAL
     with pytest.raises(phe.PheError):
         phe.phe_ksk_upload(ctx, K[:128], K[:128], 26, 1)   # n != N
+
+
+def test_matmul_packed_host_buffers_match_device_call(ctxs):
+    import torch
+    N, T = 256, 5
+    ctx = ctxs(N, "rns")
+    q = synth.Q_RNS
+    W = synth.weights(300, 290, seed=41)
+    g = _rng(42)
+    KA = g.integers(0, q, (N, 2, N), dtype=np.uint64)
+    KB = g.integers(0, q, (N, 2, N), dtype=np.uint64)
+    A = g.integers(0, q, (T, 2, N), dtype=np.uint64)
+    B = g.integers(0, q, (T, 2, N), dtype=np.uint64)
+    w = phe.phe_weights_upload(ctx, W)
+    k = phe.phe_ksk_upload(ctx, KA, KB, 13, 2)
+    try:
+        oa = torch.empty((T, 2, N), dtype=torch.int32, device="cuda")
+        ob = torch.empty_like(oa)
+        phe.phe_matmul_packed(ctx, w, k, phe.PHE_FWD, T, to_dev_u64(A), to_dev_u64(B), oa, ob)
+        torch.cuda.synchronize()
+        hA = torch.from_numpy(A.view(np.int64)).pin_memory()
+        hB = torch.from_numpy(B.view(np.int64)).pin_memory()
+        ha = torch.empty((T, 2, N), dtype=torch.int32).pin_memory()
+        hb = torch.empty_like(ha).pin_memory()
+        phe.phe_matmul_packed_host(ctx, w, k, phe.PHE_FWD, T, hA, hB, ha, hb, tok_chunk=2)
+    finally:
+        phe.phe_ksk_free(k)
+        phe.phe_weights_free(w)
+    assert torch.equal(ha, oa.cpu()) and torch.equal(hb, ob.cpu())
