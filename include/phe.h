@@ -365,7 +365,8 @@ void phe_ksk_free(phe_ksk* k);
 uint64_t phe_ksk_device_bytes(const phe_ksk* k);
 
 /* Packs T x rows given LWE ciphertexts of dimension N.
- *   d_lwe_mask  [T][rows][N] uint64 mod q (as phe_matmul writes with PHE_OUT_RAW)
+ *   d_lwe_mask  [T][rows][N] uint64 words below q (as phe_matmul writes with PHE_OUT_RAW;
+ *               larger words give unspecified results, never a fault)
  *   d_lwe_body  [T][rows]    uint64 mod q
  *   d_out_a, d_out_b  [T][G][N]: uint32 words mod 2^log2_qout (PHE_OUT_SWITCHED)
  *               or uint64 mod q (PHE_OUT_RAW); RLWE_g of token t at (t*G + g)*N.
@@ -392,6 +393,44 @@ phe_status phe_matmul_packed(phe_ctx* ctx, const phe_weights* w, const phe_ksk* 
 phe_status phe_matmul_packed_host(phe_ctx* ctx, const phe_weights* w, const phe_ksk* k, int dir, uint32_t T,
                                   const uint64_t* h_in_mask, const uint64_t* h_in_body, void* h_out_a,
                                   void* h_out_b, uint32_t flags, uint32_t tok_chunk, void* stream);
+
+/* ------------------------------------------------------------------------
+ * Wire format (Sec. 4.4: the sizes of the client's and the server's
+ * messages; Sec. 4.5: the result goes back "packed into a bit-vector").
+ * A record is a little-endian bit stream of fixed-width fields: field m of
+ * width b occupies stream bits m*b .. m*b+b-1, stream bit j is bit j%8 of
+ * byte j/8, and the record is zero-padded to a multiple of 32 bits (4-byte
+ * aligned records).
+ *   input record  8-byte seed (little endian), then the N body words of one
+ *                 block at ceil(log2 q) bits (Sec. 3.1: the mask is
+ *                 regenerated from the seed); N = 2048, q = 2^39: 9992 bytes
+ *   LWE record    the N mask words, then the body, at log2_qout bits
+ *   RLWE record   A then B (2N words) at log2_qout bits; N = 2048 at 26 bits
+ *                 gives the 13312 bytes of Sec. 4.4
+ * ------------------------------------------------------------------------ */
+
+/* Record sizes in bytes for the context (any pointer may be NULL). */
+phe_status phe_wire_sizes(const phe_ctx* ctx, uint64_t* in_record, uint64_t* lwe_record, uint64_t* rlwe_record);
+
+/* Packs n_records records of fa words from d_a (record r at d_a + r*fa) then
+ * fb words from d_b (at d_b + r*fb), each taken mod 2^log2_qout, into
+ * consecutive records of 4*ceil((fa+fb)*log2_qout/32) bytes at d_out.
+ * Device buffers.  Errors: PHE_EINVAL, PHE_ECUDA. */
+phe_status phe_wire_pack(phe_ctx* ctx, const uint32_t* d_a, uint32_t fa, const uint32_t* d_b, uint32_t fb,
+                         uint64_t n_records, void* d_out, void* stream);
+
+/* Unpacks n_records consecutive input records (4-byte aligned) into d_seeds
+ * [n_records] and d_bodies [n_records][N].  Errors: PHE_EINVAL, PHE_ECUDA. */
+phe_status phe_wire_unpack_inputs(phe_ctx* ctx, const void* d_records, uint64_t n_records, uint64_t* d_seeds,
+                                  uint64_t* d_bodies, void* stream);
+
+/* The server call on wire records: T*L input records (token-major, block
+ * minor) in; out, with k == NULL, T*rows LWE records (phe_matmul_seeded's
+ * switched outputs), or with a key-switching key, T*ceil(rows/N) RLWE records
+ * (phe_pack's outputs).  Allocates its scratch (at most 2 GiB per token
+ * chunk) on `stream`.  Errors: as phe_matmul_seeded and phe_pack. */
+phe_status phe_matmul_wire(phe_ctx* ctx, const phe_weights* w, const phe_ksk* k, int dir, uint32_t T,
+                           const void* d_in_records, void* d_out_records, void* stream);
 
 /* Size of the fixed device scratch array used by phe_matmul_noalloc. */
 #define PHE_NOALLOC_MAX_SCRATCH_BYTES (16u << 20)

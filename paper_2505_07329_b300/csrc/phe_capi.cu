@@ -191,7 +191,7 @@ cudaError_t matmul_device(phe_ctx* c, const phe_weights::Dir& D, u32 T, const u6
   const u32 N = c->prm.N;
   Span call(c, phe::kKCall, s);
   u64* ahat = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&ahat, (size_t)T * D.L * N * sizeof(u64), s);
+  cudaError_t e = phe::ctx_malloc_async(c, &ahat, (size_t)T * D.L * N * sizeof(u64), s);
   if (e != cudaSuccess) return e;
   {
     Span sp(c, phe::kKInputNtt, s);
@@ -313,6 +313,20 @@ phe_status phe_ctx_create(const phe_params* prm, int device, phe_ctx** out) {
   c->logn = floor_log2(N);
   e = cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, device);
   if (e != cudaSuccess) { delete c; return cuda_fail(e, "cudaDeviceGetAttribute"); }
+  {
+    cudaMemPoolProps props{};
+    props.allocType = cudaMemAllocationTypePinned;
+    props.location.type = cudaMemLocationTypeDevice;
+    props.location.id = device;
+    e = cudaMemPoolCreate(&c->pool, &props);
+    uint64_t keep = UINT64_MAX;  // freed scratch stays mapped for the next call
+    if (e == cudaSuccess) e = cudaMemPoolSetAttribute(c->pool, cudaMemPoolAttrReleaseThreshold, &keep);
+    if (e != cudaSuccess) {
+      if (c->pool) cudaMemPoolDestroy(c->pool);
+      delete c;
+      return cuda_fail(e, "cudaMemPoolCreate");
+    }
+  }
 
   phe::RingConst& rc = c->rc;
   rc.q = q;
@@ -344,12 +358,12 @@ phe_status phe_ctx_create(const phe_params* prm, int device, phe_ctx** out) {
   if (rns_modulus) {
     psi1 = (u32)primitive_root_2n(p1, N);
     psi2 = (u32)primitive_root_2n(p2, N);
-    if (!psi1 || !psi2) { delete c; return fail(PHE_EINVAL, "no primitive 2N-th root of unity mod p1 or p2"); }
+    if (!psi1 || !psi2) { cudaMemPoolDestroy(c->pool); delete c; return fail(PHE_EINVAL, "no primitive 2N-th root of unity mod p1 or p2"); }
     if (!pow2) psi = crt2(psi1, p1, psi2, p2);
   } else {
     psi = primitive_root_2n(q, N);
   }
-  if (!psi && !pow2) { delete c; return fail(PHE_EINVAL, "no primitive 2N-th root of unity found for q"); }
+  if (!psi && !pow2) { cudaMemPoolDestroy(c->pool); delete c; return fail(PHE_EINVAL, "no primitive 2N-th root of unity found for q"); }
 
   // 64-bit tables mod q (none for q = 2^k: everything runs through p1 p2)
   phe_status st = pow2 ? PHE_OK : build_tables(c, [&](u32 br, bool inverse) -> ulonglong2 {
@@ -403,6 +417,7 @@ phe_status phe_ctx_create(const phe_params* prm, int device, phe_ctx** out) {
   if (st != PHE_OK) {
     free_tables(c->tab);
     free_tables(c->tab32);
+    cudaMemPoolDestroy(c->pool);
     delete c;
     return st;
   }
@@ -423,6 +438,8 @@ void phe_ctx_destroy(phe_ctx* c) {
   for (auto e : c->tracer.pool) cudaEventDestroy(e);
   free_tables(c->tab);
   free_tables(c->tab32);
+  // a pool with frees still in flight is released once they complete
+  if (c->pool) cudaMemPoolDestroy(c->pool);
   delete c;
 }
 
@@ -592,10 +609,10 @@ phe_status phe_matmul_host(phe_ctx* c, const phe_weights* w, int dir, uint32_t T
   const u32 nchunks = (T + tc - 1) / tc;
   for (int i = 0; i < 2 && i < (int)nchunks && e == cudaSuccess; ++i) {
     cudaStream_t s = c->side[i];
-    if ((e = cudaMallocAsync((void**)&buf[i].a, tc * in_tok, s)) != cudaSuccess) break;
-    if ((e = cudaMallocAsync((void**)&buf[i].b, tc * in_tok, s)) != cudaSuccess) break;
-    if ((e = cudaMallocAsync((void**)&buf[i].om, tc * om_tok, s)) != cudaSuccess) break;
-    e = cudaMallocAsync((void**)&buf[i].ob, tc * ob_tok, s);
+    if ((e = phe::ctx_malloc_async(c, &buf[i].a, tc * in_tok, s)) != cudaSuccess) break;
+    if ((e = phe::ctx_malloc_async(c, &buf[i].b, tc * in_tok, s)) != cudaSuccess) break;
+    if ((e = phe::ctx_malloc_async(c, &buf[i].om, tc * om_tok, s)) != cudaSuccess) break;
+    e = phe::ctx_malloc_async(c, &buf[i].ob, tc * ob_tok, s);
   }
   for (u32 n = 0; n < nchunks && e == cudaSuccess; ++n) {
     const u32 t0 = n * tc, tn = (T - t0 < tc) ? T - t0 : tc;
@@ -700,9 +717,9 @@ phe_status phe_client_encrypt(phe_ctx* c, uint32_t T, uint32_t d, const uint64_t
   const u32 blocks = T * L;
   u64* ahat = nullptr;
   ulonglong2* shat = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&ahat, (size_t)blocks * N * sizeof(u64), s);
+  cudaError_t e = phe::ctx_malloc_async(c, &ahat, (size_t)blocks * N * sizeof(u64), s);
   if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(A_hat)");
-  e = cudaMallocAsync((void**)&shat, (size_t)N * sizeof(ulonglong2), s);
+  e = phe::ctx_malloc_async(c, &shat, (size_t)N * sizeof(ulonglong2), s);
   if (e == cudaSuccess) {
     phe::NttJob nj{reinterpret_cast<const u64*>(d_A), ahat, blocks};
     e = phe::launch_input_ntt(c, &nj, 1, s, /*force64=*/true);

@@ -42,6 +42,7 @@ struct NttJob {             // forward transform of T*L input blocks
   u64* dst;                 // A_hat layout [blocks][N]
   u32 blocks;
   const u64* seeds = nullptr;  // [blocks] 64-bit seeds: masks expanded on the fly
+  const int32_t* digits = nullptr;  // [blocks][N] small signed integers instead of src (packing digits)
 };
 
 enum OutMode : int { kOutSwitched = 0, kOutRaw = 1, kOutRing = 2, kPow2 = 4 /* flag: q = 2^k via the RNS form */ };
@@ -100,6 +101,10 @@ struct phe_ctx {
   phe::Tables tab32;      // RNS form (RNS contexts)
   int num_sms = 0;
   cudaStream_t side[2] = {nullptr, nullptr};  // streams for overlapped host-buffer chunks
+  // The context's own stream-ordered memory pool: scratch freed at the end of
+  // a call stays mapped for the next one (the device's default pool would
+  // release it at every synchronization and map it again).
+  cudaMemPool_t pool = nullptr;
   phe::Tracer tracer;
 };
 
@@ -148,6 +153,13 @@ struct Span {
     c->tracer.recs.push_back({kid, a, b});
   }
 };
+
+// Scratch for one call, from the context's pool, ordered on `s` (release it
+// with cudaFreeAsync on a stream ordered after its last use).
+template <class T>
+inline cudaError_t ctx_malloc_async(const phe_ctx* c, T** p, size_t bytes, cudaStream_t s) {
+  return cudaMallocFromPoolAsync(reinterpret_cast<void**>(p), bytes, c->pool, s);
+}
 
 // Launchers (phe_kernels.cu).  All asynchronous on `s`.
 // The hot-path launchers use the context's form (RNS when c->rns) unless

@@ -74,17 +74,28 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB)
 #pragma unroll
     for (int e = 0; e < 16; ++e) v[e] = buf64[pad_idx(pass_pos<LOGN, NP - 1>(p, e))];
     __syncthreads();
-  } else {
+  } else if (!job.digits) {
     const u64* src = job.src + (size_t)(active ? b : 0) * S::N;
 #pragma unroll
     for (int e = 0; e < 16; ++e) v[e] = active ? reduce_word(src[pass_pos<LOGN, NP - 1>(p, e)], rc) : 0ull;
   }
   W x[16];
+  if (job.digits) {
+    // small signed integers (|d| < 2^31): d, or the modulus plus d
+    const int32_t* src = job.digits + (size_t)(active ? b : 0) * S::N;
 #pragma unroll
-  for (int e = 0; e < 16; ++e) {
-    if constexpr (P2) x[e] = pow2_residues(v[e], rk);
-    else if constexpr (RNS) x[e] = to_residues(v[e], rk);
-    else x[e] = v[e];
+    for (int e = 0; e < 16; ++e) {
+      const int d = active ? src[pass_pos<LOGN, NP - 1>(p, e)] : 0;
+      if constexpr (RNS) x[e] = make_uint2(d < 0 ? rk.p1 + d : (u32)d, d < 0 ? rk.p2 + d : (u32)d);
+      else x[e] = d < 0 ? rc.q - (u64)(-(long long)d) : (u64)d;
+    }
+  } else {
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      if constexpr (P2) x[e] = pow2_residues(v[e], rk);
+      else if constexpr (RNS) x[e] = to_residues(v[e], rk);
+      else x[e] = v[e];
+    }
   }
   ntt_regs<LOGN>(x, p, buf, reinterpret_cast<const typename R::Tw*>(tw0v),
                  reinterpret_cast<const typename R::Tw*>(twcv), make_ring<RNS>(rc, rk, false));

@@ -10,7 +10,7 @@
 // products.  Kernels:
 //   pack_decompose_kernel  digits d_l(a_j[i]) of the masks, transposed so
 //                          that D_il is a row over j (natural order, mod q)
-//   input_ntt_kernel       D_il -> NTT domain, in place
+//   input_ntt_kernel       D_il (int32 digits) -> NTT domain
 //   pack_mac_kernel        per NTT slot: sum over (i,l) of D_hat * KSK_hat
 //                          (the key carries -N^-1 and Shoup quotients)
 //   pack_finish_kernel     inverse NTT of A_hat and B_hat, + b_j X^j, switch
@@ -56,15 +56,15 @@ __device__ __forceinline__ void gadget_digits(u64 a, const RingConst& rcK, u32 b
   }
 }
 
-// Masks [T][rows][N] (mod q) -> digit rows D[u][i*ell + l][j] of the units
-// u_base + u, unit = t*G + g,
-// holding d_l(a_{gN+j}[i]) mod q for gN + j < rows and 0 past the last row.
+// Masks [T][rows][N] (words below q) -> digit rows D[u][i*ell + l][j] of
+// the units u_base + u, unit = t*G + g, holding the signed digit
+// d_l(a_{gN+j}[i]) for gN + j < rows and 0 past the last row.
 // A 32x32 tile of (j, i) goes through shared memory so that both the load
 // (along i) and the store (along j) are coalesced.
 template <int ELL>
 __global__ void __launch_bounds__(256)
     pack_decompose_kernel(const u64* __restrict__ mask, u32 rows, u32 N, u32 G, u32 u_base, u32 base_log,
-                          RingConst rcK, u64* __restrict__ D) {
+                          RingConst rcK, int32_t* __restrict__ D) {
   __shared__ int tile[ELL][32][33];
   const u32 u = blockIdx.z;  // unit within the chunk; D holds the chunk's units
   const u32 t = (u_base + u) / G, g = (u_base + u) % G;
@@ -74,7 +74,7 @@ __global__ void __launch_bounds__(256)
     const u32 j = j0 + k, row = g * N + j;
     int d[ELL];
     if (row < rows) {
-      gadget_digits<ELL>(reduce_word(mask[((size_t)t * rows + row) * N + i0 + tx], rcK), rcK, base_log, d);
+      gadget_digits<ELL>(mask[((size_t)t * rows + row) * N + i0 + tx], rcK, base_log, d);
     } else {
 #pragma unroll
       for (int l = 0; l < ELL; ++l) d[l] = 0;
@@ -83,14 +83,10 @@ __global__ void __launch_bounds__(256)
     for (int l = 0; l < ELL; ++l) tile[l][tx][k] = d[l];
   }
   __syncthreads();
-  const u64 q = rcK.q;
   for (u32 k = ty; k < 32; k += 8) {
     const u32 i = i0 + k;
 #pragma unroll
-    for (int l = 0; l < ELL; ++l) {
-      const int v = tile[l][k][tx];
-      D[(((size_t)u * N + i) * ELL + l) * N + j0 + tx] = (v < 0) ? q - (u64)(-v) : (u64)v;
-    }
+    for (int l = 0; l < ELL; ++l) D[(((size_t)u * N + i) * ELL + l) * N + j0 + tx] = tile[l][k][tx];
   }
 }
 
@@ -128,15 +124,6 @@ __global__ void ksk_finish_kernel(const u64* __restrict__ src, void* __restrict_
   }
 }
 
-// a mod p for a < 2^43 (a sum of at most 2^12 lazy products below 2p).
-__device__ __forceinline__ u32 reduce_acc32(u64 a, u32 p, u32 c32, u32 c32p) {
-  u32 lo = (u32)a;
-  lo = (lo >= 4 * p) ? lo - 4 * p : lo;
-  lo = sub_if32(sub_if32(lo, 2 * p), p);
-  const u32 hi = sub_if32(mul_shoup32((u32)(a >> 32), c32, c32p, p), p);
-  return sub_if32(lo + hi, p);
-}
-
 // Per NTT slot s, unit u and segment g of the contraction:
 //   P_hat[g][u][c][s] = sum_{r in segment g} D_hat[u][r][s] K_hat[r][c][s]   (c = 0: A, 1: B),
 // fully reduced.  A block covers 256 slots, one segment and UB units, so each
@@ -144,7 +131,7 @@ __device__ __forceinline__ u32 reduce_acc32(u64 a, u32 p, u32 c32, u32 c32p) {
 // contraction) give enough blocks to fill the GPU and are summed by the
 // finishing kernel.
 template <bool RNS, int UB>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
     pack_mac_kernel(const u64* __restrict__ Dhat, const void* __restrict__ khatv, u32 nr, u32 rseg, u32 N, u32 units,
                     u64* __restrict__ Phat, RingConst rc, RnsConst rk) {
   const u32 s = blockIdx.x * blockDim.x + threadIdx.x;
@@ -155,7 +142,8 @@ __global__ void __launch_bounds__(256)
   u64* part = Phat + (size_t)seg * units * 2 * N;
   if constexpr (RNS) {
     const uint4* kh = reinterpret_cast<const uint4*>(khatv);
-    u64 acc[UB][4];
+    const u32 p1 = rk.p1, p2 = rk.p2, p1x2 = 2 * rk.p1, p2x2 = 2 * rk.p2;
+    u32 acc[UB][4];  // kept in [0, 2p): each Shoup product is below 2p
 #pragma unroll
     for (int k = 0; k < UB; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0;
 #pragma unroll 2
@@ -166,10 +154,10 @@ __global__ void __launch_bounds__(256)
       for (int k = 0; k < UB; ++k) {
         if (k < nu) {
           const uint2 d = __ldg(reinterpret_cast<const uint2*>(Dhat) + ((size_t)(u0 + k) * nr + r) * N + s);
-          acc[k][0] += mul_shoup32(d.x, ka.x, ka.y, rk.p1);  // each < 2p: 2^12 of them stay below 2^43
-          acc[k][1] += mul_shoup32(d.y, ka.z, ka.w, rk.p2);
-          acc[k][2] += mul_shoup32(d.x, kb.x, kb.y, rk.p1);
-          acc[k][3] += mul_shoup32(d.y, kb.z, kb.w, rk.p2);
+          acc[k][0] = sub_if32(acc[k][0] + mul_shoup32(d.x, ka.x, ka.y, p1), p1x2);
+          acc[k][1] = sub_if32(acc[k][1] + mul_shoup32(d.y, ka.z, ka.w, p2), p2x2);
+          acc[k][2] = sub_if32(acc[k][2] + mul_shoup32(d.x, kb.x, kb.y, p1), p1x2);
+          acc[k][3] = sub_if32(acc[k][3] + mul_shoup32(d.y, kb.z, kb.w, p2), p2x2);
         }
       }
     }
@@ -177,10 +165,8 @@ __global__ void __launch_bounds__(256)
     for (int k = 0; k < UB; ++k) {
       if (k < nu) {
         uint2* out = reinterpret_cast<uint2*>(part) + (size_t)(u0 + k) * 2 * N + s;
-        out[0] = make_uint2(reduce_acc32(acc[k][0], rk.p1, rk.c32a, rk.c32ap),
-                            reduce_acc32(acc[k][1], rk.p2, rk.c32b, rk.c32bp));
-        out[N] = make_uint2(reduce_acc32(acc[k][2], rk.p1, rk.c32a, rk.c32ap),
-                            reduce_acc32(acc[k][3], rk.p2, rk.c32b, rk.c32bp));
+        out[0] = make_uint2(sub_if32(acc[k][0], p1), sub_if32(acc[k][1], p2));
+        out[N] = make_uint2(sub_if32(acc[k][2], p1), sub_if32(acc[k][3], p2));
       }
     }
   } else {
@@ -341,7 +327,7 @@ constexpr int kMacUnits = 8;                        // units per pack_mac_kernel
 constexpr uint64_t kPackScratchBytes = 2ull << 30;  // digit rows in flight per phe_pack chunk
 
 cudaError_t launch_decompose(const phe_ctx* c, const phe_ksk* k, const u64* mask, u32 rows, u32 G, u32 u_base,
-                             u32 cu, u64* D, cudaStream_t s) {
+                             u32 cu, int32_t* D, cudaStream_t s) {
   const u32 N = c->prm.N;
   phe::RingConst rcK = c->rc;
   rcK.log2_qout = k->base_log * k->ell;
@@ -423,15 +409,17 @@ cudaError_t pack_device(phe_ctx* c, const phe_ksk* k, u32 T, u32 rows, const u64
   const u32 N = c->prm.N, nr = k->n * k->ell;
   const u32 G = (rows + N - 1) / N;
   const u64 units = (u64)T * G;
-  const u64 unit_bytes = (u64)nr * N * sizeof(u64);
+  // per unit: int32 digit rows, then their transforms (8 bytes per word)
+  const u64 unit_bytes = (u64)nr * N * (sizeof(int32_t) + sizeof(u64));
   const u32 per = (u32)std::max<u64>(1, std::min<u64>(units, kPackScratchBytes / unit_bytes));
   Span call(c, phe::kKPackCall, s);
-  u64* D = nullptr;
+  u64* Dhat = nullptr;
   u64* Phat = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&D, (size_t)per * unit_bytes, s);
+  cudaError_t e = phe::ctx_malloc_async(c, &Dhat, (size_t)per * unit_bytes, s);
   if (e != cudaSuccess) return e;
+  int32_t* D = reinterpret_cast<int32_t*>(Dhat + (size_t)per * nr * N);
   const u32 nseg_max = mac_segments(c, k, 1);  // the smallest chunk needs the most segments
-  e = cudaMallocAsync((void**)&Phat, (size_t)nseg_max * per * 2 * N * sizeof(u64), s);
+  e = phe::ctx_malloc_async(c, &Phat, (size_t)nseg_max * per * 2 * N * sizeof(u64), s);
   for (u64 u0 = 0; u0 < units && e == cudaSuccess; u0 += per) {
     const u32 cu = (u32)std::min<u64>(per, units - u0);
     {
@@ -440,13 +428,13 @@ cudaError_t pack_device(phe_ctx* c, const phe_ksk* k, u32 T, u32 rows, const u64
     }
     if (e == cudaSuccess) {
       Span sp(c, phe::kKInputNtt, s);
-      phe::NttJob nj{D, D, cu * nr, nullptr};
+      phe::NttJob nj{nullptr, Dhat, cu * nr, nullptr, D};
       e = phe::launch_input_ntt(c, &nj, 1, s);
     }
     const u32 nseg = mac_segments(c, k, cu);
     if (e == cudaSuccess) {
       Span sp(c, phe::kKPackMac, s);
-      e = launch_mac(c, k, D, cu, nseg, Phat, s);
+      e = launch_mac(c, k, Dhat, cu, nseg, Phat, s);
     }
     if (e == cudaSuccess) {
       Span sp(c, phe::kKPackFinish, s);
@@ -454,7 +442,7 @@ cudaError_t pack_device(phe_ctx* c, const phe_ksk* k, u32 T, u32 rows, const u64
     }
   }
   cudaError_t f1 = Phat ? cudaFreeAsync(Phat, s) : cudaSuccess;
-  cudaError_t f2 = cudaFreeAsync(D, s);
+  cudaError_t f2 = cudaFreeAsync(Dhat, s);
   if (e != cudaSuccess) return e;
   return f1 != cudaSuccess ? f1 : f2;
 }
@@ -568,7 +556,7 @@ phe_status phe_matmul_packed(phe_ctx* c, const phe_weights* w, const phe_ksk* k,
   const u32 per = (u32)std::max<u64>(1, std::min<u64>(T, kPackScratchBytes / tok_bytes));
   const size_t osz = flags == PHE_OUT_RAW ? sizeof(u64) : sizeof(u32);
   u64* raw = nullptr;
-  cudaError_t e = cudaMallocAsync((void**)&raw, (size_t)per * tok_bytes, s);
+  cudaError_t e = phe::ctx_malloc_async(c, &raw, (size_t)per * tok_bytes, s);
   if (e != cudaSuccess) return cuda_fail(e, "phe_matmul_packed: scratch");
   u64* raw_body = raw + (size_t)per * rows * N;
   for (u32 t0 = 0; t0 < T && st == PHE_OK; t0 += per) {
@@ -619,10 +607,10 @@ phe_status phe_matmul_packed_host(phe_ctx* c, const phe_weights* w, const phe_ks
   const u32 nchunks = (T + tc - 1) / tc;
   for (int i = 0; i < 2 && i < (int)nchunks && e == cudaSuccess; ++i) {
     cudaStream_t s = c->side[i];
-    if ((e = cudaMallocAsync((void**)&buf[i].a, tc * in_tok, s)) != cudaSuccess) break;
-    if ((e = cudaMallocAsync((void**)&buf[i].b, tc * in_tok, s)) != cudaSuccess) break;
-    if ((e = cudaMallocAsync((void**)&buf[i].oa, tc * out_tok, s)) != cudaSuccess) break;
-    e = cudaMallocAsync((void**)&buf[i].ob, tc * out_tok, s);
+    if ((e = phe::ctx_malloc_async(c, &buf[i].a, tc * in_tok, s)) != cudaSuccess) break;
+    if ((e = phe::ctx_malloc_async(c, &buf[i].b, tc * in_tok, s)) != cudaSuccess) break;
+    if ((e = phe::ctx_malloc_async(c, &buf[i].oa, tc * out_tok, s)) != cudaSuccess) break;
+    e = phe::ctx_malloc_async(c, &buf[i].ob, tc * out_tok, s);
   }
   for (u32 n = 0; n < nchunks && e == cudaSuccess && st == PHE_OK; ++n) {
     const u32 t0 = n * tc, tn = std::min(tc, T - t0);

@@ -141,9 +141,9 @@ cudaError_t launch_iteration(phe_server* s, Iteration& it) {
       q = &s->reqs[j.id];
     }
     const phe_weights::Dir& D = q->r.w->dir[q->r.dir];
-    if ((e = cudaMallocAsync((void**)&j.ahat, (size_t)j.tn * D.L * N * 8, s->stream)) != cudaSuccess) return e;
-    if ((e = cudaMallocAsync(&j.om, (size_t)j.tn * D.rows * N * osz, s->stream)) != cudaSuccess) return e;
-    if ((e = cudaMallocAsync(&j.ob, (size_t)j.tn * D.rows * osz, s->stream)) != cudaSuccess) return e;
+    if ((e = phe::ctx_malloc_async(s->ctx, &j.ahat, (size_t)j.tn * D.L * N * 8, s->stream)) != cudaSuccess) return e;
+    if ((e = phe::ctx_malloc_async(s->ctx, &j.om, (size_t)j.tn * D.rows * N * osz, s->stream)) != cudaSuccess) return e;
+    if ((e = phe::ctx_malloc_async(s->ctx, &j.ob, (size_t)j.tn * D.rows * osz, s->stream)) != cudaSuccess) return e;
     const size_t tok_words = (size_t)D.L * N;
     phe::NttJob nj{nullptr, j.ahat, j.tn * D.L};
     if (q->r.d_in_seeds)

@@ -121,6 +121,10 @@ SIGNATURES = {
     "phe_pack": (_i32, [_vp, _vp, _u32, _u32, _vp, _vp, _vp, _vp, _u32, _vp]),
     "phe_matmul_packed": (_i32, [_vp, _vp, _vp, _i32, _u32, _vp, _vp, _vp, _vp, _u32, _vp]),
     "phe_matmul_packed_host": (_i32, [_vp, _vp, _vp, _i32, _u32, _vp, _vp, _vp, _vp, _u32, _u32, _vp]),
+    "phe_wire_sizes": (_i32, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
+    "phe_wire_pack": (_i32, [_vp, _vp, _u32, _vp, _u32, _u64, _vp, _vp]),
+    "phe_wire_unpack_inputs": (_i32, [_vp, _vp, _u64, _vp, _vp, _vp]),
+    "phe_matmul_wire": (_i32, [_vp, _vp, _vp, _i32, _u32, _vp, _vp, _vp]),
 }
 
 _lib = None
@@ -417,3 +421,23 @@ def phe_matmul_packed_host(ctx, w, k, direction: int, T: int, h_in_mask, h_in_bo
                            flags: int = PHE_OUT_SWITCHED, tok_chunk: int = 8, stream=None) -> None:
     _check(lib().phe_matmul_packed_host(ctx, w, k, direction, T, _hptr(h_in_mask), _hptr(h_in_body),
                                         _hptr(h_out_a), _hptr(h_out_b), flags, tok_chunk, _stream(stream)))
+
+
+def phe_wire_sizes(ctx) -> dict:
+    """Record sizes in bytes: {"input", "lwe", "rlwe"}."""
+    a, b, c = _u64(), _u64(), _u64()
+    _check(lib().phe_wire_sizes(ctx, ctypes.byref(a), ctypes.byref(b), ctypes.byref(c)))
+    return {"input": a.value, "lwe": b.value, "rlwe": c.value}
+
+
+def phe_wire_pack(ctx, a, fa: int, b, fb: int, n_records: int, out, stream=None) -> None:
+    _check(lib().phe_wire_pack(ctx, _dptr(a), fa, _dptr(b), fb, n_records, _dptr(out), _stream(stream)))
+
+
+def phe_wire_unpack_inputs(ctx, records, n_records: int, seeds, bodies, stream=None) -> None:
+    _check(lib().phe_wire_unpack_inputs(ctx, _dptr(records), n_records, _dptr(seeds), _dptr(bodies),
+                                        _stream(stream)))
+
+
+def phe_matmul_wire(ctx, w, k, direction: int, T: int, in_records, out_records, stream=None) -> None:
+    _check(lib().phe_matmul_wire(ctx, w, k, direction, T, _dptr(in_records), _dptr(out_records), _stream(stream)))
