@@ -42,8 +42,8 @@ METRIC = "encrypted W·[x] tokens/s per Llama-1B layer; p50/p99 latency; % of ro
 # with ncu, and the algorithmic bytes of that launch.  Valid only for the
 # kernel sources the counters were taken on (hash of phe_kernels.cu +
 # phe_device.cuh).
-TRAFFIC_KERNEL_HASH = "71035676985d25fb"
-TRAFFIC_BYTES_PER_LAUNCH = 96444.6e6
+TRAFFIC_KERNEL_HASH = "d882f277542bdd90"
+TRAFFIC_BYTES_PER_LAUNCH = 96353.6e6
 TRAFFIC_ALG_BYTES_PER_LAUNCH = 95891.8e6
 
 
@@ -664,8 +664,8 @@ def measure_e2e(phe, ctx, weights, wl, mm, keys, inputs, tokens, stream):
     dt = time.perf_counter() - t0
     return {"value": tokens * steps / dt, "unit": "tokens/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "tokens_per_step": tokens,
-            "note": "host-buffer C-ABI call; every result word of the layer's 14 products returns to pinned host "
-                    "memory (output explosion without the paper's keyswitch packing)"}
+            "note": "host-buffer C-ABI call; every LWE result word of the layer's 14 products returns to pinned "
+                    "host memory (unpacked outputs; `packed.e2e` has the path with Eq. (pack_rotate))"}
 
 
 def _negacyclic_small(a, s, mod):
