@@ -124,36 +124,75 @@ __global__ void ksk_finish_kernel(const u64* __restrict__ src, void* __restrict_
   }
 }
 
+// Asynchronous global -> shared copies (cp.async, sm_80 and later): each
+// thread stages only the words it reads itself, so the pipeline needs no
+// block barrier, only the thread's own wait_group.
+__device__ __forceinline__ void cp_async16(void* smem, const void* g) {
+  const u32 sa = (u32)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(sa), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async8(void* smem, const void* g) {
+  const u32 sa = (u32)__cvta_generic_to_shared(smem);
+  asm volatile("cp.async.ca.shared.global [%0], [%1], 8;\n" ::"r"(sa), "l"(g) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int PENDING>
+__device__ __forceinline__ void cp_async_wait() {
+  asm volatile("cp.async.wait_group %0;\n" ::"n"(PENDING) : "memory");
+}
+
 // Per NTT slot s, unit u and segment g of the contraction:
 //   P_hat[g][u][c][s] = sum_{r in segment g} D_hat[u][r][s] K_hat[r][c][s]   (c = 0: A, 1: B),
 // fully reduced.  A block covers 256 slots, one segment and UB units, so each
 // key entry it loads serves UB units; the segments (a split of the n*ell
 // contraction) give enough blocks to fill the GPU and are summed by the
-// finishing kernel.
-template <bool RNS, int UB>
-__global__ void __launch_bounds__(256, 4)
+// finishing kernel.  The key entries (16 bytes) and transformed digits
+// (8 bytes) of row r stream through a STAGES-deep ring in shared memory, so
+// that a thread keeps STAGES-1 rows of loads in flight.
+template <bool RNS, int UB, int STAGES>
+__global__ void __launch_bounds__(256, 2)
     pack_mac_kernel(const u64* __restrict__ Dhat, const void* __restrict__ khatv, u32 nr, u32 rseg, u32 N, u32 units,
                     u64* __restrict__ Phat, RingConst rc, RnsConst rk) {
-  const u32 s = blockIdx.x * blockDim.x + threadIdx.x;
+  extern __shared__ uint4 mac_smem[];
+  uint4* sk = mac_smem;                                        // [STAGES][2][256] key entries
+  uint2* sd = reinterpret_cast<uint2*>(mac_smem + STAGES * 2 * 256);  // [STAGES][UB][256] digit words
+  const u32 tid = threadIdx.x;
+  const u32 s = blockIdx.x * blockDim.x + tid;  // N is a multiple of 256: s < N
   const u32 seg = blockIdx.y, u0 = blockIdx.z * UB;
-  if (s >= N) return;
   const int nu = (int)min((u32)UB, units - u0);
   const u32 r0 = seg * rseg, r1 = min(nr, r0 + rseg);
   u64* part = Phat + (size_t)seg * units * 2 * N;
+  const uint4* kh = reinterpret_cast<const uint4*>(khatv);
+  const uint2* dh = reinterpret_cast<const uint2*>(Dhat);
+  auto issue = [&](u32 r, int st) {
+    cp_async16(&sk[(st * 2) * 256 + tid], &kh[((size_t)r * 2) * N + s]);
+    cp_async16(&sk[(st * 2 + 1) * 256 + tid], &kh[((size_t)r * 2 + 1) * N + s]);
+#pragma unroll
+    for (int k = 0; k < UB; ++k)
+      if (k < nu) cp_async8(&sd[(st * UB + k) * 256 + tid], &dh[((size_t)(u0 + k) * nr + r) * N + s]);
+  };
+#pragma unroll
+  for (int st = 0; st < STAGES - 1; ++st) {
+    if (r0 + st < r1) issue(r0 + st, st);
+    cp_async_commit();
+  }
   if constexpr (RNS) {
-    const uint4* kh = reinterpret_cast<const uint4*>(khatv);
     const u32 p1 = rk.p1, p2 = rk.p2, p1x2 = 2 * rk.p1, p2x2 = 2 * rk.p2;
     u32 acc[UB][4];  // kept in [0, 2p): each Shoup product is below 2p
 #pragma unroll
     for (int k = 0; k < UB; ++k) acc[k][0] = acc[k][1] = acc[k][2] = acc[k][3] = 0;
-#pragma unroll 2
     for (u32 r = r0; r < r1; ++r) {
-      const uint4 ka = __ldg(&kh[((size_t)r * 2) * N + s]);
-      const uint4 kb = __ldg(&kh[((size_t)r * 2 + 1) * N + s]);
+      const u32 rn = r + STAGES - 1;
+      if (rn < r1) issue(rn, (int)((rn - r0) % STAGES));
+      cp_async_commit();
+      cp_async_wait<STAGES - 1>();
+      const int st = (int)((r - r0) % STAGES);
+      const uint4 ka = sk[(st * 2) * 256 + tid];
+      const uint4 kb = sk[(st * 2 + 1) * 256 + tid];
 #pragma unroll
       for (int k = 0; k < UB; ++k) {
         if (k < nu) {
-          const uint2 d = __ldg(reinterpret_cast<const uint2*>(Dhat) + ((size_t)(u0 + k) * nr + r) * N + s);
+          const uint2 d = sd[(st * UB + k) * 256 + tid];
           acc[k][0] = sub_if32(acc[k][0] + mul_shoup32(d.x, ka.x, ka.y, p1), p1x2);
           acc[k][1] = sub_if32(acc[k][1] + mul_shoup32(d.y, ka.z, ka.w, p2), p2x2);
           acc[k][2] = sub_if32(acc[k][2] + mul_shoup32(d.x, kb.x, kb.y, p1), p1x2);
@@ -170,19 +209,22 @@ __global__ void __launch_bounds__(256, 4)
       }
     }
   } else {
-    const ulonglong2* kh = reinterpret_cast<const ulonglong2*>(khatv);
     const u64 q = rc.q, q4 = rc.q4;
     u64 acc[UB][2];
 #pragma unroll
     for (int k = 0; k < UB; ++k) acc[k][0] = acc[k][1] = 0;
-#pragma unroll 2
     for (u32 r = r0; r < r1; ++r) {
-      const ulonglong2 ka = __ldg(&kh[((size_t)r * 2) * N + s]);
-      const ulonglong2 kb = __ldg(&kh[((size_t)r * 2 + 1) * N + s]);
+      const u32 rn = r + STAGES - 1;
+      if (rn < r1) issue(rn, (int)((rn - r0) % STAGES));
+      cp_async_commit();
+      cp_async_wait<STAGES - 1>();
+      const int st = (int)((r - r0) % STAGES);
+      const ulonglong2 ka = reinterpret_cast<const ulonglong2*>(sk)[(st * 2) * 256 + tid];
+      const ulonglong2 kb = reinterpret_cast<const ulonglong2*>(sk)[(st * 2 + 1) * 256 + tid];
 #pragma unroll
       for (int k = 0; k < UB; ++k) {
         if (k < nu) {
-          const u64 d = __ldg(&Dhat[((size_t)(u0 + k) * nr + r) * N + s]);
+          const u64 d = reinterpret_cast<const u64*>(sd)[(st * UB + k) * 256 + tid];
           const u64 a = acc[k][0] + mul_shoup_lazy(d, ka.x, ka.y, q);  // each term < 4q, sum < 8q
           const u64 b = acc[k][1] + mul_shoup_lazy(d, kb.x, kb.y, q);
           acc[k][0] = (a >= q4) ? a - q4 : a;
@@ -199,6 +241,7 @@ __global__ void __launch_bounds__(256, 4)
       }
     }
   }
+  cp_async_wait<0>();  // no copy outlives the block
 }
 
 // Inverse transform of P_hat[u][c] (c = 0: A, c = 1: B), + b_{gN+m} at
@@ -324,6 +367,8 @@ struct DeviceGuard {
 };
 
 constexpr int kMacUnits = 8;                        // units per pack_mac_kernel block
+constexpr int kMacStages = 4;                       // rows in flight per pack_mac_kernel thread
+constexpr size_t kMacSmem = (size_t)kMacStages * 256 * (2 * 16 + kMacUnits * 8);
 constexpr uint64_t kPackScratchBytes = 2ull << 30;  // digit rows in flight per phe_pack chunk
 
 cudaError_t launch_decompose(const phe_ctx* c, const phe_ksk* k, const u64* mask, u32 rows, u32 G, u32 u_base,
@@ -355,10 +400,11 @@ cudaError_t launch_mac(const phe_ctx* c, const phe_ksk* k, const u64* Dhat, u32 
   const u32 N = c->prm.N, nr = k->n * k->ell;
   const u32 rseg = (nr + nseg - 1) / nseg;
   const dim3 grid(N / 256, nseg, (cu + kMacUnits - 1) / kMacUnits);
-  if (c->rns)
-    phe::pack_mac_kernel<true, kMacUnits><<<grid, 256, 0, s>>>(Dhat, k->khat, nr, rseg, N, cu, Phat, c->rc, c->rk);
-  else
-    phe::pack_mac_kernel<false, kMacUnits><<<grid, 256, 0, s>>>(Dhat, k->khat, nr, rseg, N, cu, Phat, c->rc, c->rk);
+  auto kern = c->rns ? phe::pack_mac_kernel<true, kMacUnits, kMacStages>
+                     : phe::pack_mac_kernel<false, kMacUnits, kMacStages>;
+  cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMacSmem);
+  if (e != cudaSuccess) return e;
+  kern<<<grid, 256, kMacSmem, s>>>(Dhat, k->khat, nr, rseg, N, cu, Phat, c->rc, c->rk);
   return cudaGetLastError();
 }
 

@@ -237,3 +237,27 @@ def test_matmul_packed_host_buffers_match_device_call(ctxs):
         phe.phe_ksk_free(k)
         phe.phe_weights_free(w)
     assert torch.equal(ha, oa.cpu()) and torch.equal(hb, ob.cpu())
+
+
+def test_pack_largest_ring_and_empty_calls(orc, ctxs):
+    """N = 8192 (the largest ring: the finishing kernel's exchange buffer is
+    above 48 KB of shared memory), 100 rows, sampled against the oracle; and
+    T = 0 / rows = 0 calls return without launching anything."""
+    N, T, rows = 8192, 1, 100
+    q = synth.Q_RNS
+    ctx = ctxs(N, "rns")
+    g = _rng(81)
+    KA = g.integers(0, q, (N, 1, N), dtype=np.uint64)
+    KB = g.integers(0, q, (N, 1, N), dtype=np.uint64)
+    masks = g.integers(0, q, (T, rows, N), dtype=np.uint64)
+    bodies = g.integers(0, q, (T, rows), dtype=np.uint64)
+    k = phe.phe_ksk_upload(ctx, KA, KB, 26, 1)
+    try:
+        ga, gb = _gpu_pack(ctx, k, masks, bodies, N, phe.PHE_OUT_RAW)
+        phe.phe_pack(ctx, k, 0, rows, None, None, None, None)
+        phe.phe_pack(ctx, k, 3, 0, None, None, None, None)
+    finally:
+        phe.phe_ksk_free(k)
+    rs = np.array([0, 1, 99, 100, 4096, 8191])
+    ea, eb = orc.pack_coeffs(masks[0], bodies[0], KA, KB, q, 26, 1, rs)
+    assert np.array_equal(ga[0, 0, rs], ea) and np.array_equal(gb[0, 0, rs], eb)
