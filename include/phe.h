@@ -376,13 +376,20 @@ uint64_t phe_ksk_device_bytes(const phe_ksk* k);
 phe_status phe_pack(phe_ctx* ctx, const phe_ksk* k, uint32_t T, uint32_t rows, const uint64_t* d_lwe_mask,
                      const uint64_t* d_lwe_body, void* d_out_a, void* d_out_b, uint32_t flags, void* stream);
 
-/* phe_matmul followed by phe_pack, token chunk by token chunk (the raw LWE
- * outputs of a chunk stay in a scratch buffer of at most 2 GiB): the paper's
- * whole server path, Eq. (LWEdot) then Eq. (pack_rotate).  Inputs as
- * phe_matmul; outputs as phe_pack with rows of direction `dir`. */
+/* The paper's whole server path, Eq. (LWEdot) then Eq. (pack_rotate), token
+ * chunk by token chunk: the product kernel switches the LWE masks straight to
+ * the gadget modulus B^ell (all that Decomp reads) and keeps the bodies mod
+ * q, in a scratch buffer of at most 2 GiB, then the packing runs on them.
+ * The result equals phe_matmul (PHE_OUT_RAW) followed by phe_pack.  Inputs
+ * as phe_matmul; outputs as phe_pack with rows of direction `dir`. */
 phe_status phe_matmul_packed(phe_ctx* ctx, const phe_weights* w, const phe_ksk* k, int dir, uint32_t T,
                              const uint64_t* d_in_mask, const uint64_t* d_in_body, void* d_out_a, void* d_out_b,
                              uint32_t flags, void* stream);
+
+/* phe_matmul_packed with seeded input masks (as phe_matmul_seeded). */
+phe_status phe_matmul_packed_seeded(phe_ctx* ctx, const phe_weights* w, const phe_ksk* k, int dir, uint32_t T,
+                                    const uint64_t* d_in_seeds, const uint64_t* d_in_body, void* d_out_a,
+                                    void* d_out_b, uint32_t flags, void* stream);
 
 /* phe_matmul_packed with HOST buffers, `tok_chunk` tokens at a time (0
  * selects 8): inputs host->device, the packed path, packed outputs

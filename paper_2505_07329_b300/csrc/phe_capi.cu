@@ -236,6 +236,21 @@ phe_status check_matmul_args(phe_ctx* c, const phe_weights* w, int dir, uint32_t
 
 namespace phe {
 void set_last_error(const char* msg) { g_err = msg; }
+
+void set_switch_target(RnsConst& k, u32 log2_target) {
+  const u32 p1 = k.p1, p2 = k.p2;
+  const u64 two_k = 1ull << log2_target;
+  k.a1 = (u32)(two_k / p1);
+  k.b1 = (u32)(two_k % p1);
+  k.b1p = shoup32(k.b1, p1);
+  k.a2 = (u32)(two_k / p2);
+  k.b2 = (u32)(two_k % p2);
+  k.b2p = shoup32(k.b2, p2);
+  k.inv_a2 = (u32)((1ull << 32) / p2);
+  k.half1 = (p1 - 1) / 2;
+  k.half2 = (p2 - 1) / 2;
+  k.kmask = (u32)(two_k - 1);
+}
 }  // namespace phe
 
 extern "C" {
@@ -381,17 +396,7 @@ phe_status phe_ctx_create(const phe_params* prm, int device, phe_ctx** out) {
     k.c32ap = shoup32(k.c32a, p1);
     k.c32b = (u32)((1ull << 32) % p2);
     k.c32bp = shoup32(k.c32b, p2);
-    const u64 two_k = 1ull << prm->log2_qout;
-    k.a1 = (u32)(two_k / p1);
-    k.b1 = (u32)(two_k % p1);
-    k.b1p = shoup32(k.b1, p1);
-    k.a2 = (u32)(two_k / p2);
-    k.b2 = (u32)(two_k % p2);
-    k.b2p = shoup32(k.b2, p2);
-    k.inv_a2 = (u32)((1ull << 32) / p2);
-    k.half1 = (p1 - 1) / 2;
-    k.half2 = (p2 - 1) / 2;
-    k.kmask = (u32)(two_k - 1);
+    phe::set_switch_target(k, prm->log2_qout);
     if (pow2) {
       k.p2k = (u32)floor_log2(q);
       k.p2shift = k.p2k - prm->log2_qout;

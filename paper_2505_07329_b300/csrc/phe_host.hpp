@@ -45,7 +45,11 @@ struct NttJob {             // forward transform of T*L input blocks
   const int32_t* digits = nullptr;  // [blocks][N] small signed integers instead of src (packing digits)
 };
 
-enum OutMode : int { kOutSwitched = 0, kOutRaw = 1, kOutRing = 2, kPow2 = 4 /* flag: q = 2^k via the RNS form */ };
+// kOutPackIn: masks switched to the gadget modulus B^ell (uint32, what
+// Decomp reads) and bodies raw mod q (uint64), the inputs of the packing.
+enum OutMode : int {
+  kOutSwitched = 0, kOutRaw = 1, kOutRing = 2, kOutPackIn = 3, kPow2 = 4 /* flag: q = 2^k via the RNS form */
+};
 
 // Kernel names for tracing; kKCall brackets a whole phe_matmul call.
 enum KernelId : int {
@@ -169,6 +173,9 @@ cudaError_t launch_weight_ntt(const phe_ctx* c, const int8_t* W, u32 rows, u32 c
                               u32 col_stride, u32 L, int rev, void* what, cudaStream_t s, bool force64 = false);
 cudaError_t launch_lwedot(const phe_ctx* c, const LweJobTable& jt, int mode, int grid_limit, cudaStream_t s,
                           bool force64 = false);
+// lwedot in kOutPackIn mode, with the switch constants rcK / rkK of 2^(base_log*ell).
+cudaError_t launch_lwedot_packin(const phe_ctx* c, const LweJobTable& jt, const RingConst& rcK, const RnsConst& rkK,
+                                 cudaStream_t s);
 cudaError_t launch_modswitch(const phe_ctx* c, const u64* in, u32* out, size_t n, cudaStream_t s);
 cudaError_t launch_expand_masks(const phe_ctx* c, const u64* seeds, u32 n, u64* masks, cudaStream_t s);
 int lwedot_threads(int logn);
@@ -177,6 +184,9 @@ int lwedot_threads(int logn);
 cudaError_t prepare_launches(const phe_ctx* c);
 // Sets the calling thread's phe_last_error() message (phe_capi.cu).
 void set_last_error(const char* msg);
+// Sets the constants of rns_modswitch in k (p1, p2 set) for the target
+// modulus 2^log2_target, 1 <= log2_target <= 32 (phe_capi.cu).
+void set_switch_target(RnsConst& k, u32 log2_target);
 size_t lwedot_smem(int logn);
 
 }  // namespace phe

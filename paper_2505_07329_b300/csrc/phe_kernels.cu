@@ -236,6 +236,7 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, PHE_LWEDOT_MIN_BLOCKS)
   constexpr bool P2 = (MODE & kPow2) != 0;      // power-of-two q through the RNS modulus
   static_assert(!(RNS && OUT == kOutRing), "client encryption runs in the 64-bit form");
   static_assert(RNS || !P2, "a power-of-two q runs in the RNS form");
+  static_assert(!(P2 && OUT == kOutPackIn), "no packing for a power-of-two q");
   using S = Shape<LOGN>;
   using R = RingOf<RNS>;
   using W = typename R::Word;
@@ -328,7 +329,8 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, PHE_LWEDOT_MIN_BLOCKS)
       }
       intt_regs<LOGN>(x, p, buf, tw0, twc, ring);  // barriers inside also order red[]
       if (active) {
-        if constexpr (OUT == kOutSwitched || OUT == kOutRaw) {
+        if constexpr (OUT == kOutSwitched || OUT == kOutRaw || OUT == kOutPackIn) {
+          constexpr bool SWM = OUT == kOutSwitched || OUT == kOutPackIn;  // masks switched
 #pragma unroll
           for (int e = 0; e < 16; ++e) {
             const int pos = pass_pos<LOGN, NP - 1>(p, e);
@@ -336,16 +338,16 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, PHE_LWEDOT_MIN_BLOCKS)
             if constexpr (P2) {
               const u32 c1 = sub_if32(x[e].x, rk.p1);
               const u64 v = pow2_from_crt(c1, crt_digit(c1, sub_if32(x[e].y, rk.p2), rk), rk);
-              if constexpr (OUT == kOutSwitched) reinterpret_cast<uint32_t*>(J.out)[o] = pow2_modswitch(v, rk);
+              if constexpr (SWM) reinterpret_cast<uint32_t*>(J.out)[o] = pow2_modswitch(v, rk);
               else reinterpret_cast<u64*>(J.out)[o] = v;
             } else if constexpr (RNS) {
               const u32 c1 = sub_if32(x[e].x, rk.p1);
               const u32 h = crt_digit(c1, sub_if32(x[e].y, rk.p2), rk);
-              if constexpr (OUT == kOutSwitched) reinterpret_cast<uint32_t*>(J.out)[o] = rns_modswitch(c1, h, rk);
+              if constexpr (SWM) reinterpret_cast<uint32_t*>(J.out)[o] = rns_modswitch(c1, h, rk);
               else reinterpret_cast<u64*>(J.out)[o] = (u64)c1 + (u64)rk.p1 * h;
             } else {
               const u64 c = reduce_4q(x[e], q, rc.q2);
-              if constexpr (OUT == kOutSwitched) reinterpret_cast<uint32_t*>(J.out)[o] = modswitch_word(c, rc);
+              if constexpr (SWM) reinterpret_cast<uint32_t*>(J.out)[o] = modswitch_word(c, rc);
               else reinterpret_cast<u64*>(J.out)[o] = c;
             }
           }
@@ -551,6 +553,29 @@ cudaError_t launch_lwedot(const phe_ctx* c, const LweJobTable& jt, int mode, int
     if (mode == kOutRaw) return lwedot_impl<LOGN, kOutRaw, false>(c, jt, grid_limit, s);
     if (mode == kOutRing) return lwedot_impl<LOGN, kOutRing, false>(c, jt, grid_limit, s);
     return cudaErrorInvalidValue;
+  });
+}
+
+cudaError_t launch_lwedot_packin(const phe_ctx* c, const LweJobTable& jt, const RingConst& rcK, const RnsConst& rkK,
+                                 cudaStream_t s) {
+  const u32 total = jt.prefix[jt.n];
+  if (total == 0) return cudaSuccess;
+  return by_logn(c->logn, [&](auto lg) -> cudaError_t {
+    constexpr int LOGN = decltype(lg)::value;
+    using S = Shape<LOGN>;
+    const size_t smem = (size_t)S::SLOTS * S::PADN * sizeof(u64);
+    if (c->rns) {
+      cudaError_t e = set_smem(lwedot_kernel<LOGN, kOutPackIn, true>, smem);
+      if (e != cudaSuccess) return e;
+      lwedot_kernel<LOGN, kOutPackIn, true><<<total, S::TPB, smem, s>>>(jt, rcK, rkK, tw0_of(c, true, true),
+                                                                       twc_of(c, true, true));
+    } else {
+      cudaError_t e = set_smem(lwedot_kernel<LOGN, kOutPackIn, false>, smem);
+      if (e != cudaSuccess) return e;
+      lwedot_kernel<LOGN, kOutPackIn, false><<<total, S::TPB, smem, s>>>(jt, rcK, rkK, tw0_of(c, false, true),
+                                                                        twc_of(c, false, true));
+    }
+    return cudaGetLastError();
   });
 }
 

@@ -29,6 +29,8 @@ using phe::u64;
 struct phe_ksk {
   phe_ctx* ctx = nullptr;
   uint32_t n = 0, base_log = 0, ell = 0;
+  phe::RingConst rcK{};  // the context's constants with the switch target 2^(base_log*ell)
+  phe::RnsConst rkK{};
   void* khat = nullptr;  // [n*ell][2][N] entries of 16 bytes (A then B), A_hat slot order
   uint64_t bytes = 0;
 };
@@ -40,9 +42,12 @@ namespace phe {
 // base-B digits d_0 (most significant) .. d_{ell-1} in [-B/2, B/2); a carry
 // out of d_0 is a multiple of B^ell and is dropped.  rcK is the context's
 // constants with log2_qout = base_log * ell (<= 32).
+// Signed gadget digits (Sec. 3.2 Decomp, read as the approximate signed
+// decomposition of TFHE) of a~ = ModulusSwitch of a from q to B^ell: base-B
+// digits d_0 (most significant) .. d_{ell-1} in [-B/2, B/2); a carry out of
+// d_0 is a multiple of B^ell and is dropped.
 template <int ELL>
-__device__ __forceinline__ void gadget_digits(u64 a, const RingConst& rcK, u32 base_log, int (&d)[ELL]) {
-  u32 v = modswitch_word(a, rcK);
+__device__ __forceinline__ void signed_digits(u32 v, u32 base_log, int (&d)[ELL]) {
   const u32 B = 1u << base_log, half = B >> 1, mask = B - 1;
 #pragma unroll
   for (int l = ELL - 1; l >= 0; --l) {
@@ -56,14 +61,16 @@ __device__ __forceinline__ void gadget_digits(u64 a, const RingConst& rcK, u32 b
   }
 }
 
-// Masks [T][rows][N] (words below q) -> digit rows D[u][i*ell + l][j] of
-// the units u_base + u, unit = t*G + g, holding the signed digit
-// d_l(a_{gN+j}[i]) for gN + j < rows and 0 past the last row.
+// Masks [T][rows][N] -> digit rows D[u][i*ell + l][j] of the units
+// u_base + u, unit = t*G + g, holding the signed digit d_l(a_{gN+j}[i]) for
+// gN + j < rows and 0 past the last row.  SWITCHED: the masks are already
+// a~ (uint32, switched to B^ell by the product kernel's epilogue); otherwise
+// they are words below q, switched here with rcK (log2_qout = base_log*ell).
 // A 32x32 tile of (j, i) goes through shared memory so that both the load
 // (along i) and the store (along j) are coalesced.
-template <int ELL>
+template <int ELL, bool SWITCHED>
 __global__ void __launch_bounds__(256)
-    pack_decompose_kernel(const u64* __restrict__ mask, u32 rows, u32 N, u32 G, u32 u_base, u32 base_log,
+    pack_decompose_kernel(const void* __restrict__ maskv, u32 rows, u32 N, u32 G, u32 u_base, u32 base_log,
                           RingConst rcK, int32_t* __restrict__ D) {
   __shared__ int tile[ELL][32][33];
   const u32 u = blockIdx.z;  // unit within the chunk; D holds the chunk's units
@@ -74,7 +81,10 @@ __global__ void __launch_bounds__(256)
     const u32 j = j0 + k, row = g * N + j;
     int d[ELL];
     if (row < rows) {
-      gadget_digits<ELL>(mask[((size_t)t * rows + row) * N + i0 + tx], rcK, base_log, d);
+      const size_t at = ((size_t)t * rows + row) * N + i0 + tx;
+      const u32 v = SWITCHED ? static_cast<const u32*>(maskv)[at]
+                             : modswitch_word(static_cast<const u64*>(maskv)[at], rcK);
+      signed_digits<ELL>(v, base_log, d);
     } else {
 #pragma unroll
       for (int l = 0; l < ELL; ++l) d[l] = 0;
@@ -371,18 +381,22 @@ constexpr int kMacStages = 4;                       // rows in flight per pack_m
 constexpr size_t kMacSmem = (size_t)kMacStages * 256 * (2 * 16 + kMacUnits * 8);
 constexpr uint64_t kPackScratchBytes = 2ull << 30;  // digit rows in flight per phe_pack chunk
 
-cudaError_t launch_decompose(const phe_ctx* c, const phe_ksk* k, const u64* mask, u32 rows, u32 G, u32 u_base,
-                             u32 cu, int32_t* D, cudaStream_t s) {
+cudaError_t launch_decompose(const phe_ctx* c, const phe_ksk* k, const void* mask, bool switched, u32 rows, u32 G,
+                             u32 u_base, u32 cu, int32_t* D, cudaStream_t s) {
   const u32 N = c->prm.N;
-  phe::RingConst rcK = c->rc;
-  rcK.log2_qout = k->base_log * k->ell;
   const dim3 grid(N / 32, N / 32, cu), block(32, 8);
+#define PHE_DECOMP(E)                                                                                       \
+  (switched ? phe::pack_decompose_kernel<E, true><<<grid, block, 0, s>>>(mask, rows, N, G, u_base, k->base_log, \
+                                                                          k->rcK, D)                        \
+            : phe::pack_decompose_kernel<E, false><<<grid, block, 0, s>>>(mask, rows, N, G, u_base, k->base_log, \
+                                                                           k->rcK, D))
   switch (k->ell) {
-    case 1: phe::pack_decompose_kernel<1><<<grid, block, 0, s>>>(mask, rows, N, G, u_base, k->base_log, rcK, D); break;
-    case 2: phe::pack_decompose_kernel<2><<<grid, block, 0, s>>>(mask, rows, N, G, u_base, k->base_log, rcK, D); break;
-    case 3: phe::pack_decompose_kernel<3><<<grid, block, 0, s>>>(mask, rows, N, G, u_base, k->base_log, rcK, D); break;
-    default: phe::pack_decompose_kernel<4><<<grid, block, 0, s>>>(mask, rows, N, G, u_base, k->base_log, rcK, D); break;
+    case 1: PHE_DECOMP(1); break;
+    case 2: PHE_DECOMP(2); break;
+    case 3: PHE_DECOMP(3); break;
+    default: PHE_DECOMP(4); break;
   }
+#undef PHE_DECOMP
   return cudaGetLastError();
 }
 
@@ -450,8 +464,8 @@ cudaError_t launch_finish(const phe_ctx* c, int mode, const u64* Phat, u32 nseg,
 }
 
 // The packing of T x rows LWE ciphertexts on `s`, in chunks of units.
-cudaError_t pack_device(phe_ctx* c, const phe_ksk* k, u32 T, u32 rows, const u64* mask, const u64* body, void* oa,
-                        void* ob, int mode, cudaStream_t s) {
+cudaError_t pack_device(phe_ctx* c, const phe_ksk* k, u32 T, u32 rows, const void* mask, bool switched,
+                        const u64* body, void* oa, void* ob, int mode, cudaStream_t s) {
   const u32 N = c->prm.N, nr = k->n * k->ell;
   const u32 G = (rows + N - 1) / N;
   const u64 units = (u64)T * G;
@@ -470,7 +484,7 @@ cudaError_t pack_device(phe_ctx* c, const phe_ksk* k, u32 T, u32 rows, const u64
     const u32 cu = (u32)std::min<u64>(per, units - u0);
     {
       Span sp(c, phe::kKPackDecompose, s);
-      e = launch_decompose(c, k, mask, rows, G, (u32)u0, cu, D, s);
+      e = launch_decompose(c, k, mask, switched, rows, G, (u32)u0, cu, D, s);
     }
     if (e == cudaSuccess) {
       Span sp(c, phe::kKInputNtt, s);
@@ -491,6 +505,60 @@ cudaError_t pack_device(phe_ctx* c, const phe_ksk* k, u32 T, u32 rows, const u64
   cudaError_t f2 = cudaFreeAsync(Dhat, s);
   if (e != cudaSuccess) return e;
   return f1 != cudaSuccess ? f1 : f2;
+}
+
+// Eq. (LWEdot) with the masks switched straight to B^ell (what Decomp
+// reads) and raw bodies, then the packing, token chunk by token chunk.
+cudaError_t matmul_packed_device(phe_ctx* c, const phe_weights::Dir& D, const phe_ksk* k, u32 T, const u64* in_mask,
+                                 const u64* in_seeds, const u64* in_body, void* oa, void* ob, int mode,
+                                 cudaStream_t s) {
+  const u32 N = c->prm.N, G = (D.rows + N - 1) / N;
+  const size_t osz = mode == phe::kOutRaw ? sizeof(u64) : sizeof(u32);
+  const u64 ahat_tok = (u64)D.L * N * sizeof(u64), atil_tok = (u64)D.rows * N * sizeof(u32);
+  const u64 tok_bytes = ahat_tok + atil_tok + (u64)D.rows * sizeof(u64);
+  const u32 per = (u32)std::max<u64>(1, std::min<u64>(T, kPackScratchBytes / tok_bytes));
+  Span call(c, phe::kKCall, s);
+  char* scratch = nullptr;
+  cudaError_t e = phe::ctx_malloc_async(c, &scratch, (size_t)per * tok_bytes, s);
+  if (e != cudaSuccess) return e;
+  u64* ahat = reinterpret_cast<u64*>(scratch);
+  u32* atil = reinterpret_cast<u32*>(scratch + (size_t)per * ahat_tok);
+  u64* rawb = reinterpret_cast<u64*>(scratch + (size_t)per * (ahat_tok + atil_tok));
+  for (u32 t0 = 0; t0 < T && e == cudaSuccess; t0 += per) {
+    const u32 tn = std::min(per, T - t0);
+    {
+      Span sp(c, phe::kKInputNtt, s);
+      phe::NttJob nj{in_mask ? in_mask + (size_t)t0 * D.L * N : nullptr, ahat, tn * D.L,
+                     in_seeds ? in_seeds + (size_t)t0 * D.L : nullptr};
+      e = phe::launch_input_ntt(c, &nj, 1, s);
+    }
+    if (e == cudaSuccess) {
+      phe::LweJobTable jt{};
+      jt.n = 1;
+      phe::LweJob& J = jt.j[0];
+      J.what = D.what;
+      J.ahat = ahat;
+      J.out = atil;
+      J.wrow = D.wrow;
+      J.bin = in_body + (size_t)t0 * D.L * N;
+      J.out_body = rawb;
+      J.rows = D.rows;
+      J.cols = D.cols;
+      J.T = tn;
+      J.L = D.L;
+      J.tok_chunk = 16;
+      J.tiles = D.rows * ((tn + J.tok_chunk - 1) / J.tok_chunk);
+      jt.prefix[0] = 0;
+      jt.prefix[1] = J.tiles;
+      Span sp(c, phe::kKLwedot, s);
+      e = phe::launch_lwedot_packin(c, jt, k->rcK, k->rkK, s);
+    }
+    if (e == cudaSuccess)
+      e = pack_device(c, k, tn, D.rows, atil, true, rawb, static_cast<char*>(oa) + (size_t)t0 * G * N * osz,
+                      static_cast<char*>(ob) + (size_t)t0 * G * N * osz, mode, s);
+  }
+  cudaError_t f = cudaFreeAsync(scratch, s);
+  return e != cudaSuccess ? e : f;
 }
 
 phe_status check_ksk(const phe_ctx* c, const phe_ksk* k, const char* who) {
@@ -521,6 +589,10 @@ phe_status phe_ksk_upload(phe_ctx* c, const uint64_t* h_ka, const uint64_t* h_kb
   k->n = n;
   k->base_log = base_log;
   k->ell = ell;
+  k->rcK = c->rc;
+  k->rcK.log2_qout = base_log * ell;
+  k->rkK = c->rk;
+  if (c->rns) phe::set_switch_target(k->rkK, base_log * ell);
   const size_t nr = (size_t)n * ell, words = nr * 2 * N;
   k->bytes = words * 16;
   u64* tmp = nullptr;
@@ -574,8 +646,8 @@ phe_status phe_pack(phe_ctx* c, const phe_ksk* k, uint32_t T, uint32_t rows, con
                                            (unsigned long long)((u64)T * G));
   DeviceGuard g(c->device);
   if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
-  cudaError_t e = pack_device(c, k, T, rows, reinterpret_cast<const u64*>(d_lwe_mask),
-                              reinterpret_cast<const u64*>(d_lwe_body), d_out_a, d_out_b,
+  cudaError_t e = pack_device(c, k, T, rows, d_lwe_mask, false, reinterpret_cast<const u64*>(d_lwe_body), d_out_a,
+                              d_out_b,
                               flags == PHE_OUT_RAW ? phe::kOutRaw : phe::kOutSwitched, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "phe_pack");
   return PHE_OK;
@@ -593,30 +665,34 @@ phe_status phe_matmul_packed(phe_ctx* c, const phe_weights* w, const phe_ksk* k,
     return fail(PHE_EINVAL, "phe_matmul_packed: flags=%u", flags);
   if (T == 0) return PHE_OK;
   if (!d_in_mask || !d_in_body || !d_out_a || !d_out_b) return fail(PHE_EINVAL, "phe_matmul_packed: null buffer");
-  const u32 N = c->prm.N, G = (rows + N - 1) / N;
   DeviceGuard g(c->device);
   if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
-  cudaStream_t s = (cudaStream_t)stream;
-  // raw LWE outputs of a chunk of tokens, then their packing
-  const u64 tok_bytes = (u64)rows * (N + 1) * sizeof(u64);
-  const u32 per = (u32)std::max<u64>(1, std::min<u64>(T, kPackScratchBytes / tok_bytes));
-  const size_t osz = flags == PHE_OUT_RAW ? sizeof(u64) : sizeof(u32);
-  u64* raw = nullptr;
-  cudaError_t e = phe::ctx_malloc_async(c, &raw, (size_t)per * tok_bytes, s);
-  if (e != cudaSuccess) return cuda_fail(e, "phe_matmul_packed: scratch");
-  u64* raw_body = raw + (size_t)per * rows * N;
-  for (u32 t0 = 0; t0 < T && st == PHE_OK; t0 += per) {
-    const u32 tn = std::min(per, T - t0);
-    const size_t in_off = (size_t)t0 * L * N, out_off = (size_t)t0 * G * N * osz;
-    st = phe_matmul(c, w, dir, tn, d_in_mask + in_off, d_in_body + in_off, raw, raw_body, PHE_OUT_RAW, stream);
-    if (st == PHE_OK)
-      st = phe_pack(c, k, tn, rows, reinterpret_cast<const uint64_t*>(raw),
-                    reinterpret_cast<const uint64_t*>(raw_body), static_cast<char*>(d_out_a) + out_off,
-                    static_cast<char*>(d_out_b) + out_off, flags, stream);
-  }
-  e = cudaFreeAsync(raw, s);
+  cudaError_t e = matmul_packed_device(c, w->dir[dir], k, T, reinterpret_cast<const u64*>(d_in_mask), nullptr,
+                                       reinterpret_cast<const u64*>(d_in_body), d_out_a, d_out_b,
+                                       flags == PHE_OUT_RAW ? phe::kOutRaw : phe::kOutSwitched, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "phe_matmul_packed");
+  return PHE_OK;
+}
+
+phe_status phe_matmul_packed_seeded(phe_ctx* c, const phe_weights* w, const phe_ksk* k, int dir, uint32_t T,
+                                    const uint64_t* d_in_seeds, const uint64_t* d_in_body, void* d_out_a,
+                                    void* d_out_b, uint32_t flags, void* stream) {
+  phe_status st = check_ksk(c, k, "phe_matmul_packed_seeded");
   if (st != PHE_OK) return st;
-  if (e != cudaSuccess) return cuda_fail(e, "phe_matmul_packed: free");
+  uint32_t rows = 0, cols = 0, L = 0;
+  if (!w || w->ctx != c) return fail(PHE_EINVAL, "phe_matmul_packed_seeded: weights missing or of another context");
+  if ((st = phe_weights_shape(w, dir, &rows, &cols, &L)) != PHE_OK) return st;
+  if (flags != PHE_OUT_SWITCHED && flags != PHE_OUT_RAW)
+    return fail(PHE_EINVAL, "phe_matmul_packed_seeded: flags=%u", flags);
+  if (T == 0) return PHE_OK;
+  if (!d_in_seeds || !d_in_body || !d_out_a || !d_out_b)
+    return fail(PHE_EINVAL, "phe_matmul_packed_seeded: null buffer");
+  DeviceGuard g(c->device);
+  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
+  cudaError_t e = matmul_packed_device(c, w->dir[dir], k, T, nullptr, reinterpret_cast<const u64*>(d_in_seeds),
+                                       reinterpret_cast<const u64*>(d_in_body), d_out_a, d_out_b,
+                                       flags == PHE_OUT_RAW ? phe::kOutRaw : phe::kOutSwitched, (cudaStream_t)stream);
+  if (e != cudaSuccess) return cuda_fail(e, "phe_matmul_packed_seeded");
   return PHE_OK;
 }
 

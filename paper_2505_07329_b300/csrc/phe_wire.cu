@@ -183,7 +183,7 @@ phe_status phe_matmul_wire(phe_ctx* c, const phe_weights* w, const phe_ksk* k, i
   // per-token scratch: seeds and bodies, then the switched outputs (and, when
   // packing, the raw LWE outputs inside phe_pack's own scratch)
   const u64 in_tok = (u64)L * (N + 1) * 8;
-  const u64 out_tok = k ? (u64)G * 2 * N * 4 + (u64)rows * (N + 1) * 8 : (u64)rows * (N + 1) * 4;
+  const u64 out_tok = k ? (u64)G * 2 * N * 4 : (u64)rows * (N + 1) * 4;
   const u32 per = (u32)std::max<u64>(1, std::min<u64>(T, kWireScratchBytes / (in_tok + out_tok)));
   char* scratch = nullptr;
   cudaError_t e = phe::ctx_malloc_async(c, &scratch, (size_t)per * (in_tok + out_tok), s);
@@ -198,15 +198,10 @@ phe_status phe_matmul_wire(phe_ctx* c, const phe_weights* w, const phe_ksk* k, i
                                 reinterpret_cast<uint64_t*>(bodies), stream);
     if (st != PHE_OK) break;
     if (k) {
-      u64* raw = reinterpret_cast<u64*>(outs + (size_t)tn * G * 2 * N * 4);
-      u64* raw_body = raw + (size_t)tn * rows * N;
       u32* oa = reinterpret_cast<u32*>(outs);
       u32* ob = oa + (size_t)tn * G * N;
-      st = phe_matmul_seeded(c, w, dir, tn, reinterpret_cast<uint64_t*>(seeds), reinterpret_cast<uint64_t*>(bodies),
-                             raw, raw_body, PHE_OUT_RAW, stream);
-      if (st == PHE_OK)
-        st = phe_pack(c, k, tn, rows, reinterpret_cast<uint64_t*>(raw), reinterpret_cast<uint64_t*>(raw_body), oa,
-                      ob, PHE_OUT_SWITCHED, stream);
+      st = phe_matmul_packed_seeded(c, w, k, dir, tn, reinterpret_cast<uint64_t*>(seeds),
+                                    reinterpret_cast<uint64_t*>(bodies), oa, ob, PHE_OUT_SWITCHED, stream);
       if (st == PHE_OK) {
         // RLWE record g of token t: A then B of unit t*G + g
         e = pack_records(c, oa, N, ob, N, (u64)tn * G, static_cast<char*>(d_out_records) + (size_t)t0 * G * rlwe_rec,

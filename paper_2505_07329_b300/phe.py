@@ -120,6 +120,7 @@ SIGNATURES = {
     "phe_ksk_device_bytes": (_u64, [_vp]),
     "phe_pack": (_i32, [_vp, _vp, _u32, _u32, _vp, _vp, _vp, _vp, _u32, _vp]),
     "phe_matmul_packed": (_i32, [_vp, _vp, _vp, _i32, _u32, _vp, _vp, _vp, _vp, _u32, _vp]),
+    "phe_matmul_packed_seeded": (_i32, [_vp, _vp, _vp, _i32, _u32, _vp, _vp, _vp, _vp, _u32, _vp]),
     "phe_matmul_packed_host": (_i32, [_vp, _vp, _vp, _i32, _u32, _vp, _vp, _vp, _vp, _u32, _u32, _vp]),
     "phe_wire_sizes": (_i32, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
     "phe_wire_pack": (_i32, [_vp, _vp, _u32, _vp, _u32, _u64, _vp, _vp]),
@@ -441,3 +442,9 @@ def phe_wire_unpack_inputs(ctx, records, n_records: int, seeds, bodies, stream=N
 
 def phe_matmul_wire(ctx, w, k, direction: int, T: int, in_records, out_records, stream=None) -> None:
     _check(lib().phe_matmul_wire(ctx, w, k, direction, T, _dptr(in_records), _dptr(out_records), _stream(stream)))
+
+
+def phe_matmul_packed_seeded(ctx, w, k, direction: int, T: int, in_seeds, in_body, out_a, out_b,
+                             flags: int = PHE_OUT_SWITCHED, stream=None) -> None:
+    _check(lib().phe_matmul_packed_seeded(ctx, w, k, direction, T, _dptr(in_seeds), _dptr(in_body), _dptr(out_a),
+                                          _dptr(out_b), flags, _stream(stream)))

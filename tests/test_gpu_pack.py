@@ -261,3 +261,37 @@ def test_pack_largest_ring_and_empty_calls(orc, ctxs):
     rs = np.array([0, 1, 99, 100, 4096, 8191])
     ea, eb = orc.pack_coeffs(masks[0], bodies[0], KA, KB, q, 26, 1, rs)
     assert np.array_equal(ga[0, 0, rs], ea) and np.array_equal(gb[0, 0, rs], eb)
+
+
+@pytest.mark.parametrize("modulus", ["rns", "prime"])
+def test_matmul_packed_seeded_matches_mask_form(orc, ctxs, modulus):
+    import torch
+    N, T = 256, 3
+    q = MODULI[modulus][0]
+    ctx = ctxs(N, modulus)
+    g = _rng(91)
+    W = synth.weights(290, 300, seed=92)
+    KA = g.integers(0, q, (N, 2, N), dtype=np.uint64)
+    KB = g.integers(0, q, (N, 2, N), dtype=np.uint64)
+    seeds = g.integers(0, 2 ** 64, (T, 2), dtype=np.uint64)
+    A = orc.expand_masks(seeds, N, q)
+    B = g.integers(0, q, (T, 2, N), dtype=np.uint64)
+    w = phe.phe_weights_upload(ctx, W)
+    k = phe.phe_ksk_upload(ctx, KA, KB, 13, 2)
+    try:
+        oa = torch.empty((T, 2, N), dtype=torch.int64, device="cuda")
+        ob = torch.empty_like(oa)
+        phe.phe_matmul_packed_seeded(ctx, w, k, phe.PHE_FWD, T, to_dev_u64(seeds), to_dev_u64(B), oa, ob,
+                                     phe.PHE_OUT_RAW)
+        torch.cuda.synchronize()
+    finally:
+        phe.phe_ksk_free(k)
+        phe.phe_weights_free(w)
+    la, lb = orc.lwedot_all(W, A, B, q)
+    for t in range(T):
+        for grp in range(2):
+            m = min(N, 290 - grp * N)
+            ea, eb = orc.pack_coeffs(la[t, grp * N:grp * N + m], lb[t, grp * N:grp * N + m], KA, KB, q, 13, 2,
+                                     np.arange(N))
+            assert np.array_equal(oa[t, grp].cpu().numpy().view(np.uint64), ea), (t, grp)
+            assert np.array_equal(ob[t, grp].cpu().numpy().view(np.uint64), eb), (t, grp)
