@@ -42,8 +42,8 @@ METRIC = "encrypted W·[x] tokens/s per Llama-1B layer; p50/p99 latency; % of ro
 # with ncu, and the algorithmic bytes of that launch.  Valid only for the
 # kernel sources the counters were taken on (hash of phe_kernels.cu +
 # phe_device.cuh).
-TRAFFIC_KERNEL_HASH = "d882f277542bdd90"
-TRAFFIC_BYTES_PER_LAUNCH = 96353.6e6
+TRAFFIC_KERNEL_HASH = "130ee03dbc893ae3"
+TRAFFIC_BYTES_PER_LAUNCH = 95933.0e6
 TRAFFIC_ALG_BYTES_PER_LAUNCH = 95891.8e6
 
 
@@ -71,6 +71,8 @@ def parse():
     ap.add_argument("--tokens", type=int, default=0, help="override tokens per GPU (0 = the workload's)")
     ap.add_argument("--e2e-tokens", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--paper-table", type=int, default=1,
+                    help="1: also time the shapes of the paper's timing table at its parameter set (N=2048, q=2^39)")
     ap.add_argument("--packed-tokens", type=int, default=16,
                     help="tokens of the packed-output measurement (Eq. (pack_rotate) after each product; 0 = skip)")
     ap.add_argument("--no-cpu", action="store_true")
@@ -477,6 +479,10 @@ def main():
     if not args.no_e2e:
         e2e = measure_e2e(phe, ctx, weights, wl, mm, keys, inputs, args.e2e_tokens, stream)
 
+    paper_table = None
+    if args.paper_table and rank == 0:
+        paper_table = measure_paper_table(phe, dev)
+
     packed = None
     if args.packed_tokens > 0:
         packed = measure_packed(phe, ctx, weights, wl, mm, keys, inputs, S, q, min(args.packed_tokens, T), stream,
@@ -488,7 +494,8 @@ def main():
         for pl in plans:
             phe.phe_plan_destroy(pl)
         plans = []
-        serving = measure_serving(phe, ctx, weights, wl, inputs, keys, args.serve_requests, args.serve_rate, T)
+        serving = measure_serving(phe, ctx, weights, wl, inputs, keys, args.serve_requests, args.serve_rate, T,
+                                  tuning[0] if tuning else 2)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -516,6 +523,7 @@ def main():
                 "other_form": other,
                 "serving": serving,
                 "packed": packed,
+                "paper_table": paper_table,
                 "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
                 "kernels": {k: {"launches": v["launches"], "total_ms": v["total_ms"]} for k, v in trace.items()},
                 "clocks": clk, "sanity_decrypt": check}
@@ -573,7 +581,7 @@ def sanity_decrypt(wl, mm, inputs, keys, outs, S, T, chunk):
     return f"{ok}/{tot}"
 
 
-def measure_serving(phe, ctx, weights, wl, inputs, keys, n_requests, rate, T_avail):
+def measure_serving(phe, ctx, weights, wl, inputs, keys, n_requests, rate, T_avail, tok_chunk=2):
     """The served form: requests from 64 clients arrive as a Poisson process
     (mean `rate` per second); each is one projection of the layer in one
     direction with U{64..2048} tokens (its inputs are slices of the resident
@@ -586,7 +594,7 @@ def measure_serving(phe, ctx, weights, wl, inputs, keys, n_requests, rate, T_ava
     dirs = r.integers(0, 2, size=n_requests)
     toks = r.integers(64, 2049, size=n_requests)
     N = wl.ring.N
-    srv = phe.phe_server_create(ctx, 24 << 30, chunk_tokens=32, tok_chunk=8, blocks_per_sm=0, max_active=64,
+    srv = phe.phe_server_create(ctx, 24 << 30, chunk_tokens=32, tok_chunk=tok_chunk, blocks_per_sm=0, max_active=64,
                                 max_jobs_per_iteration=64, max_queue=4096, wait_timeout_ms=600000)
     ids = []
     items = 0
@@ -780,6 +788,55 @@ def measure_packed(phe, ctx, weights, wl, mm, keys, inputs, S, q, tokens, stream
             "sanity_decrypt": f"{ok}/{y.shape[0]} coefficients, {zero}/{N - y.shape[0]} unused zero",
             "e2e": {"value": tokens * steps / dt, "unit": "tokens/s", "h2d_bytes_per_step": h2d,
                     "d2h_bytes_per_step": out_bytes * tokens, "tokens_per_step": tokens}}
+
+
+# Per-token latencies of W.[x] printed in Table fhe_matmul_timing (Sec. 6.3)
+# for the paper's parameter set on its laptop GPU, including its output packing.
+PAPER_TABLE = (((768, 768), 0.0809), ((3072, 768), 0.1528), ((2048, 2048), 0.2402), ((768, 3072), 0.3389),
+               ((8192, 2048), 0.6368), ((2048, 8192), 1.0539))
+
+
+def measure_paper_table(phe, dev, tokens=64):
+    """The shapes of Table fhe_matmul_timing at the paper's parameter set
+    (N = 2048, q = 2^39 computed through p1 p2, q_out = 2^26): one-token
+    latency of phe_matmul and throughput on `tokens` tokens (device-resident,
+    CUDA events).  The paper's times include its output packing, which this
+    parameter set does not run here, so they are context only."""
+    import torch
+    ctx = phe.phe_ctx_create(2048, 1 << 39, 26, dev.index or 0, rns=(synth.RNS_P1, synth.RNS_P2))
+    rows_out = []
+    try:
+        stream = torch.cuda.current_stream(dev)
+        for (d_in, d_out), paper_s in PAPER_TABLE:
+            W = synth.weights(d_out, d_in, seed=synth.SEED_W + d_in + d_out)
+            w = phe.phe_weights_upload(ctx, W, phe.PHE_DIR_FWD_BIT)
+            L = synth.blocks(d_in, 2048)
+            g = torch.Generator(device=dev)
+            g.manual_seed(d_in * 7 + d_out)
+            A = torch.randint(0, 1 << 39, (tokens, L, 2048), device=dev, generator=g, dtype=torch.int64)
+            B = torch.randint(0, 1 << 39, (tokens, L, 2048), device=dev, generator=g, dtype=torch.int64)
+            om = torch.empty((tokens, d_out, 2048), dtype=torch.int32, device=dev)
+            ob = torch.empty((tokens, d_out), dtype=torch.int32, device=dev)
+            res = {}
+            for T in (1, tokens):
+                for _ in range(2):
+                    phe.phe_matmul(ctx, w, phe.PHE_FWD, T, A, B, om, ob, phe.PHE_OUT_SWITCHED, stream)
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                reps = 5
+                a.record(stream)
+                for _ in range(reps):
+                    phe.phe_matmul(ctx, w, phe.PHE_FWD, T, A, B, om, ob, phe.PHE_OUT_SWITCHED, stream)
+                b.record(stream)
+                torch.cuda.synchronize()
+                res[T] = a.elapsed_time(b) / reps
+            phe.phe_weights_free(w)
+            rows_out.append({"shape": f"{d_in}->{d_out}", "paper_s_per_token": paper_s,
+                             "latency_ms_1_token": res[1], "tokens_per_s": tokens / (res[tokens] / 1e3)})
+    finally:
+        phe.phe_ctx_destroy(ctx)
+    return {"params": "N=2048, q=2^39 (exact through p1 p2), q_out=2^26", "tokens": tokens, "rows": rows_out,
+            "note": "paper times: laptop GPU, one token, with output packing; ours: one B300, no packing at q=2^39"}
 
 
 if __name__ == "__main__":

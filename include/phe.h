@@ -260,7 +260,7 @@ phe_status phe_plan_info(const phe_plan* plan, phe_plan_stats* out);
 void phe_plan_destroy(phe_plan* plan);
 
 /* Autotuner: times candidate tile shapes (tokens per tile in
- * {4, 8, 16, 32, 64} x persistent or one-block-per-tile grids) on the first
+ * {2, 4, 8, 16, 32, 64} x persistent or one-block-per-tile grids) on the first
  * `sample_tokens` tokens (0 = 64) of every job, with CUDA events on
  * `stream` (non-default), and returns the fastest.  Writes the jobs' output
  * buffers.  Results are cached per ring and job shapes; a cached answer is

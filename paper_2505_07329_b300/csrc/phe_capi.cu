@@ -212,7 +212,7 @@ cudaError_t matmul_device(phe_ctx* c, const phe_weights::Dir& D, u32 T, const u6
     J.cols = D.cols;
     J.T = T;
     J.L = D.L;
-    J.tok_chunk = 16;
+    J.tok_chunk = phe::kDefaultTokChunk;
     J.tiles = D.rows * ((T + J.tok_chunk - 1) / J.tok_chunk);
     jt.prefix[0] = 0;
     jt.prefix[1] = J.tiles;
@@ -357,6 +357,8 @@ phe_status phe_ctx_create(const phe_params* prm, int device, phe_ctx** out) {
   rc.c60p = shoup(rc.c60, q);
   rc.c64 = (u64)(((u128)1 << 64) % q);
   rc.c64p = shoup(rc.c64, q);
+  rc.c32 = (1ull << 32) % q;
+  rc.c32p = shoup(rc.c32, q);
   rc.log2_qout = prm->log2_qout;
   c->pow2 = pow2;
   if (!pow2) {

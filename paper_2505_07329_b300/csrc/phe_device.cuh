@@ -38,6 +38,8 @@ struct RingConst {
   u64 c60p;       // Shoup quotient of c60
   u64 c64;        // 2^64 mod q (reduces 128-bit keystream words of seeded masks)
   u64 c64p;       // Shoup quotient of c64
+  u64 c32;        // 2^32 mod q (recombines the byte-plane body parts)
+  u64 c32p;       // Shoup quotient of c32
   u32 ms_s;       // s = floor(log2 q)
   u32 log2_qout;  // k: output modulus 2^k, 1 <= k <= 32
 };

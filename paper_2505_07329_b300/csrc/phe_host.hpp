@@ -15,6 +15,9 @@
 namespace phe {
 
 constexpr int kMaxJobs = 32;      // jobs in one batched launch (passed by value)
+// Tokens per lwedot tile for the calls that do not autotune (measured best on
+// the layer workload: 2-token tiles, all tiles of one row adjacent).
+constexpr unsigned kDefaultTokChunk = 2;
 constexpr int kMinLogN = 8;
 constexpr int kMaxLogN = 13;
 

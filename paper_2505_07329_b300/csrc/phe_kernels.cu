@@ -217,6 +217,59 @@ __device__ __forceinline__ void body_partial(const LweJob& J, u32 row, u32 t, in
   }
 }
 
+// Byte-plane form of the same dot product, for rows whose length is a
+// multiple of 4 and 16-byte aligned bodies: four consecutive words B[k..k+3]
+// are cut into their 8 byte planes (byte l of each word, one plane per 32-bit
+// register, by byte permutes), and each plane meets the four int8 weights in
+// one dp4a (signed x unsigned bytes, int32 accumulate).  The thread's sum
+// sum_l acc_l 2^(8l) leaves as two int64 parts, lo (planes 0-3) + hi 2^32
+// (planes 4-7); |acc_l| <= 2^21 for rows up to 16384.
+__device__ __forceinline__ int dp4a_su(int a, u32 b, int c) {
+  int d;
+  asm("dp4a.s32.u32 %0, %1, %2, %3;" : "=r"(d) : "r"(a), "r"(b), "r"(c));
+  return d;
+}
+__device__ __forceinline__ void planes4(u32 x0, u32 x1, u32 x2, u32 x3, u32 (&pl)[4]) {
+  const u32 t01 = __byte_perm(x0, x1, 0x5140), t23 = __byte_perm(x2, x3, 0x5140);
+  const u32 u01 = __byte_perm(x0, x1, 0x7362), u23 = __byte_perm(x2, x3, 0x7362);
+  pl[0] = __byte_perm(t01, t23, 0x5410);
+  pl[1] = __byte_perm(t01, t23, 0x7632);
+  pl[2] = __byte_perm(u01, u23, 0x5410);
+  pl[3] = __byte_perm(u01, u23, 0x7632);
+}
+__device__ __forceinline__ void body_partial_planes(const LweJob& J, u32 row, u32 t, int p, int P, int N,
+                                                    long long (&acc)[3]) {
+  const int8_t* wr = J.wrow + (size_t)row * J.cols;
+  const u64* bt = J.bin + (size_t)t * J.L * (size_t)N;
+  int a[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+  for (u32 k4 = 4 * (u32)p; k4 < J.cols; k4 += 4 * (u32)P) {
+    const int w4 = __ldg(reinterpret_cast<const int*>(wr + k4));
+    const ulonglong2 b01 = __ldg(reinterpret_cast<const ulonglong2*>(bt + k4));
+    const ulonglong2 b23 = __ldg(reinterpret_cast<const ulonglong2*>(bt + k4 + 2));
+    u32 lo[4], hi[4];
+    planes4((u32)b01.x, (u32)b01.y, (u32)b23.x, (u32)b23.y, lo);
+    planes4((u32)(b01.x >> 32), (u32)(b01.y >> 32), (u32)(b23.x >> 32), (u32)(b23.y >> 32), hi);
+#pragma unroll
+    for (int l = 0; l < 4; ++l) {
+      a[l] = dp4a_su(w4, lo[l], a[l]);
+      a[4 + l] = dp4a_su(w4, hi[l], a[4 + l]);
+    }
+  }
+  acc[0] = (long long)a[0] + ((long long)a[1] << 8) + ((long long)a[2] << 16) + ((long long)a[3] << 24);
+  acc[1] = (long long)a[4] + ((long long)a[5] << 8) + ((long long)a[6] << 16) + ((long long)a[7] << 24);
+  acc[2] = 0;
+}
+
+// The body mod q from block-reduced parts: S0 + S1 2^30 + S2 2^60 (word
+// split), or S0 + S1 2^32 (byte planes).
+__device__ __forceinline__ u64 body_combine_planes(const long long (&S)[3], const RingConst& rc) {
+  const u64 q = rc.q;
+  const u64 v0 = (S[0] < 0) ? q - (u64)(-S[0]) % q : (u64)S[0] % q;
+  const u64 v1 = (S[1] < 0) ? q - (u64)(-S[1]) % q : (u64)S[1] % q;
+  const u64 h = reduce_2q(mul_shoup(v1, rc.c32, rc.c32p, q), q);
+  return reduce_2q(reduce_2q(v0, q) + h, q);
+}
+
 // The body mod q from the block-reduced partial sums S0 + S1 2^30 + S2 2^60.
 __device__ __forceinline__ u64 body_combine(const long long (&S)[3], const RingConst& rc) {
   const u64 q = rc.q;
@@ -271,12 +324,30 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, PHE_LWEDOT_MIN_BLOCKS)
     const u32 t0 = (local % nch) * J.tok_chunk;
     const u32 t1 = min(J.T, t0 + J.tok_chunk);
     const Tw* wrow = reinterpret_cast<const Tw*>(J.what) + (size_t)row * J.L * N;
+    const bool planes = (J.cols % 4 == 0) && ((reinterpret_cast<uintptr_t>(J.bin) & 15) == 0);
     const u32 iters = (t1 - t0 + S::SLOTS - 1) / S::SLOTS;
 
     for (u32 it = 0; it < iters; ++it, ++seq) {
       const u32 t = t0 + it * S::SLOTS + slot;
       const bool active = t < t1;
       const int par = seq & 1;
+      // the body first, while no transform words are live
+      if constexpr (BODY) {
+        long long acc[3] = {0, 0, 0};
+        if (active) {
+          if (planes) body_partial_planes(J, row, t, p, P, N, acc);
+          else body_partial(J, row, t, p, P, N, acc);
+        }
+#pragma unroll
+        for (int off = GW / 2; off > 0; off >>= 1) {
+#pragma unroll
+          for (int i = 0; i < 3; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off, GW);
+        }
+        if (p % GW == 0) {
+#pragma unroll
+          for (int i = 0; i < 3; ++i) red[par][slot][p / GW][i] = acc[i];
+        }
+      }
       W x[16];
 #pragma unroll
       for (int r = 0; r < 16; ++r) {
@@ -312,19 +383,6 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, PHE_LWEDOT_MIN_BLOCKS)
               x[r + 1] = (s1 >= q4) ? s1 - q4 : s1;
             }
           }
-        }
-      }
-      if constexpr (BODY) {
-        long long acc[3] = {0, 0, 0};
-        if (active) body_partial(J, row, t, p, P, N, acc);
-#pragma unroll
-        for (int off = GW / 2; off > 0; off >>= 1) {
-#pragma unroll
-          for (int i = 0; i < 3; ++i) acc[i] += __shfl_xor_sync(0xffffffffu, acc[i], off, GW);
-        }
-        if (p % GW == 0) {
-#pragma unroll
-          for (int i = 0; i < 3; ++i) red[par][slot][p / GW][i] = acc[i];
         }
       }
       intt_regs<LOGN>(x, p, buf, tw0, twc, ring);  // barriers inside also order red[]
@@ -380,14 +438,15 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, PHE_LWEDOT_MIN_BLOCKS)
               for (int i = 0; i < 3; ++i) S3[i] += red[par][slot][g][i];
             }
             if constexpr (P2) {
-              // S0 + S1 2^30 + S2 2^60 mod 2^64 is exact mod q = 2^p2k
-              const u64 v = ((u64)S3[0] + ((u64)S3[1] << 30) + ((u64)S3[2] << 60)) & (rc.q - 1);
+              // the parts' sum mod 2^64 is exact mod q = 2^p2k
+              const u64 v = (planes ? ((u64)S3[0] + ((u64)S3[1] << 32))
+                                    : ((u64)S3[0] + ((u64)S3[1] << 30) + ((u64)S3[2] << 60))) & (rc.q - 1);
               if constexpr (OUT == kOutSwitched)
                 reinterpret_cast<uint32_t*>(J.out_body)[(size_t)t * J.rows + row] = pow2_modswitch(v, rk);
               else
                 reinterpret_cast<u64*>(J.out_body)[(size_t)t * J.rows + row] = v;
             } else {
-              const u64 v = body_combine(S3, rc);
+              const u64 v = planes ? body_combine_planes(S3, rc) : body_combine(S3, rc);
               if constexpr (OUT == kOutSwitched)
                 reinterpret_cast<uint32_t*>(J.out_body)[(size_t)t * J.rows + row] = modswitch_word(v, rc);
               else

@@ -546,7 +546,7 @@ cudaError_t matmul_packed_device(phe_ctx* c, const phe_weights::Dir& D, const ph
       J.cols = D.cols;
       J.T = tn;
       J.L = D.L;
-      J.tok_chunk = 16;
+      J.tok_chunk = phe::kDefaultTokChunk;
       J.tiles = D.rows * ((tn + J.tok_chunk - 1) / J.tok_chunk);
       jt.prefix[0] = 0;
       jt.prefix[1] = J.tiles;

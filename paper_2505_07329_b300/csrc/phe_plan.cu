@@ -323,7 +323,7 @@ phe_status phe_autotune(phe_ctx* c, const phe_job* jobs, uint32_t n_jobs, uint32
   DeviceGuard g(c->device);
   if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
-  const uint32_t chunks[] = {4, 8, 16, 32, 64};
+  const uint32_t chunks[] = {2, 4, 8, 16, 32, 64};
   const uint32_t bps[] = {0, 3};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
