@@ -1,0 +1,52 @@
+"""CPU checks of the benchmark's host-side arithmetic: the algorithmic work
+and bytes it divides by, and the client-side decryption helper it uses for
+the packed path's sanity check (against the oracle's negacyclic product)."""
+import math
+import os
+import sys
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import bench  # noqa: E402
+import synth  # noqa: E402
+
+
+def test_layer_work_and_bytes():
+    wl = synth.WORKLOADS["layer"]
+    N = wl.ring.N
+    mm = bench.matmuls(wl)
+    assert len(mm) == 14
+    rows = sum(r for _, _, _, r, _, _ in mm)
+    assert rows == 44032                       # 23 552 forward + 20 480 backward output rows
+    # L*N pointwise + (N/2) log2 N inverse-transform butterflies per output row
+    want = sum(r * (L * N + (N // 2) * int(math.log2(N))) for _, _, _, r, _, L in mm)
+    assert bench.modmuls_per_token(wl) == want
+    assert bench.out_bytes_per_token(wl) == rows * (N + 1) * 4
+    # inputs shared the way a layer shares them: x feeds q, k, v; h feeds gate, up
+    keys = {v[0] for v in bench.input_keys(wl).values()}
+    assert len(keys) == 11
+
+
+def test_alu_peaks_follow_the_probe_figures():
+    assert abs(bench.alu_peak_gmodmul("rns") - 148 * bench.BFLY32_PER_SM_CLK / 2 * 2.032) < 1e-9
+    assert abs(bench.alu_peak_gmodmul("prime") - 148 * bench.BFLY64_PER_SM_CLK * 2.032) < 1e-9
+
+
+def test_client_decryption_product_matches_the_oracle(orc):
+    rng = np.random.Generator(np.random.PCG64(5))
+    N, mod = 64, 1 << 32
+    a = rng.integers(0, mod, N, dtype=np.uint64)
+    s = rng.integers(-1, 2, N)
+    got = bench._negacyclic_small(a.astype(np.uint32), s, mod)
+    sq = np.array([v % mod for v in s.tolist()], dtype=np.uint64)
+    assert np.array_equal(got.astype(np.uint64), orc.negacyclic_mul(a, sq, mod))
+
+
+def test_paper_table_is_the_papers_six_shapes():
+    shapes = [shape for shape, _ in bench.PAPER_TABLE]
+    assert shapes == [(768, 768), (3072, 768), (2048, 2048), (768, 3072), (8192, 2048), (2048, 8192)]
+    assert all(t > 0 for _, t in bench.PAPER_TABLE)
