@@ -82,6 +82,8 @@ def parse():
                          "prime: q = 2^60 - 2^14 + 1 (64-bit kernels)")
     ap.add_argument("--serve-requests", type=int, default=48, help="requests in the serving measurement (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="mean Poisson arrival rate, requests/s")
+    ap.add_argument("--serve-light-rate", type=float, default=3.5,
+                    help="arrival rate of a second, light-load serving measurement (16 requests; 0 = skip)")
     return ap.parse_args()
 
 
@@ -227,7 +229,8 @@ def oracle_tokens_per_s(wl, seconds: float):
     return {"value": 1.0 / sec_per_token, "unit": "tokens/s", "cores": threads, "kind": "oracle",
             "sample": f"{done} (token,row) products, {rounds} rounds over all {len(mm)} projection/direction "
                       f"shapes, oracle NTT path on {threads} host threads, {elapsed:.1f} s wall; per-shape "
-                      f"mean time x rows, summed over the {per_token_items} products of one token"}
+                      f"mean time x rows, summed over the {per_token_items} products of one token; "
+                      f"q = 2^60-2^14+1 (the oracle's NTT needs a prime; same word size as p1 p2)"}
 
 
 def run_reference(args, wl, rank):
@@ -245,7 +248,9 @@ def run_reference(args, wl, rank):
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "tokens/s", "n_gpus": args.gpus,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value * wl.tokens,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64 (mod q)",
-            "data": "synthetic", "config": workload_config(wl, args, form="CPU oracle, bounded sample"),
+            "data": "synthetic",
+            "config": workload_config(wl, argparse.Namespace(**{**vars(args), "modulus": "prime"}),
+                                      form="CPU oracle, bounded sample (NTT path, extrapolated per token)"),
             "cpu_baseline": cb, "e2e": {"value": value, "unit": "tokens/s", "h2d_bytes_per_step": 0,
                                         "d2h_bytes_per_step": 0},
             "wall_s": time.perf_counter() - t_all}
@@ -496,6 +501,11 @@ def main():
         plans = []
         serving = measure_serving(phe, ctx, weights, wl, inputs, keys, args.serve_requests, args.serve_rate, T,
                                   tuning[0] if tuning else 2)
+        if args.serve_light_rate > 0:
+            # the same request mix at about half the served capacity: latency
+            # without a standing queue
+            serving["light_load"] = measure_serving(phe, ctx, weights, wl, inputs, keys, 16, args.serve_light_rate,
+                                                    T, tuning[0] if tuning else 2)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -544,6 +554,17 @@ def main():
 # taken at the 2032 MHz maximum (so the peaks below are not understated).
 BFLY64_PER_SM_CLK = 2.50
 BFLY32_PER_SM_CLK = 10.07
+# Measured HBM copy bandwidth (STREAM-style copy) from MEASURED_PEAKS.json
+# beside this file, else the same figure as recorded when this was written.
+def _hbm_gbps() -> float:
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"])
+    except (OSError, KeyError, ValueError):
+        return 6505.6
+
+
+HBM_GBPS = _hbm_gbps()
 
 
 def alu_peak_gmodmul(modulus: str) -> float:
@@ -629,8 +650,14 @@ def measure_serving(phe, ctx, weights, wl, inputs, keys, n_requests, rate, T_ava
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"], "mean_ms": st["mean_ms"],
             "iterations": st["iterations"], "mem_budget_bytes": 24 << 30,
             "peak_reserved_bytes": st["peak_reserved_bytes"],
-            "note": "offered load is far above capacity, so latency is mostly queueing; tokens/s here are tokens of "
-                    "single-projection requests, layer_equiv divides (token,row) items by the 44032 of a layer token"}
+            # saturated: the queue takes long to drain after the last arrival
+            "saturated": bool(wall - float(arrivals[-1]) > 0.25 * wall),
+            "note": ("offered load above capacity: latency is mostly queueing; "
+                     if wall - float(arrivals[-1]) > 0.25 * wall else
+                     "offered load below capacity: latency is service time plus short waits, and the rates divide "
+                     "by the server's busy time (idle waits between arrivals included); ") +
+                    "tokens/s are tokens of single-projection requests; layer_equiv divides (token,row) items by "
+                    "the 44032 of a layer token"}
 
 
 def measure_e2e(phe, ctx, weights, wl, mm, keys, inputs, tokens, stream):
@@ -746,6 +773,24 @@ def measure_packed(phe, ctx, weights, wl, mm, keys, inputs, S, q, tokens, stream
         phe.phe_trace_enable(ctx, False)
         kern = {n: round(v["total_ms"] / steps / tokens, 4) for n, v in tr.items()
                 if n.endswith("_kernel")}
+        # rooflines of the packing's two main kernels, per layer token: the
+        # digit transforms (ALU: 32-bit butterflies, two residues) and the MAC
+        # (HBM: transformed digits once, the key once per 8 units)
+        units = sum((rows + N - 1) // N for (_, _, _, rows, _, _) in mm)
+        lg = int(math.log2(N))
+        bfly = units * N * (N // 2) * lg * 2
+        mac_bytes = units * (N * N * 8 + 2 * N * N * 16 / 8)
+        pack_roof = []
+        if kern.get("input_ntt_kernel"):
+            ach = bfly / (kern["input_ntt_kernel"] / 1e3) / 1e9
+            peak = 148 * BFLY32_PER_SM_CLK * 2.032
+            pack_roof.append({"kernel": "input_ntt_kernel (digit rows)", "bound": "alu", "unit": "G 32-bit bfly/s",
+                              "achieved": ach, "peak": peak, "frac": ach / peak,
+                              "note": "the kernel time also holds the 16 input-mask transforms, < 1%"})
+        if kern.get("pack_mac_kernel"):
+            ach = mac_bytes / (kern["pack_mac_kernel"] / 1e3) / 1e9
+            pack_roof.append({"kernel": "pack_mac_kernel", "bound": "hbm", "unit": "GB/s", "achieved": ach,
+                              "peak": HBM_GBPS, "frac": ach / HBM_GBPS})
         # client-side check: RLWE of the first product, first token, first group
         pi, name, d, rows, cols, L = mm[0]
         _, _, X = inputs[keys[(pi, d)][0]]
@@ -784,6 +829,7 @@ def measure_packed(phe, ctx, weights, wl, mm, keys, inputs, S, q, tokens, stream
     return {"value": tokens * steps / (ms / 1e3), "unit": "tokens/s", "tokens": tokens,
             "ms_per_token": ms / steps / tokens, "kernel_ms_per_token": kern,
             "ksk": {"base_log": base_log, "ell": 1, "device_bytes": 2 * N * N * 16},
+            "roofline": pack_roof,
             "out_bytes_per_token": out_bytes, "unpacked_out_bytes_per_token": out_bytes_per_token(wl),
             "sanity_decrypt": f"{ok}/{y.shape[0]} coefficients, {zero}/{N - y.shape[0]} unused zero",
             "e2e": {"value": tokens * steps / dt, "unit": "tokens/s", "h2d_bytes_per_step": h2d,
