@@ -14,40 +14,14 @@
 
 using phe::u32;
 using phe::u64;
+using phe::cuda_fail;
+using phe::DeviceGuard;
+using phe::fail;
 typedef unsigned __int128 u128;
 
 namespace {
 
 thread_local std::string g_err;
-
-phe_status fail(phe_status s, const char* fmt, ...) {
-  char buf[512];
-  va_list ap;
-  va_start(ap, fmt);
-  vsnprintf(buf, sizeof(buf), fmt, ap);
-  va_end(ap);
-  g_err = buf;
-  return s;
-}
-
-phe_status cuda_fail(cudaError_t e, const char* what) {
-  if (e == cudaErrorMemoryAllocation) return fail(PHE_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
-  return fail(PHE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
-}
-
-// Makes the context's device current for the duration of a call.
-struct DeviceGuard {
-  int prev = -1;
-  cudaError_t err = cudaSuccess;
-  explicit DeviceGuard(int dev) {
-    err = cudaGetDevice(&prev);
-    if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
 
 // --- host modular arithmetic (parameter set-up only) ---------------------
 u64 mulmod(u64 a, u64 b, u64 q) { return (u64)(((u128)a * b) % q); }
@@ -236,6 +210,21 @@ phe_status check_matmul_args(phe_ctx* c, const phe_weights* w, int dir, uint32_t
 
 namespace phe {
 void set_last_error(const char* msg) { g_err = msg; }
+
+phe_status fail(phe_status s, const char* fmt, ...) {
+  char buf[512];
+  va_list ap;
+  va_start(ap, fmt);
+  vsnprintf(buf, sizeof(buf), fmt, ap);
+  va_end(ap);
+  g_err = buf;
+  return s;
+}
+
+phe_status cuda_fail(cudaError_t e, const char* what) {
+  if (e == cudaErrorMemoryAllocation) return fail(PHE_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
+  return fail(PHE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
+}
 
 void set_switch_target(RnsConst& k, u32 log2_target) {
   const u32 p1 = k.p1, p2 = k.p2;

@@ -187,6 +187,24 @@ int lwedot_threads(int logn);
 cudaError_t prepare_launches(const phe_ctx* c);
 // Sets the calling thread's phe_last_error() message (phe_capi.cu).
 void set_last_error(const char* msg);
+// Sets the message from a printf-style format and returns s (phe_capi.cu).
+phe_status fail(phe_status s, const char* fmt, ...);
+// fail() with a CUDA error's text; an allocation failure maps to PHE_ENOMEM.
+phe_status cuda_fail(cudaError_t e, const char* what);
+
+// Makes a device current for the duration of a call.
+struct DeviceGuard {
+  int prev = -1;
+  cudaError_t err = cudaSuccess;
+  explicit DeviceGuard(int dev) {
+    err = cudaGetDevice(&prev);
+    if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
+  }
+  ~DeviceGuard() {
+    int cur = -1;
+    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
+  }
+};
 // Sets the constants of rns_modswitch in k (p1, p2 set) for the target
 // modulus 2^log2_target, 1 <= log2_target <= 32 (phe_capi.cu).
 void set_switch_target(RnsConst& k, u32 log2_target);

@@ -15,6 +15,10 @@
 
 #include "phe_host.hpp"
 
+using phe::cuda_fail;
+using phe::DeviceGuard;
+using phe::fail;
+
 namespace {
 
 // The scratch array.  Every GPU that loads the library holds it until the
@@ -28,15 +32,6 @@ constexpr int kMaxDevices = 64;
 std::mutex g_mutex;
 phe::u64* g_scratch_ptr[kMaxDevices] = {};
 
-phe_status fail(phe_status s, const char* fmt, ...) {
-  char buf[256];
-  va_list ap;
-  va_start(ap, fmt);
-  vsnprintf(buf, sizeof(buf), fmt, ap);
-  va_end(ap);
-  phe::set_last_error(buf);
-  return s;
-}
 
 // Device address of the scratch array on `device` (which must be current),
 // looked up once per device.

@@ -15,6 +15,9 @@
 
 using phe::u32;
 using phe::u64;
+using phe::cuda_fail;
+using phe::DeviceGuard;
+using phe::fail;
 
 struct phe_plan {
   phe_ctx* ctx = nullptr;
@@ -40,33 +43,8 @@ struct phe_plan {
 
 namespace {
 
-phe_status fail(phe_status s, const char* fmt, ...) {
-  char buf[384];
-  va_list ap;
-  va_start(ap, fmt);
-  vsnprintf(buf, sizeof(buf), fmt, ap);
-  va_end(ap);
-  phe::set_last_error(buf);
-  return s;
-}
 
-phe_status cuda_fail(cudaError_t e, const char* what) {
-  if (e == cudaErrorMemoryAllocation) return fail(PHE_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
-  return fail(PHE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
-}
 
-struct DeviceGuard {
-  int prev = -1;
-  cudaError_t err = cudaSuccess;
-  explicit DeviceGuard(int dev) {
-    err = cudaGetDevice(&prev);
-    if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    int cur = -1;
-    if (prev >= 0 && cudaGetDevice(&cur) == cudaSuccess && cur != prev) cudaSetDevice(prev);
-  }
-};
 
 phe_status check_job(const phe_ctx* c, const phe_job& j, uint32_t idx) {
   if (!j.w) return fail(PHE_EINVAL, "job %u: null weights", idx);

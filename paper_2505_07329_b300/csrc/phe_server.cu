@@ -31,19 +31,13 @@
 
 using phe::u32;
 using phe::u64;
+using phe::cuda_fail;
+using phe::DeviceGuard;
+using phe::fail;
 using Clock = std::chrono::steady_clock;
 
 namespace {
 
-phe_status fail(phe_status s, const char* fmt, ...) {
-  char buf[384];
-  va_list ap;
-  va_start(ap, fmt);
-  vsnprintf(buf, sizeof(buf), fmt, ap);
-  va_end(ap);
-  phe::set_last_error(buf);
-  return s;
-}
 
 double ms_since(Clock::time_point a, Clock::time_point b) {
   return std::chrono::duration<double, std::milli>(b - a).count();

@@ -17,6 +17,9 @@
 
 using phe::u32;
 using phe::u64;
+using phe::cuda_fail;
+using phe::DeviceGuard;
+using phe::fail;
 
 namespace phe {
 
@@ -73,32 +76,8 @@ namespace {
 
 using phe::Span;
 
-phe_status fail(phe_status s, const char* fmt, ...) {
-  char buf[384];
-  va_list ap;
-  va_start(ap, fmt);
-  vsnprintf(buf, sizeof(buf), fmt, ap);
-  va_end(ap);
-  phe::set_last_error(buf);
-  return s;
-}
 
-phe_status cuda_fail(cudaError_t e, const char* what) {
-  if (e == cudaErrorMemoryAllocation) return fail(PHE_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
-  return fail(PHE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
-}
 
-struct DeviceGuard {
-  int prev = -1;
-  cudaError_t err = cudaSuccess;
-  explicit DeviceGuard(int dev) {
-    err = cudaGetDevice(&prev);
-    if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    if (prev >= 0) cudaSetDevice(prev);
-  }
-};
 
 u32 words_of(u64 fields, u32 bits) { return (u32)((fields * bits + 31) / 32); }
 
