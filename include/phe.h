@@ -366,13 +366,13 @@ uint64_t phe_ksk_device_bytes(const phe_ksk* k);
 
 /* Packs T x rows given LWE ciphertexts of dimension N.
  *   d_lwe_mask  [T][rows][N] uint64 words below q (as phe_matmul writes with PHE_OUT_RAW;
- *               larger words give unspecified results, never a fault)
+ *               larger words give unspecified results, never a fault); 16-byte aligned
  *   d_lwe_body  [T][rows]    uint64 mod q
  *   d_out_a, d_out_b  [T][G][N]: uint32 words mod 2^log2_qout (PHE_OUT_SWITCHED)
  *               or uint64 mod q (PHE_OUT_RAW); RLWE_g of token t at (t*G + g)*N.
  * Allocates its scratch (at most 2 GiB of digit rows at a time) on `stream`
- * with cudaMallocAsync.  Errors: PHE_EINVAL (handles, flags, T*G > 2^24),
- * PHE_ENOMEM, PHE_ECUDA. */
+ * from the context's memory pool.  Errors: PHE_EINVAL (handles, flags,
+ * T*G > 2^24, unaligned masks), PHE_ENOMEM, PHE_ECUDA. */
 phe_status phe_pack(phe_ctx* ctx, const phe_ksk* k, uint32_t T, uint32_t rows, const uint64_t* d_lwe_mask,
                      const uint64_t* d_lwe_body, void* d_out_a, void* d_out_b, uint32_t flags, void* stream);
 

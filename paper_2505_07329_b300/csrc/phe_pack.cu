@@ -25,6 +25,9 @@
 
 using phe::u32;
 using phe::u64;
+using phe::cuda_fail;
+using phe::DeviceGuard;
+using phe::fail;
 
 struct phe_ksk {
   phe_ctx* ctx = nullptr;
@@ -66,37 +69,53 @@ __device__ __forceinline__ void signed_digits(u32 v, u32 base_log, int (&d)[ELL]
 // gN + j < rows and 0 past the last row.  SWITCHED: the masks are already
 // a~ (uint32, switched to B^ell by the product kernel's epilogue); otherwise
 // they are words below q, switched here with rcK (log2_qout = base_log*ell).
-// A 32x32 tile of (j, i) goes through shared memory so that both the load
-// (along i) and the store (along j) are coalesced.
+// A block moves a 64 (i) x 32 (j) tile through shared memory, so that both
+// the load (two words of i per thread) and the store (along j) are coalesced.
 template <int ELL, bool SWITCHED>
 __global__ void __launch_bounds__(256)
     pack_decompose_kernel(const void* __restrict__ maskv, u32 rows, u32 N, u32 G, u32 u_base, u32 base_log,
                           RingConst rcK, int32_t* __restrict__ D) {
-  __shared__ int tile[ELL][32][33];
+  __shared__ int tile[ELL][64][33];
   const u32 u = blockIdx.z;  // unit within the chunk; D holds the chunk's units
   const u32 t = (u_base + u) / G, g = (u_base + u) % G;
-  const u32 i0 = blockIdx.x * 32, j0 = blockIdx.y * 32;
+  const u32 i0 = blockIdx.x * 64, j0 = blockIdx.y * 32;
   const u32 tx = threadIdx.x, ty = threadIdx.y;
-  for (u32 k = ty; k < 32; k += 8) {
-    const u32 j = j0 + k, row = g * N + j;
-    int d[ELL];
-    if (row < rows) {
-      const size_t at = ((size_t)t * rows + row) * N + i0 + tx;
-      const u32 v = SWITCHED ? static_cast<const u32*>(maskv)[at]
-                             : modswitch_word(static_cast<const u64*>(maskv)[at], rcK);
-      signed_digits<ELL>(v, base_log, d);
+  const size_t first = ((size_t)t * rows + (size_t)g * N + j0) * N + i0;  // mask word (row gN+j0, column i0)
+#pragma unroll
+  for (u32 m = 0; m < 4; ++m) {
+    const u32 k = ty + 8 * m;
+    int d0[ELL], d1[ELL];
+    if (g * N + j0 + k < rows) {
+      u32 v0, v1;
+      if constexpr (SWITCHED) {
+        const uint2 v = *reinterpret_cast<const uint2*>(static_cast<const u32*>(maskv) + first + (size_t)k * N + 2 * tx);
+        v0 = v.x;
+        v1 = v.y;
+      } else {
+        const ulonglong2 v =
+            *reinterpret_cast<const ulonglong2*>(static_cast<const u64*>(maskv) + first + (size_t)k * N + 2 * tx);
+        v0 = modswitch_word(v.x, rcK);
+        v1 = modswitch_word(v.y, rcK);
+      }
+      signed_digits<ELL>(v0, base_log, d0);
+      signed_digits<ELL>(v1, base_log, d1);
     } else {
 #pragma unroll
-      for (int l = 0; l < ELL; ++l) d[l] = 0;
+      for (int l = 0; l < ELL; ++l) d0[l] = d1[l] = 0;
     }
 #pragma unroll
-    for (int l = 0; l < ELL; ++l) tile[l][tx][k] = d[l];
+    for (int l = 0; l < ELL; ++l) {
+      tile[l][2 * tx][k] = d0[l];
+      tile[l][2 * tx + 1][k] = d1[l];
+    }
   }
   __syncthreads();
-  for (u32 k = ty; k < 32; k += 8) {
-    const u32 i = i0 + k;
+  int32_t* out = D + ((size_t)u * N + i0) * ELL * N + j0;
 #pragma unroll
-    for (int l = 0; l < ELL; ++l) D[(((size_t)u * N + i) * ELL + l) * N + j0 + tx] = tile[l][k][tx];
+  for (u32 m = 0; m < 8; ++m) {
+    const u32 k = ty + 8 * m;  // i = i0 + k
+#pragma unroll
+    for (int l = 0; l < ELL; ++l) out[((size_t)k * ELL + l) * N + tx] = tile[l][k][tx];
   }
 }
 
@@ -349,32 +368,8 @@ namespace {
 
 using phe::Span;
 
-phe_status fail(phe_status s, const char* fmt, ...) {
-  char buf[384];
-  va_list ap;
-  va_start(ap, fmt);
-  vsnprintf(buf, sizeof(buf), fmt, ap);
-  va_end(ap);
-  phe::set_last_error(buf);
-  return s;
-}
 
-phe_status cuda_fail(cudaError_t e, const char* what) {
-  if (e == cudaErrorMemoryAllocation) return fail(PHE_ENOMEM, "%s: %s", what, cudaGetErrorString(e));
-  return fail(PHE_ECUDA, "%s: %s", what, cudaGetErrorString(e));
-}
 
-struct DeviceGuard {
-  int prev = -1;
-  cudaError_t err = cudaSuccess;
-  explicit DeviceGuard(int dev) {
-    err = cudaGetDevice(&prev);
-    if (err == cudaSuccess && prev != dev) err = cudaSetDevice(dev);
-  }
-  ~DeviceGuard() {
-    if (prev >= 0) cudaSetDevice(prev);
-  }
-};
 
 constexpr int kMacUnits = 8;                        // units per pack_mac_kernel block
 constexpr int kMacStages = 4;                       // rows in flight per pack_mac_kernel thread
@@ -384,7 +379,7 @@ constexpr uint64_t kPackScratchBytes = 2ull << 30;  // digit rows in flight per 
 cudaError_t launch_decompose(const phe_ctx* c, const phe_ksk* k, const void* mask, bool switched, u32 rows, u32 G,
                              u32 u_base, u32 cu, int32_t* D, cudaStream_t s) {
   const u32 N = c->prm.N;
-  const dim3 grid(N / 32, N / 32, cu), block(32, 8);
+  const dim3 grid(N / 64, N / 32, cu), block(32, 8);
 #define PHE_DECOMP(E)                                                                                       \
   (switched ? phe::pack_decompose_kernel<E, true><<<grid, block, 0, s>>>(mask, rows, N, G, u_base, k->base_log, \
                                                                           k->rcK, D)                        \
@@ -641,6 +636,8 @@ phe_status phe_pack(phe_ctx* c, const phe_ksk* k, uint32_t T, uint32_t rows, con
   if (flags != PHE_OUT_SWITCHED && flags != PHE_OUT_RAW) return fail(PHE_EINVAL, "phe_pack: flags=%u", flags);
   if (T == 0 || rows == 0) return PHE_OK;
   if (!d_lwe_mask || !d_lwe_body || !d_out_a || !d_out_b) return fail(PHE_EINVAL, "phe_pack: null buffer");
+  if (reinterpret_cast<uintptr_t>(d_lwe_mask) % 16)
+    return fail(PHE_EINVAL, "phe_pack: d_lwe_mask must be 16-byte aligned (the masks are read two words at a time)");
   const u32 G = (rows + c->prm.N - 1) / c->prm.N;
   if ((u64)T * G > (1u << 24)) return fail(PHE_EINVAL, "phe_pack: T*ceil(rows/N)=%llu exceeds 2^24",
                                            (unsigned long long)((u64)T * G));

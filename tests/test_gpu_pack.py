@@ -295,3 +295,22 @@ def test_matmul_packed_seeded_matches_mask_form(orc, ctxs, modulus):
                                      np.arange(N))
             assert np.array_equal(oa[t, grp].cpu().numpy().view(np.uint64), ea), (t, grp)
             assert np.array_equal(ob[t, grp].cpu().numpy().view(np.uint64), eb), (t, grp)
+
+
+def test_pack_rejects_unaligned_masks(ctxs):
+    import torch
+    N = 256
+    q = synth.Q_RNS
+    ctx = ctxs(N, "rns")
+    g = _rng(95)
+    k = phe.phe_ksk_upload(ctx, g.integers(0, q, (N, 1, N), dtype=np.uint64),
+                           g.integers(0, q, (N, 1, N), dtype=np.uint64), 26, 1)
+    try:
+        buf = torch.zeros(N * 40 + 1, dtype=torch.int64, device="cuda")
+        body = torch.zeros(40, dtype=torch.int64, device="cuda")
+        oa = torch.empty((1, 1, N), dtype=torch.int32, device="cuda")
+        with pytest.raises(phe.PheError) as ei:
+            phe.phe_pack(ctx, k, 1, 40, buf[1:].data_ptr(), body, oa, torch.empty_like(oa))   # 8-byte offset
+        assert ei.value.status == phe.PHE_EINVAL and "aligned" in str(ei.value)
+    finally:
+        phe.phe_ksk_free(k)
