@@ -114,3 +114,52 @@ def test_tight_budget_serialises_but_completes(env):
     ga, gb = gpu_matmul(ctx, ws[1], phe.PHE_FWD, r["A"], r["B"], 200)
     got = _result(r)
     assert np.array_equal(got[0], ga) and np.array_equal(got[1], gb)
+
+
+@pytest.mark.parametrize("q,rns,Nr", [(synth.Q_RNS, (synth.RNS_P1, synth.RNS_P2), 1024),
+                                      (1 << 39, (synth.RNS_P1, synth.RNS_P2), 2048)])
+def test_served_and_batched_forms_for_the_rns_and_power_of_two_moduli(q, rns, Nr):
+    """The served form and a plan, with the benchmark's RNS modulus and with
+    the paper's q = 2^39, equal the per-call path word for word."""
+    import torch
+    ctx = phe.phe_ctx_create(Nr, q, 26 if q == 1 << 39 else 32, 0, rns=rns)
+    Ws = [synth.weights(70, 2100, seed=11), synth.weights(300, 500, seed=12)]
+    ws = [phe.phe_weights_upload(ctx, W) for W in Ws]
+    try:
+        reqs = []
+        for n, (pi, d, T) in enumerate([(0, phe.PHE_FWD, 9), (1, phe.PHE_BWD, 5), (1, phe.PHE_FWD, 13)]):
+            W = Ws[pi] if d == phe.PHE_FWD else np.ascontiguousarray(Ws[pi].T)
+            rows, cols = W.shape
+            L = synth.blocks(cols, Nr)
+            A = synth.uniform_words((T, L, Nr), q, 40 + n)
+            B = synth.uniform_words((T, L, Nr), q, 60 + n)
+            ref_m = torch.empty((T, rows, Nr), dtype=torch.int32, device="cuda")
+            ref_b = torch.empty((T, rows), dtype=torch.int32, device="cuda")
+            dA, dB = to_dev_u64(A), to_dev_u64(B)
+            phe.phe_matmul(ctx, ws[pi], d, T, dA, dB, ref_m, ref_b)
+            hm = torch.full((T, rows, Nr), -1, dtype=torch.int32).pin_memory()
+            hb = torch.full((T, rows), -1, dtype=torch.int32).pin_memory()
+            pm, pb = torch.empty_like(ref_m), torch.empty_like(ref_b)
+            reqs.append(dict(pi=pi, d=d, T=T, dA=dA, dB=dB, ref=(ref_m, ref_b), host=(hm, hb), plan=(pm, pb)))
+        torch.cuda.synchronize()
+        srv = phe.phe_server_create(ctx, 1 << 30, chunk_tokens=4, tok_chunk=2)
+        try:
+            ids = [phe.phe_server_submit(srv, ws[r["pi"]], r["d"], r["T"], r["dA"], r["dB"], *r["host"]) for r in reqs]
+            for i in ids:
+                phe.phe_server_wait(srv, i, 120000)
+        finally:
+            phe.phe_server_destroy(srv)
+        plan = phe.phe_plan_create(ctx, [(ws[r["pi"]], r["d"], r["T"], r["dA"], r["dB"], *r["plan"]) for r in reqs],
+                                   phe.PHE_OUT_SWITCHED, (2, 0))
+        try:
+            phe.phe_plan_run(plan)
+            torch.cuda.synchronize()
+        finally:
+            phe.phe_plan_destroy(plan)
+        for r in reqs:
+            assert torch.equal(r["host"][0], r["ref"][0].cpu()) and torch.equal(r["host"][1], r["ref"][1].cpu())
+            assert torch.equal(r["plan"][0], r["ref"][0]) and torch.equal(r["plan"][1], r["ref"][1])
+    finally:
+        for w in ws:
+            phe.phe_weights_free(w)
+        phe.phe_ctx_destroy(ctx)
