@@ -232,12 +232,12 @@ void set_switch_target(RnsConst& k, u32 log2_target) {
   k.a1 = (u32)(two_k / p1);
   k.b1 = (u32)(two_k % p1);
   k.b1p = shoup32(k.b1, p1);
-  k.a2 = (u32)(two_k / p2);
-  k.b2 = (u32)(two_k % p2);
-  k.b2p = shoup32(k.b2, p2);
-  k.inv_a2 = (u32)((1ull << 32) / p2);
+  k.s2 = 0;
+  while ((p2 >> k.s2) != 0) ++k.s2;
+  k.mu2 = (u32)(((1ull << (32 + k.s2)) / p2) - (1ull << 32));  // p2 < 2^30
   k.half1 = (p1 - 1) / 2;
   k.half2 = (p2 - 1) / 2;
+  k.kbits = log2_target;
   k.kmask = (u32)(two_k - 1);
 }
 }  // namespace phe

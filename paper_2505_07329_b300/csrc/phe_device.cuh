@@ -126,10 +126,9 @@ struct RnsConst {
   u32 c32b, c32bp;    // 2^32 mod p2 and its Shoup quotient
   // switch to 2^k from residues: 2^k = a1 p1 + b1 = a2 p2 + b2
   u32 a1, b1, b1p;    // b1p = floor(b1 2^32 / p1)
-  u32 a2, b2, b2p;    // b2p = floor(b2 2^32 / p2)
-  u32 inv_a2;         // floor(2^32 / p2)
+  u32 s2, mu2;        // s2 = bit length of p2; mu2 = floor(2^(32+s2) / p2) - 2^32
   u32 half1, half2;   // (p1 - 1)/2, (p2 - 1)/2
-  u32 kmask;          // 2^k - 1
+  u32 kbits, kmask;   // k and 2^k - 1
   // A power-of-two ciphertext modulus q = 2^p2k computed through p1 p2: the
   // products are exact integers below (p1 p2)/2 in magnitude, so the centred
   // CRT value reduced mod 2^p2k is the product mod q (p2k = 0: q = p1 p2).
@@ -154,36 +153,37 @@ __device__ __forceinline__ u32 crt_digit(u32 c1, u32 c2, const RnsConst& k) {
   const u32 d = sub_if32(c2 + k.p2 - c1, k.p2);  // c1 < p1 < p2
   return sub_if32(mul_shoup32(d, k.inv, k.invp, k.p2), k.p2);
 }
+// The same digit from a lazily reduced second residue, c2 in [0, 2 p2): the
+// Shoup product takes c2 + 2 p2 - c1 in (0, 4 p2) as it is.
+__device__ __forceinline__ u32 crt_digit_lazy(u32 c1, u32 c2, const RnsConst& k) {
+  return sub_if32(mul_shoup32(c2 + 2 * k.p2 - c1, k.inv, k.invp, k.p2), k.p2);
+}
 __device__ __forceinline__ u64 from_residues(u32 c1, u32 c2, const RnsConst& k) {
   return (u64)c1 + (u64)k.p1 * crt_digit(c1, c2, k);
 }
 
 // ModulusSwitch q -> 2^k of c = c1 + p1 h given by its CRT digits, in 32-bit
-// arithmetic only.  With h 2^k = a p2 + b (0 <= b < p2) and, since q is odd,
-// floor(q/2) = p1 (p2-1)/2 + (p1-1)/2, one gets
-//   c 2^k + floor(q/2) = a q + p1 n + v,  n = b + (p2-1)/2 + g,  0 <= v < p1,
-// where g = floor((c1 2^k + (p1-1)/2) / p1); hence
-//   floor((c 2^k + floor(q/2)) / q) = a + floor(n / p2)
-// (v/p1 < 1 cannot carry n past a multiple of p2).  a, b and g come from
-// Shoup products with the constants b2 = 2^k mod p2 and b1 = 2^k mod p1,
-// and floor(n / p2) = floor(g / p2) + {0, 1, 2}.
+// arithmetic only.  q is odd, so floor(q/2) = p1 (p2-1)/2 + (p1-1)/2, and
+// floor(x / n) = floor(floor(x) / n) for an integer n gives
+//   floor((c 2^k + floor(q/2)) / q) = floor(Z / p2),
+//   Z = h 2^k + g + (p2-1)/2,  g = floor((c1 2^k + (p1-1)/2) / p1) <= 2^k.
+// g: with 2^k = a1 p1 + b1, a Shoup product c1 b1 = s1 p1 + r1 leaves r1 in
+// [0, 2 p1), so r1 + (p1-1)/2 adds 0, 1 or 2 whole p1.  floor(Z / p2): Z <
+// 2^(32+s2) (p2 < 2^s2); the top word z = floor(Z / 2^s2) times
+// mu = floor(2^(32+s2) / p2) in (2^32, 2^33) estimates it from below, off by
+// less than 2^s2/p2 + z/2^32 + 1 < 4.  The remainder Z - Qe p2 < 4 p2 < 2^32
+// is then exact in the low word and three comparisons finish the quotient.
 __device__ __forceinline__ u32 rns_modswitch(u32 c1, u32 h, const RnsConst& k) {
-  u32 s = __umulhi(k.b2p, h);
-  u32 b = h * k.b2 - s * k.p2;  // [0, 2 p2)
-  if (b >= k.p2) { b -= k.p2; ++s; }
-  const u32 a = h * k.a2 + s;
-  u32 s1 = __umulhi(k.b1p, c1);
-  u32 r1 = c1 * k.b1 - s1 * k.p1;  // [0, 2 p1)
-  if (r1 >= k.p1) { r1 -= k.p1; ++s1; }
-  const u32 g = c1 * k.a1 + s1 + (r1 + k.half1 >= k.p1 ? 1u : 0u);
-  u32 G = __umulhi(g, k.inv_a2);  // floor(g / p2) or one less
-  u32 gr = g - G * k.p2;
-  if (gr >= k.p2) { gr -= k.p2; ++G; }
-  u32 n = b + k.half2 + gr;       // < 2.5 p2
-  u32 t = 0;
-  if (n >= k.p2) { n -= k.p2; ++t; }
-  if (n >= k.p2) ++t;
-  return (a + G + t) & k.kmask;
+  const u32 s1 = __umulhi(k.b1p, c1);
+  const u32 r1 = c1 * k.b1 - s1 * k.p1;  // [0, 2 p1)
+  const u32 v = r1 + k.half1;           // [0, 2.5 p1)
+  const u32 g = c1 * k.a1 + s1 + (u32)(v >= k.p1) + (u32)(v >= 2 * k.p1);
+  const u64 Z = ((u64)h << k.kbits) + g + k.half2;
+  const u32 z = (u32)(Z >> k.s2);
+  const u32 Qe = z + __umulhi(z, k.mu2);
+  const u32 r = (u32)Z - Qe * k.p2;      // [0, 4 p2)
+  const u32 t = (u32)(r >= k.p2) + (u32)(r >= 2 * k.p2) + (u32)(r >= 3 * k.p2);
+  return (Qe + t) & k.kmask;
 }
 
 // Power-of-two q (RnsConst::p2k > 0).  Input word -> residues of its centred

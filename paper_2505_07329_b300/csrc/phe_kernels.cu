@@ -198,9 +198,14 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB)
 //         B2 < 16; |sum| < 2^14 2^7 2^30 = 2^51 < q), reduced across the
 //         block and switched.
 // --------------------------------------------------------------------------
-#ifndef PHE_LWEDOT_MIN_BLOCKS
-#define PHE_LWEDOT_MIN_BLOCKS 3
+// Resident threads per SM the register budget is sized for: 3 blocks of 256
+// (80 registers a thread).  A 512-thread block (N = 8192) gets one block's
+// worth, not three: 3 x 512 threads would leave 40 registers and spill.
+#ifndef PHE_LWEDOT_MIN_THREADS
+#define PHE_LWEDOT_MIN_THREADS 768
 #endif
+template <int TPB>
+constexpr int lwedot_min_blocks() { return (PHE_LWEDOT_MIN_THREADS / TPB) > 0 ? PHE_LWEDOT_MIN_THREADS / TPB : 1; }
 
 // One thread's share of the body dot product of (token t, row).
 __device__ __forceinline__ void body_partial(const LweJob& J, u32 row, u32 t, int p, int P, int N,
@@ -282,7 +287,7 @@ __device__ __forceinline__ u64 body_combine(const long long (&S)[3], const RingC
 }
 
 template <int LOGN, int MODE, bool RNS>
-__global__ void __launch_bounds__(Shape<LOGN>::TPB, PHE_LWEDOT_MIN_BLOCKS)
+__global__ void __launch_bounds__(Shape<LOGN>::TPB, lwedot_min_blocks<Shape<LOGN>::TPB>())
     lwedot_kernel(const LweJobTable jt, RingConst rc, RnsConst rk, const void* __restrict__ tw0v,
                   const void* __restrict__ twcv) {
   constexpr int OUT = MODE & 3;                 // kOutSwitched, kOutRaw or kOutRing
@@ -395,12 +400,12 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, PHE_LWEDOT_MIN_BLOCKS)
             const size_t o = ((size_t)t * J.rows + row) * N + (N - 1 - pos);
             if constexpr (P2) {
               const u32 c1 = sub_if32(x[e].x, rk.p1);
-              const u64 v = pow2_from_crt(c1, crt_digit(c1, sub_if32(x[e].y, rk.p2), rk), rk);
+              const u64 v = pow2_from_crt(c1, crt_digit_lazy(c1, x[e].y, rk), rk);
               if constexpr (SWM) reinterpret_cast<uint32_t*>(J.out)[o] = pow2_modswitch(v, rk);
               else reinterpret_cast<u64*>(J.out)[o] = v;
             } else if constexpr (RNS) {
               const u32 c1 = sub_if32(x[e].x, rk.p1);
-              const u32 h = crt_digit(c1, sub_if32(x[e].y, rk.p2), rk);
+              const u32 h = crt_digit_lazy(c1, x[e].y, rk);
               if constexpr (SWM) reinterpret_cast<uint32_t*>(J.out)[o] = rns_modswitch(c1, h, rk);
               else reinterpret_cast<u64*>(J.out)[o] = (u64)c1 + (u64)rk.p1 * h;
             } else {
