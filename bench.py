@@ -42,8 +42,9 @@ METRIC = "encrypted W·[x] tokens/s per Llama-1B layer; p50/p99 latency; % of ro
 # with ncu, and the algorithmic bytes of that launch.  Valid only for the
 # kernel sources the counters were taken on (hash of phe_kernels.cu +
 # phe_device.cuh).
-TRAFFIC_KERNEL_HASH = "130ee03dbc893ae3"
-TRAFFIC_BYTES_PER_LAUNCH = 95933.0e6
+TRAFFIC_KERNEL_HASH = "b8905cc2b8b53350"
+TRAFFIC_TUNING = (16, 0)
+TRAFFIC_BYTES_PER_LAUNCH = 97022.4e6
 TRAFFIC_ALG_BYTES_PER_LAUNCH = 95891.8e6
 
 
@@ -442,7 +443,8 @@ def main():
     achieved = modmuls / (kernel_ms / 1e3) / 1e9 if kernel_ms else None
     peak = alu_peak_gmodmul(args.modulus)
     traffic_ok = (kernel_source_hash() == TRAFFIC_KERNEL_HASH and wl.name == "layer" and bchunk == 128
-                  and args.form == "batched" and args.modulus == "rns" and T % bchunk == 0)
+                  and args.form == "batched" and args.modulus == "rns" and T % bchunk == 0
+                  and tuning is not None and tuple(tuning) == TRAFFIC_TUNING)
     roof = {"bound": "alu", "unit": "Gmodmul/s", "achieved": achieved, "peak": peak,
             "frac": (achieved / peak) if achieved and peak else None,
             "traffic": TRAFFIC_BYTES_PER_LAUNCH if traffic_ok else None,
@@ -500,12 +502,12 @@ def main():
             phe.phe_plan_destroy(pl)
         plans = []
         serving = measure_serving(phe, ctx, weights, wl, inputs, keys, args.serve_requests, args.serve_rate, T,
-                                  tuning[0] if tuning else 2)
+                                  tuning[0] if tuning else 8)
         if args.serve_light_rate > 0:
             # the same request mix at about half the served capacity: latency
             # without a standing queue
             serving["light_load"] = measure_serving(phe, ctx, weights, wl, inputs, keys, 16, args.serve_light_rate,
-                                                    T, tuning[0] if tuning else 2)
+                                                    T, tuning[0] if tuning else 8)
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -602,7 +604,7 @@ def sanity_decrypt(wl, mm, inputs, keys, outs, S, T, chunk):
     return f"{ok}/{tot}"
 
 
-def measure_serving(phe, ctx, weights, wl, inputs, keys, n_requests, rate, T_avail, tok_chunk=2):
+def measure_serving(phe, ctx, weights, wl, inputs, keys, n_requests, rate, T_avail, tok_chunk=8):
     """The served form: requests from 64 clients arrive as a Poisson process
     (mean `rate` per second); each is one projection of the layer in one
     direction with U{64..2048} tokens (its inputs are slices of the resident

@@ -329,7 +329,7 @@ def phe_autotune(ctx, jobs, flags: int = PHE_OUT_SWITCHED, sample_tokens: int = 
     return (best.tok_chunk, best.blocks_per_sm), (ms.value if timed else None)
 
 
-def phe_server_create(ctx, mem_budget_bytes: int, chunk_tokens: int = 32, tok_chunk: int = 2, blocks_per_sm: int = 0,
+def phe_server_create(ctx, mem_budget_bytes: int, chunk_tokens: int = 32, tok_chunk: int = 8, blocks_per_sm: int = 0,
                       max_active: int = 64, max_jobs_per_iteration: int = 64, max_queue: int = 4096,
                       wait_timeout_ms: int = 60000, flags: int = PHE_OUT_SWITCHED, simulate: bool = False,
                       sim_ns_per_item: float = 0.0):
