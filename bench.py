@@ -69,6 +69,8 @@ def parse():
     ap.add_argument("--chunk", type=int, default=32, help="tokens per plain-form call")
     ap.add_argument("--batch-chunk", type=int, default=128, help="tokens per batched-form plan")
     ap.add_argument("--no-compare", action="store_true", help="skip the secondary measurement of the other form")
+    ap.add_argument("--small-batches", default="1,8,32",
+                    help="token counts at which both forms run the layer's 14 products ('' to skip)")
     ap.add_argument("--tokens", type=int, default=0, help="override tokens per GPU (0 = the workload's)")
     ap.add_argument("--e2e-tokens", type=int, default=8)
     ap.add_argument("--no-e2e", action="store_true")
@@ -482,6 +484,12 @@ def main():
         other = {"form": "plain" if args.form == "batched" else "batched", "value": T / (o_ms / 1e3),
                  "ms_per_step": o_ms, "steps": 1, "warmup": 1}
 
+    small = None
+    if args.small_batches and wl.name == "layer" and rank == 0:
+        sizes = [int(x) for x in args.small_batches.split(",") if x]
+        small = measure_small_batches(phe, ctx, weights, mm, keys, inputs, outs,
+                                      [t for t in sizes if t <= out_tokens], stream, side)
+
     e2e = None
     if not args.no_e2e:
         e2e = measure_e2e(phe, ctx, weights, wl, mm, keys, inputs, args.e2e_tokens, stream)
@@ -533,6 +541,7 @@ def main():
                                "call_p50": calls.get("p50_ms"), "call_p99": calls.get("p99_ms"),
                                "call_tokens": bchunk if args.form == "batched" else chunk},
                 "other_form": other,
+                "small_batches": small,
                 "serving": serving,
                 "packed": packed,
                 "paper_table": paper_table,
@@ -660,6 +669,52 @@ def measure_serving(phe, ctx, weights, wl, inputs, keys, n_requests, rate, T_ava
                      "by the server's busy time (idle waits between arrivals included); ") +
                     "tokens/s are tokens of single-projection requests; layer_equiv divides (token,row) items by "
                     "the 44032 of a layer token"}
+
+
+def measure_small_batches(phe, ctx, weights, mm, keys, inputs, outs, sizes, stream, side, reps=20):
+    """Batched against plain at serving-size batches: the layer's 14 products
+    over T tokens as one autotuned plan replayed from a CUDA graph, or as 14
+    phe_matmul calls.  Device time per step over `reps` steps after 3 warm-up
+    steps, each form on its own stream; at these sizes the inputs sit in L2
+    for both forms."""
+    import torch
+    res = []
+    for T in sizes:
+        jobs = []
+        for n, (pi, name, d, rows, cols, L) in enumerate(mm):
+            A, B, _ = inputs[keys[(pi, d)][0]]
+            dirc = phe.PHE_FWD if d == "fwd" else phe.PHE_BWD
+            jobs.append((weights[pi], dirc, T, A[:T], B[:T], outs[n][0], outs[n][1]))
+        tune, _ = phe.phe_autotune(ctx, jobs, phe.PHE_OUT_SWITCHED, T, side)
+        plan = phe.phe_plan_create(ctx, jobs, phe.PHE_OUT_SWITCHED, tune)
+
+        def plain():
+            for (w, dirc, tn, A, B, om, ob) in jobs:
+                phe.phe_matmul(ctx, w, dirc, tn, A, B, om, ob, phe.PHE_OUT_SWITCHED, stream)
+
+        def batched():
+            phe.phe_plan_graph(plan, side)
+
+        r = {"tokens": T, "batched_tuning": list(tune)}
+        try:
+            for name, f, st in (("plain", plain, stream), ("batched", batched, side)):
+                for _ in range(3):
+                    f()
+                torch.cuda.synchronize()
+                a = torch.cuda.Event(enable_timing=True)
+                b = torch.cuda.Event(enable_timing=True)
+                a.record(st)
+                for _ in range(reps):
+                    f()
+                b.record(st)
+                torch.cuda.synchronize()
+                ms = a.elapsed_time(b) / reps
+                r[name] = {"ms_per_step": ms, "tokens_per_s": T / (ms / 1e3)}
+        finally:
+            phe.phe_plan_destroy(plan)
+        r["batched_speedup"] = r["plain"]["ms_per_step"] / r["batched"]["ms_per_step"]
+        res.append(r)
+    return res
 
 
 def measure_e2e(phe, ctx, weights, wl, mm, keys, inputs, tokens, stream):
