@@ -158,7 +158,9 @@ phe_status phe_expand_masks(phe_ctx* ctx, const uint64_t* d_seeds, uint32_t n, u
 
 /* Unfused ModulusSwitch (Sec. 3.2): out[i] = round(in[i] * 2^k / q) mod 2^k,
  * ties rounded up, for n words (device buffers).  Input words are reduced
- * mod q first.  Errors: PHE_EINVAL, PHE_ECUDA. */
+ * mod q first.  With an RNS modulus q = p1 p2 the words go through the same
+ * residue-form arithmetic as the fused epilogue: residues mod p1 and p2, the
+ * CRT digit, then a 32-bit quotient estimate.  Errors: PHE_EINVAL, PHE_ECUDA. */
 phe_status phe_modswitch(phe_ctx* ctx, const uint64_t* d_in, uint32_t* d_out, size_t n, void* stream);
 
 /* End-to-end form with HOST buffers: copies the inputs host->device, runs

@@ -480,10 +480,21 @@ __global__ void expand_masks_kernel(const u64* __restrict__ seeds, u32 n, u32 N,
   }
 }
 
+// Unfused switch of single words.  An RNS modulus takes the residue form of
+// the fused epilogue: residues, CRT digit, 32-bit quotient estimate.
 __global__ void modswitch_kernel(const u64* __restrict__ in, uint32_t* __restrict__ out, size_t n, RingConst rc,
-                                 RnsConst rk) {
-  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x)
-    out[i] = rk.p2k ? pow2_modswitch(reduce_word(in[i], rc), rk) : modswitch_word(reduce_word(in[i], rc), rc);
+                                 RnsConst rk, bool rns) {
+  for (size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (size_t)gridDim.x * blockDim.x) {
+    const u64 c = reduce_word(in[i], rc);
+    if (rk.p2k) {
+      out[i] = pow2_modswitch(c, rk);
+    } else if (rns) {
+      const uint2 r = to_residues(c, rk);
+      out[i] = rns_modswitch(r.x, crt_digit_lazy(r.x, r.y, rk), rk);
+    } else {
+      out[i] = modswitch_word(c, rc);
+    }
+  }
 }
 
 // --------------------------------------------------------------------------
@@ -679,7 +690,7 @@ cudaError_t launch_modswitch(const phe_ctx* c, const u64* in, uint32_t* out, siz
   size_t blocks = (n + 255) / 256;
   const size_t cap = (size_t)c->num_sms * 16;
   if (blocks > cap) blocks = cap;
-  modswitch_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, out, n, c->rc, c->rk);
+  modswitch_kernel<<<(unsigned)blocks, 256, 0, s>>>(in, out, n, c->rc, c->rk, c->rns && !c->pow2);
   return cudaGetLastError();
 }
 

@@ -50,3 +50,20 @@ def test_paper_table_is_the_papers_six_shapes():
     shapes = [shape for shape, _ in bench.PAPER_TABLE]
     assert shapes == [(768, 768), (3072, 768), (2048, 2048), (768, 3072), (8192, 2048), (2048, 8192)]
     assert all(t > 0 for _, t in bench.PAPER_TABLE)
+
+
+def test_kernel_source_hash_covers_only_the_kernel_regions():
+    # the traffic figure is tied to the text lwedot_kernel is built and
+    # launched from: edits elsewhere in phe_kernels.cu keep the hash, edits
+    # inside the kernel or the device header change it
+    csrc = os.path.join(bench.ROOT, "paper_2505_07329_b300", "csrc")
+    k = open(os.path.join(csrc, "phe_kernels.cu"), encoding="utf-8").read()
+    d = open(os.path.join(csrc, "phe_device.cuh"), encoding="utf-8").read()
+    h = bench.kernel_source_hash(k, d)
+    assert h == bench.kernel_source_hash()
+    assert bench.kernel_source_hash(k + "\n// trailing comment\n", d) == h
+    i = k.index("lwedot_kernel(const LweJobTable jt")
+    assert bench.kernel_source_hash(k[:i] + " " + k[i:], d) != h
+    j = k.index("static cudaError_t lwedot_impl")
+    assert bench.kernel_source_hash(k[:j] + k[j:].replace("grid_limit > 0", "grid_limit >= 1", 1), d) != h
+    assert bench.kernel_source_hash(k, d + "\n") != h

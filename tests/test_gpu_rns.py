@@ -135,3 +135,26 @@ def test_rns_plan_seeded_and_noalloc_paths(ctxs):
     for k in range(3):
         for f in range(2):
             assert torch.equal(res[0][k][f], res[1][0][f])
+
+
+@pytest.mark.parametrize("k", [32, 26, 7, 1])
+def test_rns_modswitch_near_ties(orc, ctxs, k):
+    # phe_modswitch on an RNS context runs the fused epilogue's residue-form
+    # switch; words whose c 2^k lies within a few q of (m + 1/2) q sit next to
+    # a rounding boundary, where a quotient estimate off by one would show
+    import torch
+    ctx = ctxs(1024, False, k)
+    rng = np.random.Generator(np.random.PCG64(500 + k))
+    cs = [0, 1, Q - 1, Q // 2, Q // 2 + 1, Q // 2 - 1, synth.RNS_P1, synth.RNS_P2, Q - synth.RNS_P1,
+          synth.RNS_P1 * (synth.RNS_P2 - 1)]
+    for m in rng.integers(0, 1 << k, 400, dtype=np.uint64):
+        base = ((2 * int(m) + 1) * Q) >> (k + 1)
+        cs += [(base + d) % Q for d in range(-3, 4)]
+    cs += [int(x) for x in rng.integers(0, Q, 4000, dtype=np.uint64)]
+    c = np.array(cs, dtype=np.uint64)
+    d_in = torch.from_numpy(c.view(np.int64).copy()).cuda()
+    d_out = torch.empty(c.shape[0], dtype=torch.int32, device="cuda")
+    phe.phe_modswitch(ctx, d_in, d_out, c.shape[0])
+    torch.cuda.synchronize()
+    got = d_out.cpu().numpy().view(np.uint32).astype(np.uint64)
+    assert np.array_equal(got, orc.modswitch(c, Q, k))
