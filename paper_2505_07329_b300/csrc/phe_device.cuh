@@ -173,17 +173,18 @@ __device__ __forceinline__ u64 from_residues(u32 c1, u32 c2, const RnsConst& k) 
 // mu = floor(2^(32+s2) / p2) in (2^32, 2^33) estimates it from below, off by
 // less than 2^s2/p2 + z/2^32 + 1 < 4.  The remainder Z - Qe p2 < 4 p2 < 2^32
 // is then exact in the low word and three comparisons finish the quotient.
+template <bool K32 = false>
 __device__ __forceinline__ u32 rns_modswitch(u32 c1, u32 h, const RnsConst& k) {
   const u32 s1 = __umulhi(k.b1p, c1);
   const u32 r1 = c1 * k.b1 - s1 * k.p1;  // [0, 2 p1)
   const u32 v = r1 + k.half1;           // [0, 2.5 p1)
   const u32 g = c1 * k.a1 + s1 + (u32)(v >= k.p1) + (u32)(v >= 2 * k.p1);
-  const u64 Z = ((u64)h << k.kbits) + g + k.half2;
+  const u64 Z = ((u64)h << (K32 ? 32 : k.kbits)) + g + k.half2;
   const u32 z = (u32)(Z >> k.s2);
   const u32 Qe = z + __umulhi(z, k.mu2);
   const u32 r = (u32)Z - Qe * k.p2;      // [0, 4 p2)
   const u32 t = (u32)(r >= k.p2) + (u32)(r >= 2 * k.p2) + (u32)(r >= 3 * k.p2);
-  return (Qe + t) & k.kmask;
+  return K32 ? Qe + t : (Qe + t) & k.kmask;
 }
 
 // Power-of-two q (RnsConst::p2k > 0).  Input word -> residues of its centred

@@ -52,7 +52,8 @@ struct NttJob {             // forward transform of T*L input blocks
 // kOutPackIn: masks switched to the gadget modulus B^ell (uint32, what
 // Decomp reads) and bodies raw mod q (uint64), the inputs of the packing.
 enum OutMode : int {
-  kOutSwitched = 0, kOutRaw = 1, kOutRing = 2, kOutPackIn = 3, kPow2 = 4 /* flag: q = 2^k via the RNS form */
+  kOutSwitched = 0, kOutRaw = 1, kOutRing = 2, kOutPackIn = 3, kPow2 = 4 /* flag: q = 2^k via the RNS form */,
+  kK32 = 8 /* flag: switched outputs at q' = 2^32, the shift and mask known at compile time */
 };
 
 // Kernel names for tracing; kKCall brackets a whole phe_matmul call.

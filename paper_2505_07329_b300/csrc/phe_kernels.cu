@@ -292,6 +292,8 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, lwedot_min_blocks<Shape<LOGN
                   const void* __restrict__ twcv) {
   constexpr int OUT = MODE & 3;                 // kOutSwitched, kOutRaw or kOutRing
   constexpr bool P2 = (MODE & kPow2) != 0;      // power-of-two q through the RNS modulus
+  constexpr bool K32 = (MODE & kK32) != 0;      // q' = 2^32 (RNS switched outputs)
+  static_assert(!K32 || (RNS && !P2 && OUT == kOutSwitched), "the 2^32 form is an RNS switched mode");
   static_assert(!(RNS && OUT == kOutRing), "client encryption runs in the 64-bit form");
   static_assert(RNS || !P2, "a power-of-two q runs in the RNS form");
   static_assert(!(P2 && OUT == kOutPackIn), "no packing for a power-of-two q");
@@ -406,7 +408,7 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, lwedot_min_blocks<Shape<LOGN
             } else if constexpr (RNS) {
               const u32 c1 = sub_if32(x[e].x, rk.p1);
               const u32 h = crt_digit_lazy(c1, x[e].y, rk);
-              if constexpr (SWM) reinterpret_cast<uint32_t*>(J.out)[o] = rns_modswitch(c1, h, rk);
+              if constexpr (SWM) reinterpret_cast<uint32_t*>(J.out)[o] = rns_modswitch<K32>(c1, h, rk);
               else reinterpret_cast<u64*>(J.out)[o] = (u64)c1 + (u64)rk.p1 * h;
             } else {
               const u64 c = reduce_4q(x[e], q, rc.q2);
@@ -620,6 +622,8 @@ cudaError_t launch_lwedot(const phe_ctx* c, const LweJobTable& jt, int mode, int
       return cudaErrorInvalidValue;
     }
     if (rns) {
+      if (mode == kOutSwitched && c->prm.log2_qout == 32)
+        return lwedot_impl<LOGN, kOutSwitched | kK32, true>(c, jt, grid_limit, s);
       if (mode == kOutSwitched) return lwedot_impl<LOGN, kOutSwitched, true>(c, jt, grid_limit, s);
       if (mode == kOutRaw) return lwedot_impl<LOGN, kOutRaw, true>(c, jt, grid_limit, s);
       return cudaErrorInvalidValue;
@@ -667,6 +671,7 @@ cudaError_t prepare_launches(const phe_ctx* c) {
     if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutRaw, false>, smem);
     if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutRing, false>, smem);
     if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutSwitched, true>, smem);
+    if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutSwitched | kK32, true>, smem);
     if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutRaw, true>, smem);
     if (e == cudaSuccess) e = set_smem(input_ntt_kernel<LOGN, true, true>, smem);
     if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutSwitched | kPow2, true>, smem);
