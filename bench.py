@@ -772,8 +772,10 @@ def measure_e2e(phe, ctx, weights, wl, mm, keys, inputs, tokens, stream):
     dt = time.perf_counter() - t0
     return {"value": tokens * steps / dt, "unit": "tokens/s", "h2d_bytes_per_step": h2d, "d2h_bytes_per_step": d2h,
             "tokens_per_step": tokens,
+            "host_link_GBps": (h2d + d2h) * steps / dt / 1e9,
             "note": "host-buffer C-ABI call; every LWE result word of the layer's 14 products returns to pinned "
-                    "host memory (unpacked outputs; `packed.e2e` has the path with Eq. (pack_rotate))"}
+                    "host memory (unpacked outputs; `packed.e2e` has the path with Eq. (pack_rotate)); "
+                    "host_link_GBps is the copied bytes over the whole step time, compute included"}
 
 
 def _negacyclic_small(a, s, mod):
