@@ -42,7 +42,7 @@ METRIC = "encrypted W·[x] tokens/s per Llama-1B layer; p50/p99 latency; % of ro
 # with ncu, and the algorithmic bytes of that launch.  Valid only for the
 # kernel sources the counters were taken on (kernel_source_hash) and the
 # tuning the captured run picked.
-TRAFFIC_KERNEL_HASH = "14910e0c46e94dc5"
+TRAFFIC_KERNEL_HASH = "96e09498048b3366"
 TRAFFIC_TUNING = (16, 0)
 TRAFFIC_BYTES_PER_LAUNCH = 97455.9e6
 TRAFFIC_ALG_BYTES_PER_LAUNCH = 95891.8e6
@@ -57,18 +57,28 @@ KERNEL_SOURCE_REGIONS = (
 )
 
 
+def _code_only(text: str) -> str:
+    """C++ source without comments and whitespace runs (the sources' string
+    literals hold no comment markers)."""
+    import re
+    text = re.sub(r"/\*.*?\*/", " ", text, flags=re.S)
+    text = re.sub(r"//[^\n]*", " ", text)
+    return " ".join(text.split())
+
+
 def kernel_source_hash(kernels_text=None, device_text=None) -> str:
+    """Hash of the code (comments and layout ignored) in the regions above."""
     import hashlib
     csrc = os.path.join(ROOT, "paper_2505_07329_b300", "csrc")
     if kernels_text is None:
         kernels_text = open(os.path.join(csrc, "phe_kernels.cu"), encoding="utf-8").read()
     if device_text is None:
         device_text = open(os.path.join(csrc, "phe_device.cuh"), encoding="utf-8").read()
-    parts = [hashlib.sha256(device_text.encode()).hexdigest()]
+    parts = [hashlib.sha256(_code_only(device_text).encode()).hexdigest()]
     for begin, end in KERNEL_SOURCE_REGIONS:
         i = kernels_text.index(begin)
         j = kernels_text.index(end, i)
-        parts.append(hashlib.sha256(kernels_text[i:j].encode()).hexdigest())
+        parts.append(hashlib.sha256(_code_only(kernels_text[i:j]).encode()).hexdigest())
     return hashlib.sha256((":".join(parts) + "\n").encode()).hexdigest()[:16]
 
 

@@ -173,6 +173,7 @@ __device__ __forceinline__ u64 from_residues(u32 c1, u32 c2, const RnsConst& k) 
 // mu = floor(2^(32+s2) / p2) in (2^32, 2^33) estimates it from below, off by
 // less than 2^s2/p2 + z/2^32 + 1 < 4.  The remainder Z - Qe p2 < 4 p2 < 2^32
 // is then exact in the low word and three comparisons finish the quotient.
+// K32: k = 32 known at compile time (no variable shift, no final mask).
 template <bool K32 = false>
 __device__ __forceinline__ u32 rns_modswitch(u32 c1, u32 h, const RnsConst& k) {
   const u32 s1 = __umulhi(k.b1p, c1);

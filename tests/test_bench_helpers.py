@@ -53,9 +53,9 @@ def test_paper_table_is_the_papers_six_shapes():
 
 
 def test_kernel_source_hash_covers_only_the_kernel_regions():
-    # the traffic figure is tied to the text lwedot_kernel is built and
-    # launched from: edits elsewhere in phe_kernels.cu keep the hash, edits
-    # inside the kernel or the device header change it
+    # the traffic figure is tied to the code lwedot_kernel is built and
+    # launched from: edits elsewhere in phe_kernels.cu keep the hash, code
+    # edits inside the kernel or the device header change it
     csrc = os.path.join(bench.ROOT, "paper_2505_07329_b300", "csrc")
     k = open(os.path.join(csrc, "phe_kernels.cu"), encoding="utf-8").read()
     d = open(os.path.join(csrc, "phe_device.cuh"), encoding="utf-8").read()
@@ -66,4 +66,6 @@ def test_kernel_source_hash_covers_only_the_kernel_regions():
     assert bench.kernel_source_hash(k[:i] + " " + k[i:], d) != h
     j = k.index("static cudaError_t lwedot_impl")
     assert bench.kernel_source_hash(k[:j] + k[j:].replace("grid_limit > 0", "grid_limit >= 1", 1), d) != h
-    assert bench.kernel_source_hash(k, d + "\n") != h
+    # comments and layout do not count; code in the device header does
+    assert bench.kernel_source_hash(k, d + "\n// a note\n/* another */\n") == h
+    assert bench.kernel_source_hash(k, d + "\nconstexpr int kUnused = 1;\n") != h
