@@ -63,7 +63,9 @@ def test_kernel_source_hash_covers_only_the_kernel_regions():
     assert h == bench.kernel_source_hash()
     assert bench.kernel_source_hash(k + "\n// trailing comment\n", d) == h
     i = k.index("lwedot_kernel(const LweJobTable jt")
-    assert bench.kernel_source_hash(k[:i] + " " + k[i:], d) != h
+    assert bench.kernel_source_hash(k[:i] + " " + k[i:], d) == h          # layout only
+    assert bench.kernel_source_hash(k[:i] + k[i:].replace("const u32 total = jt.prefix[jt.n];",
+                                                          "const u32 total = jt.prefix[jt.n] + 0;", 1), d) != h
     j = k.index("static cudaError_t lwedot_impl")
     assert bench.kernel_source_hash(k[:j] + k[j:].replace("grid_limit > 0", "grid_limit >= 1", 1), d) != h
     # comments and layout do not count; code in the device header does
