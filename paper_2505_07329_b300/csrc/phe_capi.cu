@@ -187,7 +187,7 @@ cudaError_t matmul_device(phe_ctx* c, const phe_weights::Dir& D, u32 T, const u6
     J.T = T;
     J.L = D.L;
     J.tok_chunk = phe::kDefaultTokChunk;
-    J.tiles = D.rows * ((T + J.tok_chunk - 1) / J.tok_chunk);
+    phe::set_lwe_tiles(J, c->logn);
     jt.prefix[0] = 0;
     jt.prefix[1] = J.tiles;
     Span sp(c, phe::kKLwedot, s);
@@ -737,7 +737,7 @@ phe_status phe_client_encrypt(phe_ctx* c, uint32_t T, uint32_t d, const uint64_t
     J.L = 1;
     J.tok_chunk = 16;
     J.msg_d = d;
-    J.tiles = (blocks + 15) / 16;
+    phe::set_lwe_tiles(J, c->logn);
     jt.prefix[1] = J.tiles;
     e = phe::launch_lwedot(c, jt, phe::kOutRing, 0, s, /*force64=*/true);
   }

@@ -34,6 +34,7 @@ struct LweJob {
   const int8_t* msg;        // client encryption only: x [T][msg_d]
   u64 delta, delta_p;       // client encryption only: delta and its Shoup quotient
   u32 rows, cols, T, L, tok_chunk, tiles, msg_d;
+  u32 row_group;             // rows per tile (set_lwe_tiles)
 };
 struct LweJobTable {
   u32 n;
@@ -184,6 +185,20 @@ cudaError_t launch_lwedot_packin(const phe_ctx* c, const LweJobTable& jt, const 
 cudaError_t launch_modswitch(const phe_ctx* c, const u64* in, u32* out, size_t n, cudaStream_t s);
 cudaError_t launch_expand_masks(const phe_ctx* c, const u64* seeds, u32 n, u64* masks, cudaStream_t s);
 int lwedot_threads(int logn);
+
+// Tiles of an lwedot job: (a group of row_group adjacent rows) x (a chunk of
+// tok_chunk tokens).  A block holds SLOTS = threads / (N/16) transforms; when
+// a chunk has fewer tokens than that, the idle slots take adjacent rows, so
+// one token per call still fills the block at N <= 2048.
+inline void set_lwe_tiles(LweJob& J, int logn) {
+  const u32 slots = (u32)lwedot_threads(logn) / ((1u << logn) / 16);
+  u32 c = J.tok_chunk < J.T ? J.tok_chunk : J.T;
+  if (c == 0) c = 1;
+  u32 cs = 1;  // tokens per slot round: the largest power of two <= min(c, slots)
+  while (cs * 2 <= c && cs * 2 <= slots) cs *= 2;
+  J.row_group = slots / cs;
+  J.tiles = ((J.rows + J.row_group - 1) / J.row_group) * ((J.T + J.tok_chunk - 1) / J.tok_chunk);
+}
 // Sets the dynamic shared-memory limits of the context's kernels (needed
 // before a launch is captured into a graph when a kernel exceeds 48 KB).
 cudaError_t prepare_launches(const phe_ctx* c);

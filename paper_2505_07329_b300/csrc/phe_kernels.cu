@@ -326,17 +326,22 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, lwedot_min_blocks<Shape<LOGN
     // The token chunks of one row are adjacent tiles: CTAs resident at the
     // same time share W_hat_j through L2, so a launch reads W_hat from HBM
     // about once however small the token chunk.
+    // A tile is a group of RG adjacent rows times a chunk of tokens; the
+    // block's slots take CS tokens of each of the RG rows per round.
     const u32 nch = (J.T + J.tok_chunk - 1) / J.tok_chunk;
-    const u32 row = local / nch;
+    const u32 RG = J.row_group ? J.row_group : 1;
+    const u32 CS = S::SLOTS / RG;
+    const u32 row = (local / nch) * RG + slot / CS;
+    const bool row_ok = row < J.rows;
     const u32 t0 = (local % nch) * J.tok_chunk;
     const u32 t1 = min(J.T, t0 + J.tok_chunk);
-    const Tw* wrow = reinterpret_cast<const Tw*>(J.what) + (size_t)row * J.L * N;
+    const Tw* wrow = reinterpret_cast<const Tw*>(J.what) + (size_t)(row_ok ? row : 0) * J.L * N;
     const bool planes = (J.cols % 4 == 0) && ((reinterpret_cast<uintptr_t>(J.bin) & 15) == 0);
-    const u32 iters = (t1 - t0 + S::SLOTS - 1) / S::SLOTS;
+    const u32 iters = (t1 - t0 + CS - 1) / CS;
 
     for (u32 it = 0; it < iters; ++it, ++seq) {
-      const u32 t = t0 + it * S::SLOTS + slot;
-      const bool active = t < t1;
+      const u32 t = t0 + it * CS + slot % CS;
+      const bool active = row_ok && t < t1;
       const int par = seq & 1;
       // the body first, while no transform words are live
       if constexpr (BODY) {

@@ -94,7 +94,7 @@ extern "C" phe_status phe_matmul_noalloc(phe_ctx* c, const phe_weights* w, int d
       J.T = T;
       J.L = D.L;
       J.tok_chunk = phe::kDefaultTokChunk;
-      J.tiles = D.rows * ((T + J.tok_chunk - 1) / J.tok_chunk);
+      phe::set_lwe_tiles(J, c->logn);
       jt.prefix[1] = J.tiles;
       e = phe::launch_lwedot(c, jt, flags == PHE_OUT_RAW ? phe::kOutRaw : phe::kOutSwitched, 0, s);
     }

@@ -542,7 +542,7 @@ cudaError_t matmul_packed_device(phe_ctx* c, const phe_weights::Dir& D, const ph
       J.T = tn;
       J.L = D.L;
       J.tok_chunk = phe::kDefaultTokChunk;
-      J.tiles = D.rows * ((tn + J.tok_chunk - 1) / J.tok_chunk);
+      phe::set_lwe_tiles(J, c->logn);
       jt.prefix[0] = 0;
       jt.prefix[1] = J.tiles;
       Span sp(c, phe::kKLwedot, s);

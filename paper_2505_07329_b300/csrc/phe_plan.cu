@@ -195,7 +195,7 @@ phe_status phe_plan_create(phe_ctx* c, const phe_job* jobs, uint32_t n_jobs, uin
     J.T = j.T;
     J.L = D.L;
     J.tok_chunk = tn.tok_chunk;
-    J.tiles = D.rows * ((j.T + tn.tok_chunk - 1) / tn.tok_chunk);
+    phe::set_lwe_tiles(J, c->logn);
     cur.prefix[cur.n + 1] = cur.prefix[cur.n] + J.tiles;
     cur.n++;
     p->modmuls += (u64)j.T * D.rows * ((u64)D.L * N + (u64)(N / 2) * logn);

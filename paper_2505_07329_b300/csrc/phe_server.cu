@@ -159,7 +159,7 @@ cudaError_t launch_iteration(phe_server* s, Iteration& it) {
     J.T = j.tn;
     J.L = D.L;
     J.tok_chunk = s->cfg.tok_chunk;
-    J.tiles = D.rows * ((j.tn + J.tok_chunk - 1) / J.tok_chunk);
+    phe::set_lwe_tiles(J, c->logn);
     t.prefix[t.n + 1] = t.prefix[t.n] + J.tiles;
     if (++t.n == phe::kMaxJobs) tables.emplace_back();
   }
