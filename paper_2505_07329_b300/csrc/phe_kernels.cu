@@ -265,17 +265,20 @@ __device__ __forceinline__ void body_partial_planes(const LweJob& J, u32 row, u3
   acc[2] = 0;
 }
 
-// The body mod q from block-reduced parts: S0 + S1 2^30 + S2 2^60 (word
-// split), or S0 + S1 2^32 (byte planes).
+// The body mod q from block-reduced parts: S0 + S1 2^32 (byte planes).  With
+// rows of at most 2^14 int8 weights, |S0| < 2^14 2^7 2^32 = 2^53 and |S1| <
+// 2^14 2^7 2^28, both below q (> 2^53 for these moduli), so a negative part
+// is q minus its magnitude and no division is needed.
 __device__ __forceinline__ u64 body_combine_planes(const long long (&S)[3], const RingConst& rc) {
   const u64 q = rc.q;
-  const u64 v0 = (S[0] < 0) ? q - (u64)(-S[0]) % q : (u64)S[0] % q;
-  const u64 v1 = (S[1] < 0) ? q - (u64)(-S[1]) % q : (u64)S[1] % q;
+  const u64 v0 = (S[0] < 0) ? q - (u64)(-S[0]) : (u64)S[0];
+  const u64 v1 = (S[1] < 0) ? q - (u64)(-S[1]) : (u64)S[1];
   const u64 h = reduce_2q(mul_shoup(v1, rc.c32, rc.c32p, q), q);
-  return reduce_2q(reduce_2q(v0, q) + h, q);
+  return reduce_2q(v0 + h, q);
 }
 
-// The body mod q from the block-reduced partial sums S0 + S1 2^30 + S2 2^60.
+// The body mod q from the block-reduced partial sums S0 + S1 2^30 + S2 2^60
+// (word split).
 __device__ __forceinline__ u64 body_combine(const long long (&S)[3], const RingConst& rc) {
   const u64 q = rc.q;
   u64 v[3];
