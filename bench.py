@@ -312,7 +312,8 @@ def main():
         return run_reference(args, wl, rank)
 
     import torch
-    from paper_2505_07329_b300 import phe
+    from paper_2505_07329_b300 import build, phe
+    build.build()  # a no-op unless a source is newer than libphe.so
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
