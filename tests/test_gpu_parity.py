@@ -88,6 +88,25 @@ def test_every_ring_degree(orc, ctxs, N):
         phe.phe_weights_free(w)
 
 
+@pytest.mark.parametrize("N", [256, 1024, 2048])
+@pytest.mark.parametrize("T", [1, 2, 3])
+def test_fewer_tokens_than_transform_slots(orc, ctxs, N, T):
+    # At N <= 2048 a block holds 4096/N transform slots; with fewer tokens the
+    # idle slots take adjacent rows.  d_out = 21 leaves a ragged last row
+    # group, and T = 3 a ragged last token round.
+    d_in, d_out = N // 2 + 3, 21
+    L = synth.blocks(d_in, N)
+    W = synth.weights(d_out, d_in, seed=N + T)
+    A = synth.uniform_words((T, L, N), Q, 10 * N + T)
+    B = synth.uniform_words((T, L, N), Q, 10 * N + T + 1)
+    ctx = ctxs(N)
+    w = phe.phe_weights_upload(ctx, W, phe.PHE_DIR_FWD_BIT)
+    try:
+        _check_both_modes(orc, ctx, w, phe.PHE_FWD, W, A, B)
+    finally:
+        phe.phe_weights_free(w)
+
+
 @pytest.mark.parametrize("d_in,d_out,T", [(300, 37, 19), (256, 129, 17), (700, 5, 33)])
 def test_ragged_forward_and_backward(orc, ctxs, d_in, d_out, T):
     # Shapes that leave partial row tiles (128), token chunks (16) and blocks.
