@@ -407,15 +407,18 @@ __device__ __forceinline__ void ct_pass(typename R::Word (&x)[16], int p, const 
 }
 
 // Move the 16 words of every thread from pass A's positions to pass B's.
-// Two barriers: the buffer is reused by the next exchange.
-template <int LOGN, int PA, int PB, class W>
+// The barrier after the reads guards the buffer against the next writer.  An
+// exchange followed by the exchange out of pass B needs none: that one writes
+// exactly the pass-B positions, and each is rewritten by the thread that read
+// it (TRAIL = false).
+template <int LOGN, int PA, int PB, bool TRAIL = true, class W>
 __device__ __forceinline__ void exchange(W (&x)[16], int p, W* __restrict__ buf) {
 #pragma unroll
   for (int e = 0; e < 16; ++e) buf[pad_idx(pass_pos<LOGN, PA>(p, e))] = x[e];
   __syncthreads();
 #pragma unroll
   for (int e = 0; e < 16; ++e) x[e] = buf[pad_idx(pass_pos<LOGN, PB>(p, e))];
-  __syncthreads();
+  if constexpr (TRAIL) __syncthreads();
 }
 
 // Full inverse transform (no N^-1 scaling): bit-reversed in (pass-0 layout),
@@ -424,17 +427,18 @@ __device__ __forceinline__ void exchange(W (&x)[16], int p, W* __restrict__ buf)
 template <int LOGN, class R>
 __device__ __forceinline__ void intt_regs(typename R::Word (&x)[16], int p, typename R::Word* buf,
                                           const typename R::Tw* tw0, const typename R::Tw* twc, const R& ring) {
+  constexpr int NP = Shape<LOGN>::NPASS;
   gs_pass<LOGN, 0>(x, p, tw0, twc, ring);
-  if constexpr (Shape<LOGN>::NPASS > 1) {
-    exchange<LOGN, 0, 1>(x, p, buf);
+  if constexpr (NP > 1) {
+    exchange<LOGN, 0, 1, (NP == 2)>(x, p, buf);
     gs_pass<LOGN, 1>(x, p, tw0, twc, ring);
   }
-  if constexpr (Shape<LOGN>::NPASS > 2) {
-    exchange<LOGN, 1, 2>(x, p, buf);
+  if constexpr (NP > 2) {
+    exchange<LOGN, 1, 2, (NP == 3)>(x, p, buf);
     gs_pass<LOGN, 2>(x, p, tw0, twc, ring);
   }
-  if constexpr (Shape<LOGN>::NPASS > 3) {
-    exchange<LOGN, 2, 3>(x, p, buf);
+  if constexpr (NP > 3) {
+    exchange<LOGN, 2, 3, true>(x, p, buf);
     gs_pass<LOGN, 3>(x, p, tw0, twc, ring);
   }
 }
@@ -447,15 +451,15 @@ __device__ __forceinline__ void ntt_regs(typename R::Word (&x)[16], int p, typen
   constexpr int NP = Shape<LOGN>::NPASS;
   if constexpr (NP > 3) {
     ct_pass<LOGN, 3>(x, p, tw0, twc, ring);
-    exchange<LOGN, 3, 2>(x, p, buf);
+    exchange<LOGN, 3, 2, false>(x, p, buf);
   }
   if constexpr (NP > 2) {
     ct_pass<LOGN, 2>(x, p, tw0, twc, ring);
-    exchange<LOGN, 2, 1>(x, p, buf);
+    exchange<LOGN, 2, 1, false>(x, p, buf);
   }
   if constexpr (NP > 1) {
     ct_pass<LOGN, 1>(x, p, tw0, twc, ring);
-    exchange<LOGN, 1, 0>(x, p, buf);
+    exchange<LOGN, 1, 0, true>(x, p, buf);
   }
   ct_pass<LOGN, 0>(x, p, tw0, twc, ring);
 }
