@@ -524,6 +524,7 @@ def main():
     paper_table = None
     if args.paper_table and rank == 0:
         paper_table = measure_paper_table(phe, dev)
+        paper_table["wire"] = measure_wire_paper_set(phe, dev)
 
     packed = None
     if args.packed_tokens > 0:
@@ -910,6 +911,7 @@ def measure_packed(phe, ctx, weights, wl, mm, keys, inputs, S, q, tokens, stream
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
         h2d = sum(2 * tokens * L * N * 8 for (_, _, _, _, _, L) in mm)
+        wire = measure_wire(phe, ctx, N, weights[mm[0][0]], k, mm[0], tokens, stream, dev)
     finally:
         phe.phe_ksk_free(k)
     return {"value": tokens * steps / (ms / 1e3), "unit": "tokens/s", "tokens": tokens,
@@ -919,7 +921,56 @@ def measure_packed(phe, ctx, weights, wl, mm, keys, inputs, S, q, tokens, stream
             "out_bytes_per_token": out_bytes, "unpacked_out_bytes_per_token": out_bytes_per_token(wl),
             "sanity_decrypt": f"{ok}/{y.shape[0]} coefficients, {zero}/{N - y.shape[0]} unused zero",
             "e2e": {"value": tokens * steps / dt, "unit": "tokens/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": out_bytes * tokens, "tokens_per_step": tokens}}
+                    "d2h_bytes_per_step": out_bytes * tokens, "tokens_per_step": tokens},
+            "wire": wire}
+
+
+def measure_wire(phe, ctx, N, w, k, prod, tokens, stream, dev, reps=3):
+    """phe_matmul_wire, device-timed: `tokens` tokens of one product from
+    input records (8-byte seed + bodies at ceil(log2 q) bits) to output
+    records: LWE records at log2_qout bits, or with the key k one packed RLWE
+    record per group of N rows.  Every bit pattern of an input record is a
+    valid record, so the inputs are random words."""
+    import torch
+    pi, name, d, rows, cols, L = prod
+    sizes = phe.phe_wire_sizes(ctx)
+    g = torch.Generator(device=dev)
+    g.manual_seed(synth.SEED_X + 17)
+    rec = torch.randint(-(1 << 31), 1 << 31, (tokens * L * sizes["input"] // 4,), device=dev, generator=g,
+                        dtype=torch.int64).to(torch.int32)
+    per_tok = ((rows + N - 1) // N) * sizes["rlwe"] if k is not None else rows * sizes["lwe"]
+    out = torch.empty(((tokens * per_tok + 3) // 4,), dtype=torch.int32, device=dev)
+    direction = phe.PHE_FWD if d == "fwd" else phe.PHE_BWD
+    phe.phe_matmul_wire(ctx, w, k, direction, tokens, rec, out, stream)
+    torch.cuda.synchronize()
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    a.record(stream)
+    for _ in range(reps):
+        phe.phe_matmul_wire(ctx, w, k, direction, tokens, rec, out, stream)
+    b.record(stream)
+    torch.cuda.synchronize()
+    ms = a.elapsed_time(b) / reps
+    return {"value": tokens / (ms / 1e3), "unit": "tokens/s", "tokens": tokens, "product": f"{name} {d}",
+            "records": "packed RLWE" if k is not None else "LWE",
+            "in_bytes_per_token": L * sizes["input"], "out_bytes_per_token": per_tok}
+
+
+def measure_wire_paper_set(phe, dev, tokens=64):
+    """phe_matmul_wire at the paper's parameter set (N = 2048, q = 2^39 ->
+    q_out = 2^26) on a 2048->2048 forward product: 9992-byte input records in,
+    LWE records out (this modulus has no key switching here)."""
+    import torch
+    ctx = phe.phe_ctx_create(2048, 1 << 39, 26, dev.index or 0, rns=(synth.RNS_P1, synth.RNS_P2))
+    try:
+        w = phe.phe_weights_upload(ctx, synth.weights(2048, 2048, seed=synth.SEED_W + 4096), phe.PHE_DIR_FWD_BIT)
+        try:
+            return measure_wire(phe, ctx, 2048, w, None, (0, "2048->2048", "fwd", 2048, 2048, 1), tokens,
+                                torch.cuda.current_stream(dev), dev)
+        finally:
+            phe.phe_weights_free(w)
+    finally:
+        phe.phe_ctx_destroy(ctx)
 
 
 # Per-token latencies of W.[x] printed in Table fhe_matmul_timing (Sec. 6.3)
