@@ -340,9 +340,18 @@ def main():
 
     # weights (public, int8) for every projection, both directions
     weights = []
-    for pi, (name, d_in, d_out) in enumerate(wl.projections):
-        W = synth.weights(d_out, d_in, seed=synth.SEED_W + pi)
+    host_W = [synth.weights(d_out, d_in, seed=synth.SEED_W + pi) for pi, (name, d_in, d_out) in
+              enumerate(wl.projections)]
+    torch.cuda.synchronize()
+    t_up = time.perf_counter()
+    for W in host_W:
         weights.append(phe.phe_weights_upload(ctx, W, phe.PHE_DIR_FWD_BIT | phe.PHE_DIR_BWD_BIT))
+    torch.cuda.synchronize()
+    upload = {"seconds": time.perf_counter() - t_up, "int8_bytes": int(sum(W.size for W in host_W)),
+              "device_bytes": int(sum(phe.phe_weights_device_bytes(w) for w in weights)),
+              "note": "one-time: both directions' int8 rows and N^-1 NTT(w_hat) with Shoup quotients, "
+                      "host int8 in, device synchronized after the last upload"}
+    del host_W
 
     # encrypted inputs: A uniform mod q, S ternary, E rounded Gaussian, x int8
     S = torch.randint(-1, 2, (N,), device=dev, generator=gen, dtype=torch.int8)
@@ -570,6 +579,7 @@ def main():
                                "call_tokens": bchunk if args.form == "batched" else chunk},
                 "other_form": other,
                 "small_batches": small,
+                "weights_upload": upload,
                 "serving": serving,
                 "packed": packed,
                 "paper_table": paper_table,
