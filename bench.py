@@ -255,7 +255,18 @@ def oracle_tokens_per_s(wl, seconds: float):
     sec_per_token = sum(rows * spent[(name, d)] / count[(name, d)] for (_, name, d, rows, _, _) in mm)
     elapsed = time.perf_counter() - t_start
     done = sum(count.values())
+    # one product per call: the oracle's OpenMP loop then runs on one core
+    one = 0.0
+    for (pi, name, d, rows, cols, L) in mm:
+        W = synth.weights(64, cols, seed=pi)
+        A = synth.uniform_words((1, L, N), q, 7 * pi)
+        B = synth.uniform_words((1, L, N), q, 7 * pi + 1)
+        t0 = time.perf_counter()
+        for j in range(3):
+            oracle.lwedot_pairs(W, A, B, np.array([[0, j]], dtype=np.int64), q, method=1)
+        one += rows * (time.perf_counter() - t0) / 3
     return {"value": 1.0 / sec_per_token, "unit": "tokens/s", "cores": threads, "kind": "oracle",
+            "single_core_value": 1.0 / one,
             "sample": f"{done} (token,row) products, {rounds} rounds over all {len(mm)} projection/direction "
                       f"shapes, oracle NTT path on {threads} host threads, {elapsed:.1f} s wall; per-shape "
                       f"mean time x rows, summed over the {per_token_items} products of one token; "
