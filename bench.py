@@ -265,8 +265,14 @@ def oracle_tokens_per_s(wl, seconds: float):
         for j in range(3):
             oracle.lwedot_pairs(W, A, B, np.array([[0, j]], dtype=np.int64), q, method=1)
         one += rows * (time.perf_counter() - t0) / 3
+    cpu_model = None
+    try:
+        with open("/proc/cpuinfo") as f:
+            cpu_model = next((ln.split(":", 1)[1].strip() for ln in f if ln.startswith("model name")), None)
+    except OSError:
+        pass
     return {"value": 1.0 / sec_per_token, "unit": "tokens/s", "cores": threads, "kind": "oracle",
-            "single_core_value": 1.0 / one,
+            "single_core_value": 1.0 / one, "host_cpu": cpu_model, "host_logical_cpus": os.cpu_count(),
             "sample": f"{done} (token,row) products, {rounds} rounds over all {len(mm)} projection/direction "
                       f"shapes, oracle NTT path on {threads} host threads, {elapsed:.1f} s wall; per-shape "
                       f"mean time x rows, summed over the {per_token_items} products of one token; "
