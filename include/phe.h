@@ -359,8 +359,14 @@ typedef struct phe_ksk phe_ksk;
  *               words mod q (larger words are reduced); caller keeps them.
  *   n           LWE dimension; must equal N.
  *   base_log, ell  1 <= ell <= 4, 1 <= base_log <= 30, base_log*ell <= 32.
- * Synchronous.  Errors: PHE_EINVAL (shape or parameters), PHE_ENOMEM,
- * PHE_ECUDA. */
+ * With q = 2^K (computed through p1 p2) the contraction has no NTT mod q, so
+ * it runs exactly over the integers through p1 p2.  The centred key is split
+ * into S balanced slices of b bits, KSK = sum_s 2^(b s) KSK_s, with b the
+ * largest width such that n*ell*N*(B/2)*2^(b-1) < p1 p2 / 2 and
+ * S = ceil((K+1)/b) <= 8.  The device copy is S times larger, and the
+ * contraction runs once per slice.
+ * Synchronous.  Errors: PHE_EINVAL (shape or parameters), PHE_EUNSUPPORTED
+ * (q = 2^K with no exact slice width), PHE_ENOMEM, PHE_ECUDA. */
 phe_status phe_ksk_upload(phe_ctx* ctx, const uint64_t* h_ka, const uint64_t* h_kb, uint32_t n, uint32_t base_log,
                           uint32_t ell, phe_ksk** out);
 void phe_ksk_free(phe_ksk* k);

@@ -299,7 +299,6 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, lwedot_min_blocks<Shape<LOGN
   static_assert(!K32 || (RNS && !P2 && OUT == kOutSwitched), "the 2^32 form is an RNS switched mode");
   static_assert(!(RNS && OUT == kOutRing), "client encryption runs in the 64-bit form");
   static_assert(RNS || !P2, "a power-of-two q runs in the RNS form");
-  static_assert(!(P2 && OUT == kOutPackIn), "no packing for a power-of-two q");
   using S = Shape<LOGN>;
   using R = RingOf<RNS>;
   using W = typename R::Word;
@@ -651,7 +650,12 @@ cudaError_t launch_lwedot_packin(const phe_ctx* c, const LweJobTable& jt, const 
     constexpr int LOGN = decltype(lg)::value;
     using S = Shape<LOGN>;
     const size_t smem = (size_t)S::SLOTS * S::PADN * sizeof(u64);
-    if (c->rns) {
+    if (c->rns && c->pow2) {
+      cudaError_t e = set_smem(lwedot_kernel<LOGN, kOutPackIn | kPow2, true>, smem);
+      if (e != cudaSuccess) return e;
+      lwedot_kernel<LOGN, kOutPackIn | kPow2, true><<<total, S::TPB, smem, s>>>(jt, rcK, rkK, tw0_of(c, true, true),
+                                                                               twc_of(c, true, true));
+    } else if (c->rns) {
       cudaError_t e = set_smem(lwedot_kernel<LOGN, kOutPackIn, true>, smem);
       if (e != cudaSuccess) return e;
       lwedot_kernel<LOGN, kOutPackIn, true><<<total, S::TPB, smem, s>>>(jt, rcK, rkK, tw0_of(c, true, true),

@@ -16,6 +16,7 @@
 //   pack_finish_kernel     inverse NTT of A_hat and B_hat, + b_j X^j, switch
 //   ksk_finish_kernel      upload: NTT(KSK) -> -N^-1 NTT(KSK) with quotients
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdio>
 #include <new>
@@ -34,8 +35,12 @@ struct phe_ksk {
   uint32_t n = 0, base_log = 0, ell = 0;
   phe::RingConst rcK{};  // the context's constants with the switch target 2^(base_log*ell)
   phe::RnsConst rkK{};
-  void* khat = nullptr;  // [n*ell][2][N] entries of 16 bytes (A then B), A_hat slot order
+  void* khat = nullptr;  // [slices][n*ell][2][N] entries of 16 bytes (A then B), A_hat slot order
   uint64_t bytes = 0;
+  // q = 2^K: the centred key is split into `slices` signed pieces of
+  // slice_bits bits, KSK = sum_s 2^(slice_bits s) KSK_s, each small enough
+  // that its contraction stays below (p1 p2)/2 and is exact through p1 p2.
+  uint32_t slices = 1, slice_bits = 0;
 };
 
 namespace phe {
@@ -74,7 +79,7 @@ __device__ __forceinline__ void signed_digits(u32 v, u32 base_log, int (&d)[ELL]
 template <int ELL, bool SWITCHED>
 __global__ void __launch_bounds__(256)
     pack_decompose_kernel(const void* __restrict__ maskv, u32 rows, u32 N, u32 G, u32 u_base, u32 base_log,
-                          RingConst rcK, int32_t* __restrict__ D) {
+                          RingConst rcK, RnsConst rkK, int32_t* __restrict__ D) {
   __shared__ int tile[ELL][64][33];
   const u32 u = blockIdx.z;  // unit within the chunk; D holds the chunk's units
   const u32 t = (u_base + u) / G, g = (u_base + u) % G;
@@ -94,8 +99,13 @@ __global__ void __launch_bounds__(256)
       } else {
         const ulonglong2 v =
             *reinterpret_cast<const ulonglong2*>(static_cast<const u64*>(maskv) + first + (size_t)k * N + 2 * tx);
-        v0 = modswitch_word(v.x, rcK);
-        v1 = modswitch_word(v.y, rcK);
+        if (rkK.p2k) {  // q = 2^K: a rounding shift
+          v0 = pow2_modswitch(v.x & (rcK.q - 1), rkK);
+          v1 = pow2_modswitch(v.y & (rcK.q - 1), rkK);
+        } else {
+          v0 = modswitch_word(v.x, rcK);
+          v1 = modswitch_word(v.y, rcK);
+        }
       }
       signed_digits<ELL>(v0, base_log, d0);
       signed_digits<ELL>(v1, base_log, d1);
@@ -359,6 +369,75 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB)
   }
 }
 
+// q = 2^K (the key in slices): per slice sl, the segments' partial sums are
+// inverse-transformed and the CRT value (exact, below (p1 p2)/2 in magnitude)
+// is lifted centred; the slices combine as sum_sl 2^(bits sl) value mod 2^64,
+// which is exact mod 2^K.  Then b_{gN+m} joins coefficient m of B and the
+// words are switched to 2^k (or left mod 2^K).  Block b = u*2 + c as above;
+// slice sl's partial sums start at Phat + sl * slice_stride.
+template <int LOGN, int MODE>
+__global__ void __launch_bounds__(Shape<LOGN>::TPB)
+    pack_finish_pow2_kernel(const u64* __restrict__ Phat, u32 nseg, u32 slices, u32 bits, size_t slice_stride,
+                            const u64* __restrict__ body, u32 rows, u32 G, u32 u_base, u32 units,
+                            void* __restrict__ out_a, void* __restrict__ out_b, RnsConst rk,
+                            const void* __restrict__ tw0v, const void* __restrict__ twcv) {
+  using S = Shape<LOGN>;
+  using W = Ring2x32::Word;
+  using Tw = Ring2x32::Tw;
+  constexpr int N = S::N;
+  constexpr int P = S::P;
+  constexpr int NP = S::NPASS;
+  extern __shared__ u64 smem[];
+  const int slot = threadIdx.x / P, p = threadIdx.x % P;
+  W* buf = reinterpret_cast<W*>(smem + slot * S::PADN);
+  const u32 b = blockIdx.x * S::SLOTS + slot;
+  const bool active = b < 2 * units;
+  u64 acc[16];
+#pragma unroll
+  for (int e = 0; e < 16; ++e) acc[e] = 0;
+  for (u32 sl = 0; sl < slices; ++sl) {
+    W x[16];
+#pragma unroll
+    for (int r = 0; r < 16; ++r) x[r] = make_uint2(0u, 0u);
+    if (active) {
+      for (u32 g = 0; g < nseg; ++g) {
+        const uint4* ap = reinterpret_cast<const uint4*>(Phat + sl * slice_stride + ((size_t)g * units * 2 + b) * N);
+#pragma unroll
+        for (int r = 0; r < 16; r += 2) {
+          const uint4 v = ap[(r >> 1) * P + p];
+          x[r] = make_uint2(sub_if32(x[r].x + v.x, rk.p1), sub_if32(x[r].y + v.y, rk.p2));
+          x[r + 1] = make_uint2(sub_if32(x[r + 1].x + v.z, rk.p1), sub_if32(x[r + 1].y + v.w, rk.p2));
+        }
+      }
+    }
+    intt_regs<LOGN>(x, p, buf, reinterpret_cast<const Tw*>(tw0v), reinterpret_cast<const Tw*>(twcv),
+                    Ring2x32{rk.p1, rk.p2});
+    const u32 sh = bits * sl;
+#pragma unroll
+    for (int e = 0; e < 16; ++e) {
+      const u32 c1 = sub_if32(x[e].x, rk.p1);
+      const u64 v = pow2_from_crt(c1, crt_digit_lazy(c1, x[e].y, rk), rk);  // centred value mod 2^K
+      acc[e] += (sh < 64) ? (v << sh) : 0ull;
+    }
+  }
+  if (!active) return;
+  const u32 u = u_base + b / 2, comp = b % 2;
+  const u32 t = u / G, g = u % G;
+  void* out = comp ? out_b : out_a;
+  const u64 qmask = (1ull << rk.p2k) - 1;
+#pragma unroll
+  for (int e = 0; e < 16; ++e) {
+    const u32 pos = (u32)pass_pos<LOGN, NP - 1>(p, e);
+    const u32 row = g * N + pos;
+    u64 v = acc[e];
+    if (comp == 1 && row < rows) v += body[(size_t)t * rows + row];
+    v &= qmask;
+    const size_t o = (size_t)u * N + pos;
+    if constexpr (MODE == kOutSwitched) reinterpret_cast<u32*>(out)[o] = pow2_modswitch(v, rk);
+    else reinterpret_cast<u64*>(out)[o] = v;
+  }
+}
+
 }  // namespace phe
 
 // --------------------------------------------------------------------------
@@ -382,9 +461,9 @@ cudaError_t launch_decompose(const phe_ctx* c, const phe_ksk* k, const void* mas
   const dim3 grid(N / 64, N / 32, cu), block(32, 8);
 #define PHE_DECOMP(E)                                                                                       \
   (switched ? phe::pack_decompose_kernel<E, true><<<grid, block, 0, s>>>(mask, rows, N, G, u_base, k->base_log, \
-                                                                          k->rcK, D)                        \
+                                                                          k->rcK, k->rkK, D)                        \
             : phe::pack_decompose_kernel<E, false><<<grid, block, 0, s>>>(mask, rows, N, G, u_base, k->base_log, \
-                                                                           k->rcK, D))
+                                                                           k->rcK, k->rkK, D))
   switch (k->ell) {
     case 1: PHE_DECOMP(1); break;
     case 2: PHE_DECOMP(2); break;
@@ -405,15 +484,16 @@ u32 mac_segments(const phe_ctx* c, const phe_ksk* k, u32 cu) {
 }
 
 cudaError_t launch_mac(const phe_ctx* c, const phe_ksk* k, const u64* Dhat, u32 cu, u32 nseg, u64* Phat,
-                       cudaStream_t s) {
+                       cudaStream_t s, u32 slice = 0) {
   const u32 N = c->prm.N, nr = k->n * k->ell;
+  const void* khat = static_cast<const char*>(k->khat) + (size_t)slice * nr * 2 * N * 16;
   const u32 rseg = (nr + nseg - 1) / nseg;
   const dim3 grid(N / 256, nseg, (cu + kMacUnits - 1) / kMacUnits);
   auto kern = c->rns ? phe::pack_mac_kernel<true, kMacUnits, kMacStages>
                      : phe::pack_mac_kernel<false, kMacUnits, kMacStages>;
   cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kMacSmem);
   if (e != cudaSuccess) return e;
-  kern<<<grid, 256, kMacSmem, s>>>(Dhat, k->khat, nr, rseg, N, cu, Phat, c->rc, c->rk);
+  kern<<<grid, 256, kMacSmem, s>>>(Dhat, khat, nr, rseg, N, cu, Phat, c->rc, c->rk);
   return cudaGetLastError();
 }
 
@@ -431,6 +511,22 @@ cudaError_t finish_one(const phe_ctx* c, const u64* Phat, u32 nseg, const u64* b
   const u32 blocks = (2 * cu + S::SLOTS - 1) / S::SLOTS;
   kern<<<blocks, S::TPB, smem, s>>>(Phat, nseg, body, rows, G, u_base, cu, oa, ob, c->rc, c->rk, tab.inv_0,
                                     tab.inv_c);
+  return cudaGetLastError();
+}
+
+template <int LOGN, int MODE>
+cudaError_t finish_pow2(const phe_ctx* c, const phe_ksk* k, const u64* Phat, u32 nseg, size_t slice_stride,
+                        const u64* body, u32 rows, u32 G, u32 u_base, u32 cu, void* oa, void* ob, cudaStream_t s) {
+  using S = phe::Shape<LOGN>;
+  const size_t smem = phe::lwedot_smem(LOGN);
+  auto kern = phe::pack_finish_pow2_kernel<LOGN, MODE>;
+  if (smem > 48 * 1024) {
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return e;
+  }
+  const u32 blocks = (2 * cu + S::SLOTS - 1) / S::SLOTS;
+  kern<<<blocks, S::TPB, smem, s>>>(Phat, nseg, k->slices, k->slice_bits, slice_stride, body, rows, G, u_base, cu,
+                                    oa, ob, c->rk, c->tab32.inv_0, c->tab32.inv_c);
   return cudaGetLastError();
 }
 
@@ -458,6 +554,25 @@ cudaError_t launch_finish(const phe_ctx* c, int mode, const u64* Phat, u32 nseg,
   }
 }
 
+cudaError_t launch_finish_pow2(const phe_ctx* c, const phe_ksk* k, int mode, const u64* Phat, u32 nseg,
+                               size_t slice_stride, const u64* body, u32 rows, u32 G, u32 u_base, u32 cu, void* oa,
+                               void* ob, cudaStream_t s) {
+#define PHE_FIN2(L)                                                                                         \
+  return mode == phe::kOutRaw                                                                              \
+             ? finish_pow2<L, phe::kOutRaw>(c, k, Phat, nseg, slice_stride, body, rows, G, u_base, cu, oa, ob, s) \
+             : finish_pow2<L, phe::kOutSwitched>(c, k, Phat, nseg, slice_stride, body, rows, G, u_base, cu, oa, ob, s)
+  switch (c->logn) {
+    case 8: PHE_FIN2(8);
+    case 9: PHE_FIN2(9);
+    case 10: PHE_FIN2(10);
+    case 11: PHE_FIN2(11);
+    case 12: PHE_FIN2(12);
+    case 13: PHE_FIN2(13);
+    default: return cudaErrorInvalidValue;
+  }
+#undef PHE_FIN2
+}
+
 // The packing of T x rows LWE ciphertexts on `s`, in chunks of units.
 cudaError_t pack_device(phe_ctx* c, const phe_ksk* k, u32 T, u32 rows, const void* mask, bool switched,
                         const u64* body, void* oa, void* ob, int mode, cudaStream_t s) {
@@ -474,7 +589,7 @@ cudaError_t pack_device(phe_ctx* c, const phe_ksk* k, u32 T, u32 rows, const voi
   if (e != cudaSuccess) return e;
   int32_t* D = reinterpret_cast<int32_t*>(Dhat + (size_t)per * nr * N);
   const u32 nseg_max = mac_segments(c, k, 1);  // the smallest chunk needs the most segments
-  e = phe::ctx_malloc_async(c, &Phat, (size_t)nseg_max * per * 2 * N * sizeof(u64), s);
+  e = phe::ctx_malloc_async(c, &Phat, (size_t)k->slices * nseg_max * per * 2 * N * sizeof(u64), s);
   for (u64 u0 = 0; u0 < units && e == cudaSuccess; u0 += per) {
     const u32 cu = (u32)std::min<u64>(per, units - u0);
     {
@@ -487,13 +602,15 @@ cudaError_t pack_device(phe_ctx* c, const phe_ksk* k, u32 T, u32 rows, const voi
       e = phe::launch_input_ntt(c, &nj, 1, s);
     }
     const u32 nseg = mac_segments(c, k, cu);
-    if (e == cudaSuccess) {
+    const size_t slice_stride = (size_t)nseg * cu * 2 * N;  // words of one slice's partial sums
+    for (u32 sl = 0; sl < k->slices && e == cudaSuccess; ++sl) {
       Span sp(c, phe::kKPackMac, s);
-      e = launch_mac(c, k, Dhat, cu, nseg, Phat, s);
+      e = launch_mac(c, k, Dhat, cu, nseg, Phat + sl * slice_stride, s, sl);
     }
     if (e == cudaSuccess) {
       Span sp(c, phe::kKPackFinish, s);
-      e = launch_finish(c, mode, Phat, nseg, body, rows, G, (u32)u0, cu, oa, ob, s);
+      e = c->pow2 ? launch_finish_pow2(c, k, mode, Phat, nseg, slice_stride, body, rows, G, (u32)u0, cu, oa, ob, s)
+                  : launch_finish(c, mode, Phat, nseg, body, rows, G, (u32)u0, cu, oa, ob, s);
     }
   }
   cudaError_t f1 = Phat ? cudaFreeAsync(Phat, s) : cudaSuccess;
@@ -570,12 +687,25 @@ phe_status phe_ksk_upload(phe_ctx* c, const uint64_t* h_ka, const uint64_t* h_kb
                           uint32_t ell, phe_ksk** out) {
   if (!c || !h_ka || !h_kb || !out) return fail(PHE_EINVAL, "phe_ksk_upload: null argument");
   *out = nullptr;
-  if (c->pow2) return fail(PHE_EUNSUPPORTED, "phe_ksk_upload: packing needs an NTT-friendly q (not 2^%u)", c->rk.p2k);
   const u32 N = c->prm.N;
   if (n != N) return fail(PHE_EINVAL, "phe_ksk_upload: n=%u must equal N=%u (LWE outputs of dimension N)", n, N);
   if (ell < 1 || ell > 4 || base_log < 1 || base_log > 30 || base_log * ell > 32)
     return fail(PHE_EINVAL, "phe_ksk_upload: base_log=%u ell=%u (need 1<=ell<=4, 1<=base_log<=30, product<=32)",
                 base_log, ell);
+  const size_t nr = (size_t)n * ell, words = nr * 2 * N;
+  // q = 2^K: slices of b bits with n ell N (B/2) 2^(b-1) below (p1 p2)/2
+  u32 slices = 1, bits = 0;
+  if (c->pow2) {
+    const u32 K = c->rk.p2k;
+    const double lim = std::log2((double)c->rk.Q / 2.0) - std::log2((double)nr * N) - (double)(base_log - 1);
+    bits = (u32)std::floor(lim) + 1;  // 2^(bits-1) <= 2^lim
+    while (bits > 1 && std::ldexp((double)nr * N, (int)(base_log - 1 + bits - 1)) >= (double)c->rk.Q / 2.0) --bits;
+    if (bits < 2) return fail(PHE_EUNSUPPORTED, "phe_ksk_upload: base_log=%u ell=%u leave no exact key slice at N=%u",
+                              base_log, ell, N);
+    if (bits > K) bits = K;
+    slices = (K + 1 + bits - 1) / bits;  // balanced digits of a K-bit centred value: K+1 bits
+    if (slices > 8) return fail(PHE_EUNSUPPORTED, "phe_ksk_upload: %u key slices of %u bits needed", slices, bits);
+  }
   DeviceGuard g(c->device);
   if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
   phe_ksk* k = new (std::nothrow) phe_ksk;
@@ -584,32 +714,69 @@ phe_status phe_ksk_upload(phe_ctx* c, const uint64_t* h_ka, const uint64_t* h_kb
   k->n = n;
   k->base_log = base_log;
   k->ell = ell;
+  k->slices = slices;
+  k->slice_bits = bits;
   k->rcK = c->rc;
   k->rcK.log2_qout = base_log * ell;
   k->rkK = c->rk;
   if (c->rns) phe::set_switch_target(k->rkK, base_log * ell);
-  const size_t nr = (size_t)n * ell, words = nr * 2 * N;
-  k->bytes = words * 16;
+  if (c->pow2) k->rkK.p2shift = c->rk.p2k - base_log * ell;
+  k->bytes = (u64)slices * words * 16;
+  // the host words of one slice: rows r = i*ell + l of KA and KB interleaved
+  std::vector<u64> host;
+  if (c->pow2) {
+    try {
+      host.resize(words);
+    } catch (...) {
+      delete k;
+      return fail(PHE_ENOMEM, "phe_ksk_upload: host staging");
+    }
+  }
   u64* tmp = nullptr;
   cudaError_t e = cudaMalloc((void**)&tmp, words * sizeof(u64));
   if (e == cudaSuccess) e = cudaMalloc(&k->khat, k->bytes);
-  // rows r = i*ell + l of KA and KB interleaved: tmp[r][0] = KA_r, tmp[r][1] = KB_r
-  if (e == cudaSuccess)
-    e = cudaMemcpy2D(tmp, 2 * N * sizeof(u64), h_ka, N * sizeof(u64), N * sizeof(u64), nr, cudaMemcpyHostToDevice);
-  if (e == cudaSuccess)
-    e = cudaMemcpy2D(tmp + N, 2 * N * sizeof(u64), h_kb, N * sizeof(u64), N * sizeof(u64), nr,
-                     cudaMemcpyHostToDevice);
-  if (e == cudaSuccess) {
-    phe::NttJob nj{tmp, tmp, (u32)(nr * 2), nullptr};
-    e = phe::launch_input_ntt(c, &nj, 1, 0);
+  for (u32 sl = 0; sl < slices && e == cudaSuccess; ++sl) {
+    if (!c->pow2) {
+      e = cudaMemcpy2D(tmp, 2 * N * sizeof(u64), h_ka, N * sizeof(u64), N * sizeof(u64), nr, cudaMemcpyHostToDevice);
+      if (e == cudaSuccess)
+        e = cudaMemcpy2D(tmp + N, 2 * N * sizeof(u64), h_kb, N * sizeof(u64), N * sizeof(u64), nr,
+                         cudaMemcpyHostToDevice);
+    } else {
+      // slice sl of each centred word, as a word mod 2^K (the transform's
+      // centred lift gives back the signed slice)
+      const u32 K = c->rk.p2k;
+      const u64 qmask = (1ull << K) - 1, half = 1ull << (bits - 1);
+      for (size_t r = 0; r < nr; ++r)
+        for (u32 comp = 0; comp < 2; ++comp) {
+          const uint64_t* src = (comp ? h_kb : h_ka) + r * N;
+          u64* dst = host.data() + (r * 2 + comp) * N;
+          for (u32 m = 0; m < N; ++m) {
+            const u64 w = src[m] & qmask;
+            long long v = (w >> (K - 1)) ? (long long)w - (long long)(1ull << K) : (long long)w;  // centred
+            long long d = 0;
+            for (u32 t = 0; t <= sl; ++t) {
+              const long long lo = (long long)((((u64)v + half) & ((1ull << bits) - 1)) - half);
+              d = lo;
+              v = (v - lo) >> bits;
+            }
+            dst[m] = (u64)d & qmask;
+          }
+        }
+      e = cudaMemcpy(tmp, host.data(), words * sizeof(u64), cudaMemcpyHostToDevice);
+    }
+    if (e == cudaSuccess) {
+      phe::NttJob nj{tmp, tmp, (u32)(nr * 2), nullptr};
+      e = phe::launch_input_ntt(c, &nj, 1, 0);
+    }
+    if (e == cudaSuccess) {
+      void* dst = static_cast<char*>(k->khat) + (size_t)sl * words * 16;
+      const int blocks = (int)std::min<size_t>((words + 255) / 256, (size_t)c->num_sms * 8);
+      if (c->rns) phe::ksk_finish_kernel<true><<<blocks, 256>>>(tmp, dst, words, c->rc, c->rk, c->ninv);
+      else phe::ksk_finish_kernel<false><<<blocks, 256>>>(tmp, dst, words, c->rc, c->rk, c->ninv);
+      e = cudaGetLastError();
+    }
+    if (e == cudaSuccess) e = cudaDeviceSynchronize();
   }
-  if (e == cudaSuccess) {
-    const int blocks = (int)std::min<size_t>((words + 255) / 256, (size_t)c->num_sms * 8);
-    if (c->rns) phe::ksk_finish_kernel<true><<<blocks, 256>>>(tmp, k->khat, words, c->rc, c->rk, c->ninv);
-    else phe::ksk_finish_kernel<false><<<blocks, 256>>>(tmp, k->khat, words, c->rc, c->rk, c->ninv);
-    e = cudaGetLastError();
-  }
-  if (e == cudaSuccess) e = cudaDeviceSynchronize();
   if (tmp) cudaFree(tmp);
   if (e != cudaSuccess) {
     if (k->khat) cudaFree(k->khat);

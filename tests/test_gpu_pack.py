@@ -19,7 +19,8 @@ from tests.gpu_helpers import to_dev_u64
 
 pytestmark = pytest.mark.gpu
 
-MODULI = {"prime": (synth.Q60, None), "rns": (synth.Q_RNS, (synth.RNS_P1, synth.RNS_P2))}
+MODULI = {"prime": (synth.Q60, None), "rns": (synth.Q_RNS, (synth.RNS_P1, synth.RNS_P2)),
+          "pow2": (1 << 39, (synth.RNS_P1, synth.RNS_P2))}   # q = 2^39: the key in exact slices
 
 
 @pytest.fixture(scope="module")
@@ -58,7 +59,8 @@ def _gpu_pack(ctx, k, masks, bodies, N, flags):
 
 
 @pytest.mark.parametrize("modulus,base_log,ell", [("rns", 26, 1), ("prime", 26, 1), ("rns", 13, 2),
-                                                  ("prime", 10, 3), ("rns", 8, 4)])
+                                                  ("prime", 10, 3), ("rns", 8, 4),
+                                                  ("pow2", 26, 1), ("pow2", 13, 2), ("pow2", 8, 4)])
 def test_pack_matches_oracle(orc, ctxs, modulus, base_log, ell):
     N, T, rows = 256, 2, 300          # two row groups per token, the second ragged (44 rows)
     q = MODULI[modulus][0]
@@ -83,6 +85,43 @@ def test_pack_matches_oracle(orc, ctxs, modulus, base_log, ell):
             assert np.array_equal(raw_a[t, grp], ea) and np.array_equal(raw_b[t, grp], eb), (t, grp)
             assert np.array_equal(sw_a[t, grp], orc.modswitch(ea, q, 32))
             assert np.array_equal(sw_b[t, grp], orc.modswitch(eb, q, 32))
+
+
+def test_matmul_packed_pow2_matches_oracle(orc, ctxs):
+    # q = 2^39: Eq. (LWEdot) through p1 p2, the masks switched to 2^26 for
+    # Decomp, the key in slices; compared word for word with the oracle's
+    # composition (no decryption: with t = 2^16 the key-switching noise at
+    # this q exceeds the plaintext margin)
+    import torch
+    N, T, q = 256, 2, 1 << 39
+    ctx = ctxs(N, "pow2")
+    g = _rng(41)
+    W = synth.weights(300, 290, seed=42)
+    L = synth.blocks(290, N)
+    A = g.integers(0, q, (T, L, N), dtype=np.uint64)
+    B = g.integers(0, q, (T, L, N), dtype=np.uint64)
+    KA = g.integers(0, q, (N, 1, N), dtype=np.uint64)
+    KB = g.integers(0, q, (N, 1, N), dtype=np.uint64)
+    w = phe.phe_weights_upload(ctx, W, phe.PHE_DIR_FWD_BIT)
+    k = phe.phe_ksk_upload(ctx, KA, KB, 26, 1)
+    try:
+        oa = torch.empty((T, 2, N), dtype=torch.int32, device="cuda")
+        ob = torch.empty((T, 2, N), dtype=torch.int32, device="cuda")
+        phe.phe_matmul_packed(ctx, w, k, phe.PHE_FWD, T, to_dev_u64(A), to_dev_u64(B), oa, ob)
+        torch.cuda.synchronize()
+    finally:
+        phe.phe_ksk_free(k)
+        phe.phe_weights_free(w)
+    ga = oa.cpu().numpy().view(np.uint32).astype(np.uint64)
+    gb = ob.cpu().numpy().view(np.uint32).astype(np.uint64)
+    la, lb = orc.lwedot_all(W, A, B, q)
+    for t in range(T):
+        for grp in range(2):
+            m = min(N, 300 - grp * N)
+            ea, eb = orc.pack_coeffs(la[t, grp * N:grp * N + m], lb[t, grp * N:grp * N + m], KA, KB, q, 26, 1,
+                                     np.arange(N))
+            assert np.array_equal(ga[t, grp], orc.modswitch(ea, q, 32)), (t, grp)
+            assert np.array_equal(gb[t, grp], orc.modswitch(eb, q, 32)), (t, grp)
 
 
 @pytest.mark.parametrize("modulus", ["rns", "prime"])

@@ -125,9 +125,14 @@ def test_pow2_rejects_blocks_beyond_the_exact_range(ctxs):
         assert ei.value.status == phe.PHE_EINVAL
     finally:
         phe.phe_ctx_destroy(ctx)
-    with pytest.raises(phe.PheError) as ei:
-        phe.phe_ksk_upload(ctxs(256), np.zeros((256, 1, 256), np.uint64), np.zeros((256, 1, 256), np.uint64), 13, 1)
-    assert ei.value.status == phe.PHE_EUNSUPPORTED
+    # a key-switching key at q = 2^39 is held in exact slices: at N = n = 256,
+    # base 2^13, one level, 256 * 256 * 2^12 * 2^(b-1) < p1 p2 / 2 gives
+    # b = 31 bits, so two slices of the 40-bit balanced key
+    k = phe.phe_ksk_upload(ctxs(256), np.zeros((256, 1, 256), np.uint64), np.zeros((256, 1, 256), np.uint64), 13, 1)
+    try:
+        assert phe.phe_ksk_device_bytes(k) == 2 * (256 * 2 * 256 * 16)
+    finally:
+        phe.phe_ksk_free(k)
 
 
 def _bit_errors(y, dec, bits=BETA):
