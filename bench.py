@@ -1009,44 +1009,69 @@ PAPER_TABLE = (((768, 768), 0.0809), ((3072, 768), 0.1528), ((2048, 2048), 0.240
 def measure_paper_table(phe, dev, tokens=64):
     """The shapes of Table fhe_matmul_timing at the paper's parameter set
     (N = 2048, q = 2^39 computed through p1 p2, q_out = 2^26): one-token
-    latency of phe_matmul and throughput on `tokens` tokens (device-resident,
-    CUDA events).  The paper's times include its output packing, which this
-    parameter set does not run here, so they are context only."""
+    latency and throughput on `tokens` tokens (device-resident, CUDA events)
+    of phe_matmul (LWE outputs) and of phe_matmul_packed (one packed RLWE per
+    2048 rows, as the paper's timed path; base 2^26, one level, the key in
+    4 exact slices).  The key-switching key is random words: the server's work
+    does not depend on its values."""
     import torch
     ctx = phe.phe_ctx_create(2048, 1 << 39, 26, dev.index or 0, rns=(synth.RNS_P1, synth.RNS_P2))
     rows_out = []
+    k = None
     try:
         stream = torch.cuda.current_stream(dev)
+        kg = np.random.Generator(np.random.PCG64(synth.SEED_KEY + 39))
+        KA = kg.integers(0, 1 << 39, (2048, 1, 2048), dtype=np.uint64)
+        KB = kg.integers(0, 1 << 39, (2048, 1, 2048), dtype=np.uint64)
+        k = phe.phe_ksk_upload(ctx, KA, KB, 26, 1)
+        del KA, KB
+
+        def timed(f, T, reps=5):
+            for _ in range(2):
+                f(T)
+            a = torch.cuda.Event(enable_timing=True)
+            b = torch.cuda.Event(enable_timing=True)
+            a.record(stream)
+            for _ in range(reps):
+                f(T)
+            b.record(stream)
+            torch.cuda.synchronize()
+            return a.elapsed_time(b) / reps
+
         for (d_in, d_out), paper_s in PAPER_TABLE:
             W = synth.weights(d_out, d_in, seed=synth.SEED_W + d_in + d_out)
             w = phe.phe_weights_upload(ctx, W, phe.PHE_DIR_FWD_BIT)
             L = synth.blocks(d_in, 2048)
+            G = (d_out + 2047) // 2048
             g = torch.Generator(device=dev)
             g.manual_seed(d_in * 7 + d_out)
             A = torch.randint(0, 1 << 39, (tokens, L, 2048), device=dev, generator=g, dtype=torch.int64)
             B = torch.randint(0, 1 << 39, (tokens, L, 2048), device=dev, generator=g, dtype=torch.int64)
             om = torch.empty((tokens, d_out, 2048), dtype=torch.int32, device=dev)
             ob = torch.empty((tokens, d_out), dtype=torch.int32, device=dev)
-            res = {}
-            for T in (1, tokens):
-                for _ in range(2):
-                    phe.phe_matmul(ctx, w, phe.PHE_FWD, T, A, B, om, ob, phe.PHE_OUT_SWITCHED, stream)
-                a = torch.cuda.Event(enable_timing=True)
-                b = torch.cuda.Event(enable_timing=True)
-                reps = 5
-                a.record(stream)
-                for _ in range(reps):
-                    phe.phe_matmul(ctx, w, phe.PHE_FWD, T, A, B, om, ob, phe.PHE_OUT_SWITCHED, stream)
-                b.record(stream)
-                torch.cuda.synchronize()
-                res[T] = a.elapsed_time(b) / reps
+            pa = torch.empty((tokens, G, 2048), dtype=torch.int32, device=dev)
+            pb = torch.empty((tokens, G, 2048), dtype=torch.int32, device=dev)
+
+            def lwe(T):
+                phe.phe_matmul(ctx, w, phe.PHE_FWD, T, A, B, om, ob, phe.PHE_OUT_SWITCHED, stream)
+
+            def packed(T):
+                phe.phe_matmul_packed(ctx, w, k, phe.PHE_FWD, T, A, B, pa, pb, phe.PHE_OUT_SWITCHED, stream)
+
+            res = {T: timed(lwe, T) for T in (1, tokens)}
+            pres = {T: timed(packed, T, reps=3) for T in (1, tokens)}
             phe.phe_weights_free(w)
             rows_out.append({"shape": f"{d_in}->{d_out}", "paper_s_per_token": paper_s,
-                             "latency_ms_1_token": res[1], "tokens_per_s": tokens / (res[tokens] / 1e3)})
+                             "latency_ms_1_token": res[1], "tokens_per_s": tokens / (res[tokens] / 1e3),
+                             "packed_latency_ms_1_token": pres[1],
+                             "packed_tokens_per_s": tokens / (pres[tokens] / 1e3)})
     finally:
+        if k is not None:
+            phe.phe_ksk_free(k)
         phe.phe_ctx_destroy(ctx)
     return {"params": "N=2048, q=2^39 (exact through p1 p2), q_out=2^26", "tokens": tokens, "rows": rows_out,
-            "note": "paper times: laptop GPU, one token, with output packing; ours: one B300, no packing at q=2^39"}
+            "note": "paper times: laptop GPU, one token, with output packing; ours: one B300, LWE outputs and "
+                    "packed RLWE outputs (base 2^26, one level, key in exact slices)"}
 
 
 if __name__ == "__main__":
