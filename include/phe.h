@@ -75,9 +75,9 @@ typedef struct phe_weights phe_weights;
  *                  (masks lifted to [-2^(K-1), 2^(K-1))), then are reduced
  *                  mod 2^K; this needs N * 127 * 2^(K-1) * L < p1 p2 / 2 for
  *                  the weights' block count L (checked at upload), and the
- *                  switch is a rounding shift (ties up).  No 64-bit form,
- *                  client encryption or packing for such a q
- *                  (PHE_EUNSUPPORTED)
+ *                  switch is a rounding shift (ties up).  No 64-bit form
+ *                  and no client encryption for such a q (PHE_EUNSUPPORTED);
+ *                  packing holds the key in exact slices (phe_ksk_upload)
  *   log2_qout  k of the output modulus q' = 2^k, 1 <= k <= 32 (k < K for q = 2^K)
  *   flags      PHE_CTX_FORCE_U64: with an RNS modulus, run the 64-bit form
  *              anyway (the results are identical; for cross-checks) */

@@ -14,6 +14,9 @@
 //   pack_mac_kernel        per NTT slot: sum over (i,l) of D_hat * KSK_hat
 //                          (the key carries -N^-1 and Shoup quotients)
 //   pack_finish_kernel     inverse NTT of A_hat and B_hat, + b_j X^j, switch
+//   pack_finish_pow2_kernel  the same for q = 2^K, whose key is held in exact
+//                          slices: each slice's contraction lifted centred
+//                          by CRT, the slices combined mod 2^K
 //   ksk_finish_kernel      upload: NTT(KSK) -> -N^-1 NTT(KSK) with quotients
 #include <algorithm>
 #include <cmath>
