@@ -985,15 +985,26 @@ def measure_wire(phe, ctx, N, w, k, prod, tokens, stream, dev, reps=3):
 
 def measure_wire_paper_set(phe, dev, tokens=64):
     """phe_matmul_wire at the paper's parameter set (N = 2048, q = 2^39 ->
-    q_out = 2^26) on a 2048->2048 forward product: 9992-byte input records in,
-    LWE records out (this modulus has no key switching here)."""
+    q_out = 2^26) on a 2048->2048 forward product, 9992-byte input records in:
+    LWE records out, and packed RLWE records out (13312 bytes, the size Sec.
+    4.4 counts; a random key-switching key of base 2^26, one level, in exact
+    slices: the server's work does not depend on its values)."""
     import torch
     ctx = phe.phe_ctx_create(2048, 1 << 39, 26, dev.index or 0, rns=(synth.RNS_P1, synth.RNS_P2))
+    stream = torch.cuda.current_stream(dev)
+    prod = (0, "2048->2048", "fwd", 2048, 2048, 1)
     try:
         w = phe.phe_weights_upload(ctx, synth.weights(2048, 2048, seed=synth.SEED_W + 4096), phe.PHE_DIR_FWD_BIT)
         try:
-            return measure_wire(phe, ctx, 2048, w, None, (0, "2048->2048", "fwd", 2048, 2048, 1), tokens,
-                                torch.cuda.current_stream(dev), dev)
+            out = {"lwe": measure_wire(phe, ctx, 2048, w, None, prod, tokens, stream, dev)}
+            kg = np.random.Generator(np.random.PCG64(synth.SEED_KEY + 40))
+            k = phe.phe_ksk_upload(ctx, kg.integers(0, 1 << 39, (2048, 1, 2048), dtype=np.uint64),
+                                   kg.integers(0, 1 << 39, (2048, 1, 2048), dtype=np.uint64), 26, 1)
+            try:
+                out["packed"] = measure_wire(phe, ctx, 2048, w, k, prod, tokens, stream, dev)
+            finally:
+                phe.phe_ksk_free(k)
+            return out
         finally:
             phe.phe_weights_free(w)
     finally:

@@ -127,6 +127,45 @@ def test_matmul_wire_paper_parameter_set(orc, ctxs):
         assert fields[N] == orc.modswitch_one(int(eb[x]), Q39, k), (t, j)
 
 
+def test_matmul_wire_packed_records_paper_modulus(orc, ctxs):
+    # q = 2^39 -> 2^26 (the paper's moduli) with packing: seed + 39-bit body
+    # records in, RLWE records of 2N 26-bit words out (13312 bytes at
+    # N = 2048), equal to phe_matmul_packed's outputs bit-packed
+    import torch
+    N, k, T = 256, 26, 2
+    ctx = ctxs(N, Q39, k)
+    g = _rng(79)
+    W = g.integers(-127, 128, (300, 290)).astype(np.int8)
+    KA = g.integers(0, Q39, (N, 1, N), dtype=np.uint64)
+    KB = g.integers(0, Q39, (N, 1, N), dtype=np.uint64)
+    seeds = g.integers(0, 2 ** 64, (T, 2), dtype=np.uint64)
+    A = orc.expand_masks(seeds, N, Q39)
+    B = g.integers(0, Q39, (T, 2, N), dtype=np.uint64)
+    recs = np.concatenate([orc.wire_input_record(int(seeds[t, i]), B[t, i], 39) for t in range(T) for i in range(2)])
+    sizes = phe.phe_wire_sizes(ctx)
+    assert sizes["rlwe"] == 2 * N * k // 8
+    w = phe.phe_weights_upload(ctx, W, phe.PHE_DIR_FWD_BIT)
+    kk = phe.phe_ksk_upload(ctx, KA, KB, 26, 1)
+    try:
+        out = _dev_bytes(T * 2 * sizes["rlwe"])
+        phe.phe_matmul_wire(ctx, w, kk, phe.PHE_FWD, T, torch.from_numpy(recs.view(np.int32).copy()).cuda(), out)
+        oa = torch.empty((T, 2, N), dtype=torch.int32, device="cuda")
+        ob = torch.empty_like(oa)
+        phe.phe_matmul_packed(ctx, w, kk, phe.PHE_FWD, T, to_dev_u64(A), to_dev_u64(B), oa, ob)
+        torch.cuda.synchronize()
+    finally:
+        phe.phe_ksk_free(kk)
+        phe.phe_weights_free(w)
+    got = _host_bytes(out, T * 2 * sizes["rlwe"])
+    pa = oa.cpu().numpy().view(np.uint32).astype(np.uint64)
+    pb = ob.cpu().numpy().view(np.uint32).astype(np.uint64)
+    for t in range(T):
+        for grp in range(2):
+            r = t * 2 + grp
+            want = orc.pack_bits(np.concatenate([pa[t, grp], pb[t, grp]]), k)
+            assert np.array_equal(got[r * sizes["rlwe"]:(r + 1) * sizes["rlwe"]], want), (t, grp)
+
+
 def test_matmul_wire_packed_records(orc, ctxs):
     import torch
     N, k, T = 256, 26, 3
