@@ -161,11 +161,12 @@ def test_packed_ciphertext_decrypts_to_the_product(orc, N, d_in, m):
     assert [orc.decode(v, 1 << 32, t) for v in ph2] == want
 
 
-def test_packing_is_exact_when_decomp_is(orc):
-    # q = B^ell and a noiseless key: coefficient j of the packed phase equals
-    # the phase of LWE_j exactly, and the unused coefficients are 0.
-    base_log, ell = 8, 3
-    q = 1 << 24
+@pytest.mark.parametrize("base_log,ell", [(8, 3), (13, 3)])
+def test_packing_is_exact_when_decomp_is(orc, base_log, ell):
+    # q = B^ell (2^24, and the paper's 2^39) and a noiseless key: coefficient
+    # j of the packed phase equals the phase of LWE_j exactly, and the unused
+    # coefficients are 0.
+    q = 1 << (base_log * ell)
     N, n, m = 32, 32, 20
     g = _rng(10)
     S = g.integers(-1, 2, N)
