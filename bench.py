@@ -88,7 +88,9 @@ def parse():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
-    ap.add_argument("--workload", choices=["layer", "q_proj", "toy"], default="layer")
+    ap.add_argument("--workload", choices=["layer", "q_proj", "toy", "model"], default="layer",
+                    help="model: the 16-layer step (all 16 layers' weights resident, batch 8 with U{64..2048} "
+                         "tokens per sequence; plain per-call form, --batch-chunk tokens per call)")
     ap.add_argument("--form", choices=["batched", "plain"], default="batched",
                     help="batched: one autotuned plan (persistent launch, CUDA graph) per token chunk over all "
                          "products; plain: one phe_matmul call per product and token chunk")
@@ -109,10 +111,13 @@ def parse():
     ap.add_argument("--modulus", choices=["rns", "prime"], default="rns",
                     help="rns: q = p1 p2 (two 30-bit NTT primes, 32-bit residue kernels); "
                          "prime: q = 2^60 - 2^14 + 1 (64-bit kernels)")
-    ap.add_argument("--serve-requests", type=int, default=48, help="requests in the serving measurement (0 = skip)")
+    ap.add_argument("--serve-requests", type=int, default=500, help="requests in the serving measurement (0 = skip)")
     ap.add_argument("--serve-rate", type=float, default=200.0, help="mean Poisson arrival rate, requests/s")
-    ap.add_argument("--serve-light-rate", type=float, default=3.5,
-                    help="arrival rate of a second, light-load serving measurement (16 requests; 0 = skip)")
+    ap.add_argument("--serve-light-load", type=float, default=0.6,
+                    help="second serving measurement, below capacity: arrival rate as this fraction of the rate "
+                         "served in the saturated run (same request count; 0 = skip)")
+    ap.add_argument("--serving-only", action="store_true",
+                    help="skip the timed layer steps' side measurements and run only the serving measurements")
     return ap.parse_args()
 
 
@@ -272,6 +277,8 @@ def oracle_tokens_per_s(wl, seconds: float):
     except OSError:
         pass
     return {"value": 1.0 / sec_per_token, "unit": "tokens/s", "cores": threads, "kind": "oracle",
+            "extrapolated": True, "products_sampled": done, "products_per_token": per_token_items,
+            "modulus": "q = 2^60-2^14+1 (prime; the GPU line runs the RNS q = p1 p2 of the same size)",
             "single_core_value": 1.0 / one, "host_cpu": cpu_model, "host_logical_cpus": os.cpu_count(),
             "sample": f"{done} (token,row) products, {rounds} rounds over all {len(mm)} projection/direction "
                       f"shapes, oracle NTT path on {threads} host threads, {elapsed:.1f} s wall; per-shape "
@@ -292,6 +299,12 @@ def run_reference(args, wl, rank):
     cb = dict(vals[-1])
     cb["value"] = value
     line = {"impl": "reference", "metric": METRIC, "value": value, "unit": "tokens/s", "n_gpus": args.gpus,
+            "extrapolated": True,
+            "sample": (f"{sum(v['products_sampled'] for v in vals)} (token,row) products over {args.steps} steps "
+                       f"(about {cb['products_sampled'] / cb['products_per_token']:.4f} of one token's "
+                       f"{cb['products_per_token']} products per step), scaled per shape to whole tokens; "
+                       f"ms_per_step is that rate's time for the workload's {wl.tokens} tokens, not a measured step"),
+            "modulus": cb["modulus"],
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 / value * wl.tokens,
             "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "u64 (mod q)",
             "data": "synthetic",
@@ -316,6 +329,145 @@ def workload_config(wl, args, form):
 
 
 # ---------------------------------------------------------------------------
+# the 16-layer step (configuration of the full model)
+# ---------------------------------------------------------------------------
+
+def run_model(args, wl, rank, world, local):
+    """One step = every layer's 14 products (7 projections, forward and
+    backward) over a batch of 8 sequences whose token counts are drawn from
+    U{64..2048}, with all 16 layers' encoded weights resident in HBM.  Each
+    sequence is cut into calls of --batch-chunk tokens per product (ragged
+    last calls), plain per-call form.  The encrypted inputs of one layer are
+    reused by every layer: the server's work does not depend on their values,
+    and 16 layers' distinct inputs would add 16x their 8 GB."""
+    import torch
+    from paper_2505_07329_b300 import build, phe
+    from paper_2505_07329_b300.dist import max_over_ranks
+    build.build()
+    phe.use_test_library()  # the client-side encryption that makes the synthetic inputs
+    torch.cuda.set_device(local)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    N, layers = wl.ring.N, wl.extra["layers"]
+    counts = [int(c) for c in synth.model_token_counts(wl.extra["batch"], wl.extra["tok_lo"], wl.extra["tok_hi"],
+                                                       seed=synth.SEED_X + rank)]
+    T = sum(counts)
+    starts = np.concatenate([[0], np.cumsum(counts)[:-1]]).astype(int)
+    chunk = args.batch_chunk
+    dev = torch.device("cuda", local)
+    stream = torch.cuda.current_stream(dev)
+    q = synth.Q_RNS
+    ctx = phe.phe_ctx_create(N, q, wl.ring.log2_qout, local, rns=(synth.RNS_P1, synth.RNS_P2))
+    gen = torch.Generator(device=dev)
+    gen.manual_seed(synth.SEED_MASK + rank)
+    t_up = time.perf_counter()
+    weights = []
+    for layer in range(layers):
+        weights.append([phe.phe_weights_upload(ctx, synth.weights(d_out, d_in, seed=synth.SEED_W + 100 * layer + pi),
+                                               phe.PHE_DIR_FWD_BIT | phe.PHE_DIR_BWD_BIT)
+                        for pi, (name, d_in, d_out) in enumerate(wl.projections)])
+    torch.cuda.synchronize()
+    upload_s = time.perf_counter() - t_up
+    resident = sum(phe.phe_weights_device_bytes(w) for lw in weights for w in lw)
+    S = torch.randint(-1, 2, (N,), device=dev, generator=gen, dtype=torch.int8)
+    inputs = {}
+    for (pi, d), (key, cols, L) in input_keys(wl).items():
+        if key in inputs:
+            continue
+        A = torch.randint(0, q, (T, L, N), device=dev, generator=gen, dtype=torch.int64)
+        E = torch.round(torch.randn((T, L, N), device=dev, generator=gen) * wl.ring.sigma).to(torch.int32)
+        X = torch.randint(-127, 128, (T, cols), device=dev, generator=gen, dtype=torch.int8)
+        B = torch.empty_like(A)
+        phe.phe_client_encrypt(ctx, T, cols, A, S, E, X, q // wl.ring.t, B)
+        inputs[key] = (A, B, X)
+    keys = input_keys(wl)
+    mm = matmuls(wl)
+    outs = [(torch.empty((chunk, rows, N), dtype=torch.int32, device=dev),
+             torch.empty((chunk, rows), dtype=torch.int32, device=dev)) for (_, _, _, rows, _, _) in mm]
+    torch.cuda.synchronize()
+
+    def step():
+        for layer in range(layers):
+            for s0, Ts in zip(starts, counts):
+                for t0 in range(0, Ts, chunk):
+                    tn = min(chunk, Ts - t0)
+                    a = s0 + t0
+                    for n, (pi, name, d, rows, cols, L) in enumerate(mm):
+                        A, B, _ = inputs[keys[(pi, d)][0]]
+                        phe.phe_matmul(ctx, weights[layer][pi], phe.PHE_FWD if d == "fwd" else phe.PHE_BWD, tn,
+                                       A[a:a + tn], B[a:a + tn], outs[n][0], outs[n][1], phe.PHE_OUT_SWITCHED,
+                                       stream)
+
+    phe.phe_trace_enable(ctx, True)
+    for _ in range(max(args.warmup, 0)):
+        step()
+        torch.cuda.synchronize()
+        phe.phe_trace_read(ctx)
+    clocks = ClockSampler(local)
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    clocks.start()
+    alu = alu_probe(phe, local, "rns")
+    torch.cuda.synchronize()
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    ev0.record(stream)
+    for _ in range(args.steps):
+        step()
+    ev1.record(stream)
+    torch.cuda.synchronize()
+    clk = clocks.stop()
+    tr = phe.phe_trace_read(ctx)
+    phe.phe_trace_enable(ctx, False)
+    if dist:
+        dist.barrier()
+    elapsed_ms = max_over_ranks(ev0.elapsed_time(ev1), device=dev)
+    layer_tokens = T * layers * args.steps * world
+    lw = tr.get("lwedot_kernel", {})
+    modmuls = modmuls_per_token(wl) * T * layers * args.steps
+    achieved = modmuls / (lw["total_ms"] / 1e3) / 1e9 if lw.get("total_ms") else None
+    ub = unit_bound_gmodmul(clk.get("sm_max_mhz") or 2032.0)
+    if rank == 0:
+        line = {"metric": METRIC, "value": layer_tokens / (elapsed_ms / 1e3), "unit": "tokens/s",
+                "n_gpus": world, "steps": args.steps, "warmup": args.warmup, "ms_per_step": elapsed_ms / args.steps,
+                "higher_is_better": True, "scaling": "weak", "vs_baseline": None,
+                "dtype": "u64 mod q (u32 out mod 2^32)",
+                "data": "synthetic (seeded RLWE encryptions of uniform int8 activations; uniform int8 weights)",
+                "config": {"workload": "llama3.2-1b-model-step", "description": wl.description,
+                           "layers": layers, "sequence_tokens": counts, "tokens_per_step": T,
+                           "layer_tokens_per_step": T * layers, "N": N,
+                           "q": f"{synth.RNS_P1}*{synth.RNS_P2} (RNS)", "q_out": "2^32",
+                           "form": f"plain per-call, {chunk}-token phe_matmul calls per sequence and product",
+                           "weights_resident_bytes": resident, "weights_upload_s": upload_s,
+                           "inputs": "one layer's encrypted inputs, reused by every layer",
+                           "l2": "inputs larger than L2"},
+                "step_s": elapsed_ms / args.steps / 1e3,
+                "sequence_tokens_s": T * args.steps * world / (elapsed_ms / 1e3),
+                "roofline": {"bound": "alu", "unit": "Gmodmul/s", "achieved": achieved, "peak": alu["gmodmul"],
+                             "frac": achieved / alu["gmodmul"] if achieved else None,
+                             "unit_count_bound": ub, "frac_of_unit_count_bound": achieved / ub if achieved else None,
+                             "peak_basis": f"phe_probe_alu in this run: {alu['bfly_per_s'] / 1e9:.1f} G 32-bit "
+                                           f"butterflies/s / 2 residues", "traffic": None,
+                             "share_of_step": lw.get("total_ms", 0.0) / elapsed_ms},
+                "kernels": {k: {"launches": v["launches"], "total_ms": v["total_ms"]} for k, v in tr.items()},
+                "gpu_launches": sum(v["launches"] for k, v in tr.items() if not k.startswith("phe_")),
+                "clocks": clk, "paper_step_s": 3458.0,
+                "paper_step_note": "Sec. 6.3: one training step of Llama-3.2-1B under HE, B = 1, C = 16 tokens, "
+                                   "RTX 4060 Laptop GPU, packed outputs (context, not a like-for-like target)"}
+        print(json.dumps(line))
+    for lw_ in weights:
+        for w in lw_:
+            phe.phe_weights_free(w)
+    phe.phe_ctx_destroy(ctx)
+    if dist:
+        dist.destroy_process_group()
+    return 0
+
+
+# ---------------------------------------------------------------------------
 # our arm
 # ---------------------------------------------------------------------------
 
@@ -328,9 +480,12 @@ def main():
     if args.impl == "reference":
         return run_reference(args, wl, rank)
 
+    if wl.name == "model":
+        return run_model(args, wl, rank, world, local)
     import torch
     from paper_2505_07329_b300 import build, phe
-    build.build()  # a no-op unless a source is newer than libphe.so
+    build.build()
+    phe.use_test_library()  # the client-side encryption that makes the synthetic inputs
     torch.cuda.set_device(local)
     dist = None
     if world > 1:
@@ -430,6 +585,9 @@ def main():
             else:
                 phe.phe_plan_run(pl, side)
 
+    if args.serving_only:
+        args.no_compare, args.small_batches, args.no_e2e = True, "", True
+        args.paper_table, args.packed_tokens, args.no_cpu = 0, 0, True
     run_stream = side if args.form == "batched" else stream
     step = batched_step if args.form == "batched" else plain_step
 
@@ -452,6 +610,13 @@ def main():
         dist.barrier()
     torch.cuda.synchronize()
     clocks.start()
+    # the roofline denominators, measured in this process right before the
+    # timed region, under the same clock sampling
+    alu = alu_probe(phe, local, args.modulus)
+    tc_tflops = tensor_probe(phe, local)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
     ev0 = torch.cuda.Event(enable_timing=True)
     ev1 = torch.cuda.Event(enable_timing=True)
     step_ms = []
@@ -496,7 +661,8 @@ def main():
     kernel_ms = lw.get("total_ms", 0.0)
     modmuls = modmuls_per_token(wl) * T * args.steps
     achieved = modmuls / (kernel_ms / 1e3) / 1e9 if kernel_ms else None
-    peak = alu_peak_gmodmul(args.modulus)
+    peak = alu["gmodmul"]
+    unit_bound = unit_bound_gmodmul(clk.get("sm_max_mhz") or 2032.0) if args.modulus == "rns" else None
     traffic_ok = (kernel_source_hash() == TRAFFIC_KERNEL_HASH and wl.name == "layer" and bchunk == 128
                   and args.form == "batched" and args.modulus == "rns" and T % bchunk == 0
                   and tuning is not None and tuple(tuning) == TRAFFIC_TUNING)
@@ -504,14 +670,33 @@ def main():
             "frac": (achieved / peak) if achieved and peak else None,
             "traffic": TRAFFIC_BYTES_PER_LAUNCH if traffic_ok else None,
             "traffic_alg_bytes": TRAFFIC_ALG_BYTES_PER_LAUNCH if traffic_ok else None,
-            "peak_basis": (f"148 SMs x {BFLY32_PER_SM_CLK} 32-bit butterflies/clk/SM / 2 residues x 2032 MHz"
-                           if args.modulus == "rns" else
-                           f"148 SMs x {BFLY64_PER_SM_CLK} 64-bit butterflies/clk/SM x 2032 MHz") +
-                          " (register-only butterfly probe); unit: coefficient modmuls",
+            "peak_basis": (f"measured in this run by phe_probe_alu: {alu['bfly_per_s'] / 1e9:.1f} G "
+                           f"{alu['bfly']} register-only butterflies/s"
+                           + (" / 2 residues per coefficient" if args.modulus == "rns" else "")
+                           + "; unit: coefficient modmuls"),
+            "unit_count_bound": unit_bound,
+            "frac_of_unit_count_bound": (achieved / unit_bound) if achieved and unit_bound else None,
+            "unit_count_basis": ("148 SMs x 64 FMA-heavy lanes / 4 lane-slots per 32-bit Shoup butterfly / "
+                                 "2 residues x max SM clock" if unit_bound else None),
             "kernel_ms_per_launch": kernel_ms / launches if launches else None,
             "launches": launches,
             "share_of_step": kernel_ms / elapsed_ms if elapsed_ms else None,
             "out_write_GBps": out_bytes_per_token(wl) * T * args.steps / (kernel_ms / 1e3) / 1e9 if kernel_ms else None}
+    bg = trace.get("body_gemm_kernel", {})
+    roof_body = None
+    if bg.get("total_ms"):
+        body_tflops = body_flops_per_token(wl) * T * args.steps / (bg["total_ms"] / 1e3) / 1e12
+        roof_body = {"kernel": "body_gemm_kernel", "bound": "tensor", "unit": "TFLOP/s", "achieved": body_tflops,
+                     "peak": BF16_TFLOPS_SUSTAINED, "frac": body_tflops / BF16_TFLOPS_SUSTAINED,
+                     "peak_basis": "MEASURED_PEAKS bf16_tflops_sustained (cuBLAS bf16, kernel timed inside a long "
+                                   "step)",
+                     "probe_tflops": tc_tflops, "frac_of_probe": body_tflops / tc_tflops,
+                     "probe_basis": "phe_probe_tensor in this run: back-to-back tcgen05.mma kind::f16, M128 N256 "
+                                    "K16, one CTA per SM",
+                     "int8_kind": int8_kind_check(),
+                     "launches": bg.get("launches"), "ms_per_launch": bg["total_ms"] / bg["launches"],
+                     "share_of_step": bg["total_ms"] / elapsed_ms,
+                     "flops_basis": "2 x 8 base-256 digits x rows x cols per token and product"}
     if args.form == "batched":
         # graph replays: the input transforms run inside the graphs without
         # their own events; count them from the plans
@@ -543,9 +728,9 @@ def main():
         small = measure_small_batches(phe, ctx, weights, mm, keys, inputs, outs,
                                       [t for t in sizes if t <= out_tokens], stream, side)
 
-    e2e = None
+    e2e_unpacked = None
     if not args.no_e2e:
-        e2e = measure_e2e(phe, ctx, weights, wl, mm, keys, inputs, args.e2e_tokens, stream)
+        e2e_unpacked = measure_e2e(phe, ctx, weights, wl, mm, keys, inputs, args.e2e_tokens, stream)
 
     paper_table = None
     if args.paper_table and rank == 0:
@@ -555,7 +740,15 @@ def main():
     packed = None
     if args.packed_tokens > 0:
         packed = measure_packed(phe, ctx, weights, wl, mm, keys, inputs, S, q, min(args.packed_tokens, T), stream,
-                                gen, dev)
+                                gen, dev, alu)
+    # The end-to-end figure the line leads with is the paper's server path as
+    # a client sees it: host buffers in, Eq. (LWEdot), the packing of
+    # Eq. (pack_rotate) and the switch, packed RLWE results back to host.
+    e2e = None
+    if packed is not None and not args.no_e2e:
+        e2e = dict(packed["e2e"])
+        e2e["path"] = ("phe_matmul_packed_host over the layer's 14 products: pinned host inputs -> device, "
+                       "Eq. (LWEdot), Eq. (pack_rotate), switch, packed RLWE results -> pinned host")
 
     serving = None
     if args.serve_requests > 0 and wl.name == "layer":
@@ -565,11 +758,20 @@ def main():
         plans = []
         serving = measure_serving(phe, ctx, weights, wl, inputs, keys, args.serve_requests, args.serve_rate, T,
                                   tuning[0] if tuning else 8)
-        if args.serve_light_rate > 0:
-            # the same request mix at about half the served capacity: latency
-            # without a standing queue
-            serving["light_load"] = measure_serving(phe, ctx, weights, wl, inputs, keys, 16, args.serve_light_rate,
+        if args.serve_light_load > 0:
+            # the same request mix below the capacity the saturated run
+            # measured: latency without a standing queue
+            light = args.serve_light_load * serving["served_req_s"]
+            serving["light_load"] = measure_serving(phe, ctx, weights, wl, inputs, keys, args.serve_requests, light,
                                                     T, tuning[0] if tuning else 8)
+            serving["light_load"]["rate_basis"] = (f"{args.serve_light_load} x the saturated run's served "
+                                                   f"{serving['served_req_s']:.2f} req/s")
+        # the plain per-call form on the first requests of the same stream
+        n_plain = min(args.serve_requests, 100)
+        serving["plain_same_stream"] = measure_serving_plain(phe, ctx, weights, wl, inputs, keys, args.serve_requests,
+                                                             n_plain, T, stream)
+        serving["served_over_plain"] = (serving["layer_equiv_tokens_s"] /
+                                        serving["plain_same_stream"]["layer_equiv_tokens_s"])
 
     cpu = None
     if rank == 0 and world == 1 and not args.no_cpu:
@@ -600,7 +802,8 @@ def main():
                 "serving": serving,
                 "packed": packed,
                 "paper_table": paper_table,
-                "roofline": roof, "cpu_baseline": cpu, "e2e": e2e, "gpu_launches": gpu_launches,
+                "roofline": roof, "roofline_body": roof_body, "cpu_baseline": cpu, "e2e": e2e,
+                "e2e_unpacked": e2e_unpacked, "gpu_launches": gpu_launches,
                 "kernels": {k: {"launches": v["launches"], "total_ms": v["total_ms"]} for k, v in trace.items()},
                 "clocks": clk, "sanity_decrypt": check}
         print(json.dumps(line))
@@ -614,31 +817,87 @@ def main():
     return 0
 
 
-# Register-only, dependency-free butterfly probes on B300 (one full wave,
-# 0.1-0.2 s per run, clocks 1950-2032 MHz): 750.7 G 64-bit Harvey/Shoup
-# butterflies/s and 3030 G 32-bit ones/s, i.e. 2.50 and 10.07 per SM per clock
-# taken at the 2032 MHz maximum (so the peaks below are not understated).
-BFLY64_PER_SM_CLK = 2.50
-BFLY32_PER_SM_CLK = 10.07
-# Measured HBM copy bandwidth (STREAM-style copy) from MEASURED_PEAKS.json
-# beside this file, else the same figure as recorded when this was written.
-def _hbm_gbps() -> float:
+# Measured HBM copy bandwidth (STREAM-style copy) and cuBLAS bf16 rates from
+# MEASURED_PEAKS.json beside this file, else the figures recorded when this
+# was written.
+def _measured_peaks() -> dict:
     try:
         with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
-            return float(json.load(f)["hbm_gbs"])
-    except (OSError, KeyError, ValueError):
-        return 6505.6
+            return json.load(f)
+    except (OSError, ValueError):
+        return {}
 
 
-HBM_GBPS = _hbm_gbps()
+_PEAKS = _measured_peaks()
+HBM_GBPS = float(_PEAKS.get("hbm_gbs", 6505.6))
+BF16_TFLOPS = float(_PEAKS.get("bf16_tflops", 1780.9))
+BF16_TFLOPS_SUSTAINED = float(_PEAKS.get("bf16_tflops_sustained", 1397.9))
 
 
-def alu_peak_gmodmul(modulus: str) -> float:
-    """Peak coefficient modmuls/s: one 64-bit Shoup butterfly per coefficient
-    modmul in the 64-bit form; two 32-bit ones (one per residue) in the RNS form."""
-    if modulus == "rns":
-        return 148 * BFLY32_PER_SM_CLK / 2 * 2.032
-    return 148 * BFLY64_PER_SM_CLK * 2.032
+def alu_probe(phe, device: int, modulus: str, reps: int = 3) -> dict:
+    """The ALU peak, measured in this process by the library's butterfly probe
+    (phe_probe_alu: register-only Gentleman-Sande butterflies with the hot
+    path's own arithmetic, at lwedot's occupancy), best of `reps`.  One
+    coefficient modmul is two 32-bit butterflies in the RNS form (one per
+    residue) and one 64-bit butterfly in the prime form."""
+    form = 0 if modulus == "rns" else 1
+    per_s = max(phe.phe_probe_alu(device, form) for _ in range(reps))
+    return {"bfly_per_s": per_s, "gmodmul": per_s / (2.0 if modulus == "rns" else 1.0) / 1e9,
+            "bfly": "32-bit" if modulus == "rns" else "64-bit"}
+
+
+def unit_bound_gmodmul(sm_mhz: float, sms: int = 148) -> float:
+    """Unit-count bound of the RNS form in coefficient modmuls/s: 64 FMA-heavy
+    lanes per SM execute every 32-bit integer multiply; a 32-bit Shoup
+    butterfly needs two low multiplies and one high multiply at half rate,
+    4 lane-slots, so 16 butterflies per SM per clock, two per coefficient."""
+    return sms * 8 * sm_mhz / 1e3
+
+
+def tensor_probe(phe, device: int, reps: int = 3) -> float:
+    """tcgen05.mma kind::f16 rate (bf16, fp32 accumulate, M 128 N 256 K 16)
+    measured in this process, TFLOP/s, best of `reps`."""
+    return max(phe.phe_probe_tensor(device) for _ in range(reps)) / 1e12
+
+
+_I8_SNIPPET = r"""
+#include <cstdint>
+__global__ void k(uint32_t d, uint64_t a, uint64_t b, uint32_t i) {
+  asm volatile("{\n .reg .pred p;\n setp.ne.u32 p, %4, 0;\n"
+               " tcgen05.mma.cta_group::1.kind::KIND [%0], %1, %2, %3, p;\n}\n"
+               :: "r"(d), "l"(a), "l"(b), "r"(i), "r"(i));
+}
+"""
+
+
+def tensor_kind_check(kind: str, arch: str = "103a") -> str:
+    """Whether ptxas accepts tcgen05.mma of this kind for sm_<arch>: compiles
+    a one-instruction kernel with the toolchain of this machine."""
+    nvcc = os.environ.get("NVCC", "/usr/local/cuda/bin/nvcc")
+    with tempfile.TemporaryDirectory() as d:
+        src = os.path.join(d, "k.cu")
+        with open(src, "w") as f:
+            f.write(_I8_SNIPPET.replace("KIND", kind))
+        try:
+            r = subprocess.run([nvcc, "-gencode", f"arch=compute_{arch},code=sm_{arch}", "-c", src, "-o",
+                                os.path.join(d, "k.o")], capture_output=True, text=True, timeout=120)
+        except (OSError, subprocess.TimeoutExpired) as e:
+            return f"not checked: {e}"
+    if r.returncode == 0:
+        return f"kind::{kind} accepted by ptxas for sm_{arch}"
+    msg = next((ln.split("error", 1)[1].strip(" :") for ln in (r.stdout + r.stderr).splitlines()
+                if "error" in ln and "not supported" in ln), (r.stdout + r.stderr).strip().splitlines()[-1:])
+    return f"kind::{kind} refused by ptxas for sm_{arch}: {msg}"
+
+
+def int8_kind_check() -> str:
+    return tensor_kind_check("i8")
+
+
+def body_flops_per_token(wl) -> int:
+    """Algorithmic flops of the bodies in the digit-GEMM form: 2 per MAC, one
+    MAC per (row, column) per base-256 digit, 8 digits per word."""
+    return sum(2 * 8 * rows * cols for _, _, _, rows, cols, _ in matmuls(wl))
 
 
 def sanity_decrypt(wl, mm, inputs, keys, outs, S, T, chunk):
@@ -724,6 +983,54 @@ def measure_serving(phe, ctx, weights, wl, inputs, keys, n_requests, rate, T_ava
                      "by the server's busy time (idle waits between arrivals included); ") +
                     "tokens/s are tokens of single-projection requests; layer_equiv divides (token,row) items by "
                     "the 44032 of a layer token"}
+
+
+def measure_serving_plain(phe, ctx, weights, wl, inputs, keys, n_stream, n_requests, T_avail, stream, chunk=32):
+    """The plain per-call form on the first n_requests of the same request
+    stream as an n_stream-request measure_serving run (same seed and draws, so
+    the same projections, directions and token counts): every
+    request already waiting, served one after another by phe_matmul calls of
+    `chunk` tokens (the server's chunk size), results dropped.  Device time
+    over the whole stream gives its throughput beside the served form's."""
+    import torch
+    r = synth.rng(synth.SEED_ARRIVALS)
+    r.exponential(1.0, size=n_stream)  # the draws of the arrival gaps of an n_stream-request run
+    projs = r.integers(0, len(wl.projections), size=n_stream)
+    dirs = r.integers(0, 2, size=n_stream)
+    toks = r.integers(64, 2049, size=n_stream)
+    N = wl.ring.N
+    max_rows = max(max(d_in, d_out) for _, d_in, d_out in wl.projections)
+    om = torch.empty((chunk, max_rows, N), dtype=torch.int32, device=stream.device)
+    ob = torch.empty((chunk, max_rows), dtype=torch.int32, device=stream.device)
+    items = tokens = 0
+
+    def run():
+        for k in range(n_requests):
+            pi, d, Tk = int(projs[k]), ("fwd", "bwd")[int(dirs[k])], int(toks[k])
+            A, B, _ = inputs[keys[(pi, d)][0]]
+            off = (k * 97) % max(1, T_avail - Tk + 1)
+            for t0 in range(0, Tk, chunk):
+                tn = min(chunk, Tk - t0)
+                phe.phe_matmul(ctx, weights[pi], phe.PHE_FWD if d == "fwd" else phe.PHE_BWD, tn,
+                               A[off + t0:off + t0 + tn], B[off + t0:off + t0 + tn], om, ob, phe.PHE_OUT_SWITCHED,
+                               stream)
+    for k in range(n_requests):
+        pi, d, Tk = int(projs[k]), ("fwd", "bwd")[int(dirs[k])], int(toks[k])
+        name, d_in, d_out = wl.projections[pi]
+        items += Tk * (d_out if d == "fwd" else d_in)
+        tokens += Tk
+    a = torch.cuda.Event(enable_timing=True)
+    b = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    a.record(stream)
+    run()
+    b.record(stream)
+    torch.cuda.synchronize()
+    sec = a.elapsed_time(b) / 1e3
+    per_layer_token = sum(rows for _, _, _, rows, _, _ in matmuls(wl))
+    return {"requests": n_requests, "form": f"plain per-call, {chunk}-token phe_matmul calls, FIFO, all waiting",
+            "served_req_s": n_requests / sec, "served_tokens_s": tokens / sec,
+            "layer_equiv_tokens_s": items / sec / per_layer_token, "device_s": sec}
 
 
 def measure_small_batches(phe, ctx, weights, mm, keys, inputs, outs, sizes, stream, side, reps=20):
@@ -845,7 +1152,7 @@ def client_ksk(phe, ctx, S, N, q, base_log, gen, dev):
     return KA.cpu().numpy().view(np.uint64), KB.cpu().numpy().view(np.uint64)
 
 
-def measure_packed(phe, ctx, weights, wl, mm, keys, inputs, S, q, tokens, stream, gen, dev):
+def measure_packed(phe, ctx, weights, wl, mm, keys, inputs, S, q, tokens, stream, gen, dev, alu):
     """The whole server path of the paper, Eq. (LWEdot) then the packing of
     Eq. (pack_rotate) and the switch: every product of the layer through
     phe_matmul_packed on `tokens` resident tokens (device-timed), then the
@@ -897,7 +1204,7 @@ def measure_packed(phe, ctx, weights, wl, mm, keys, inputs, S, q, tokens, stream
         pack_roof = []
         if kern.get("input_ntt_kernel"):
             ach = bfly / (kern["input_ntt_kernel"] / 1e3) / 1e9
-            peak = 148 * BFLY32_PER_SM_CLK * 2.032
+            peak = alu["bfly_per_s"] / 1e9  # this run's probe (32-bit butterflies)
             pack_roof.append({"kernel": "input_ntt_kernel (digit rows)", "bound": "alu", "unit": "G 32-bit bfly/s",
                               "achieved": ach, "peak": peak, "frac": ach / peak,
                               "note": "the kernel time also holds the 16 input-mask transforms, < 1%"})

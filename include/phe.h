@@ -133,8 +133,16 @@ uint64_t phe_weights_device_bytes(const phe_weights* w);
  * of input ciphertexts (d_in_mask, d_in_body: [T][L][N] uint64) write the T x
  * rows LWE ciphertexts: masks to d_out_mask [T][rows][N] and bodies to
  * d_out_body [T][rows], as uint32 mod 2^k (flags = PHE_OUT_SWITCHED) or as
- * uint64 mod q (flags = PHE_OUT_RAW).  T = 0 is a no-op.  Uses stream-ordered
- * scratch of T*L*N*8 bytes (allocated and freed on `stream`).  Errors:
+ * uint64 mod q (flags = PHE_OUT_RAW).  T = 0 is a no-op.
+ *
+ * The masks run through negacyclic NTTs on the integer ALUs; the bodies
+ * b'_tj = sum_k W[j,k] B_t[k] (mod q) run on the tensor cores as an exact
+ * bf16 digit GEMM (tcgen05.mma, fp32 accumulation in chunks of 1024 columns,
+ * recombined mod q).  Uses stream-ordered scratch of T*L*N*8 bytes
+ * (transformed masks) plus 16*T*cols bytes rounded up (the bodies' digit
+ * rows), allocated and freed on `stream`.  Every wait inside the tensor-core
+ * kernel is bounded: a wait that runs out sets a bit in the context's status
+ * word (phe_ctx_status) and that launch's bodies are not written.  Errors:
  * PHE_EINVAL (shapes, null pointers, direction not uploaded), PHE_ENOMEM,
  * PHE_ECUDA. */
 phe_status phe_matmul(phe_ctx* ctx, const phe_weights* w, int dir, uint32_t T, const uint64_t* d_in_mask,
@@ -193,15 +201,51 @@ typedef struct phe_trace_entry {
 phe_status phe_trace_enable(phe_ctx* ctx, int on);
 phe_status phe_trace_read(phe_ctx* ctx, phe_trace_entry* out, uint32_t cap, uint32_t* n_out);
 
-/* Client-side helper for tests and benchmarks (not part of the server
- * path, which never holds the key): RLWE encryption of T int8 vectors of
- * length d (Sec. 3.1, blocks of Sec. 4.3.1):
+/* Status word of the context's kernels with bounded waits (the body GEMM):
+ * 0 when every wait completed since the last clear; otherwise bit 0 = a
+ * tensor-memory operand load, bit 1 = an MMA issue wait, bit 2 = the
+ * epilogue's wait, bit 3 = draining copies in flight timed out, and the
+ * outputs of that launch are not valid.  Synchronises the device first.
+ * clear != 0 resets the word.  Errors: PHE_EINVAL, PHE_ECUDA. */
+phe_status phe_ctx_status(phe_ctx* ctx, uint32_t* flags, int clear);
+
+/* Peak probes, run on `device` in the calling process (blocking, a few ms):
+ *   phe_probe_alu     register-only Gentleman-Sande butterflies with the
+ *                     hot path's own arithmetic, 8 independent chains per
+ *                     thread at lwedot's occupancy; form 0 = 32-bit residue
+ *                     butterflies (RNS form), 1 = 64-bit butterflies.
+ *                     *per_s = butterflies per second (iters 0 = 4096).
+ *   phe_probe_tensor  back-to-back tcgen05.mma kind::f16 (bf16, fp32
+ *                     accumulate, M 128, N 256, K 16), one CTA per SM;
+ *                     *flops_per_s = 2 M N K per MMA per second
+ *                     (iters 0 = 20000 rounds of 4 MMAs).
+ * They give the denominators of the benchmark's rooflines.  Errors:
+ * PHE_EINVAL, PHE_ETIMEOUT (an MMA wait ran out), PHE_ECUDA. */
+phe_status phe_probe_alu(int device, int form, uint32_t iters, double* per_s);
+phe_status phe_probe_tensor(int device, uint32_t iters, double* flops_per_s);
+
+#ifdef PHE_TESTING
+/* ---- Test library only (libphe_test.so, built with -DPHE_TESTING) -------
+ * Client-side helpers for tests and benchmarks.  The server never holds the
+ * key (Sec. 5): the production libphe.so does not export these calls.
+ *
+ * phe_test_keygen: a secret key of N coefficients (the context's ring) to
+ * host memory h_sk [N] int8, from a 64-bit seed (SplitMix64): kind
+ * PHE_KEY_TERNARY draws from {-1, 0, 1}, PHE_KEY_BINARY from {0, 1} (Sec.
+ * 3.1 uses a binary key; the workloads here a ternary one).  Host only.
+ *
+ * phe_client_encrypt: RLWE encryption of T int8 vectors of length d (Sec.
+ * 3.1, blocks of Sec. 4.3.1):
  *     B_ti = A_ti * S + E_ti + delta * x_hat_ti  (mod q)
  * d_A [T][L][N] masks in [0, q), d_S [N] int8 key (binary or ternary),
  * d_E [T][L][N] int32 noise, d_x [T][d] int8 messages; writes d_B [T][L][N].
- * Errors: PHE_EINVAL, PHE_ENOMEM, PHE_ECUDA. */
+ * Errors: PHE_EINVAL, PHE_ENOMEM, PHE_ECUDA, PHE_EUNSUPPORTED (q = 2^K). */
+#define PHE_KEY_BINARY 0u
+#define PHE_KEY_TERNARY 1u
+phe_status phe_test_keygen(phe_ctx* ctx, uint64_t seed, uint32_t kind, int8_t* h_sk);
 phe_status phe_client_encrypt(phe_ctx* ctx, uint32_t T, uint32_t d, const uint64_t* d_A, const int8_t* d_S,
                               const int32_t* d_E, const int8_t* d_x, uint64_t delta, uint64_t* d_B, void* stream);
+#endif /* PHE_TESTING */
 
 /* ---- Batched form ------------------------------------------------------
  * Many products at once -- e.g. every projection of a layer in both
@@ -282,7 +326,22 @@ phe_status phe_autotune(phe_ctx* ctx, const phe_job* jobs, uint32_t n_jobs, uint
  * are kept in flight.  Results of a chunk are copied to the request's host
  * buffers, or dropped when none are given (benchmarking).  Every host wait
  * is bounded by `wait_timeout_ms` (PHE_ETIMEOUT); a failed iteration fails
- * the server and every unfinished request. */
+ * the server and every unfinished request.
+ *
+ * Admission is FIFO by arrival; a request whose next chunk does not fit the
+ * budget may be passed over by younger, smaller ones for at most 4
+ * iterations in a row, after which nothing younger is admitted until its
+ * chunk fits, so no request waits without bound under sustained load.
+ *
+ * Failure: after a failed launch or a wait that ran out, no request is
+ * admitted any more, and unfinished requests are reported failed (poll -1,
+ * wait returns the server's error) only once the work already in flight on
+ * the device has drained -- until then that work may still read a request's
+ * inputs and write its host buffers.  The server waits for the drain at
+ * most max(4 * wait_timeout_ms, 3000) ms; if the device has not drained by
+ * then, those requests stay pending (waits time out), and their input and
+ * output buffers must stay valid until phe_server_destroy returns, which
+ * synchronises the server's stream. */
 typedef struct phe_server_config {
     uint64_t mem_budget_bytes;        /* device bytes for in-flight chunk buffers */
     uint32_t chunk_tokens;            /* tokens of one request per iteration */
@@ -326,7 +385,8 @@ phe_status phe_server_create(phe_ctx* ctx, const phe_server_config* cfg, phe_ser
 phe_status phe_server_submit(phe_server* srv, const phe_request* req, uint64_t* id);
 /* Wait at most timeout_ms for a request (PHE_ETIMEOUT otherwise). */
 phe_status phe_server_wait(phe_server* srv, uint64_t id, uint32_t timeout_ms, double* latency_ms);
-/* done: 1 complete, 0 pending, -1 failed. */
+/* done: 1 complete, 0 pending (or failing, with work still in flight),
+ * -1 failed (no work in flight reads or writes its buffers any more). */
 phe_status phe_server_poll(phe_server* srv, uint64_t id, int* done, double* latency_ms);
 phe_status phe_server_stats(phe_server* srv, phe_serving_stats* out);
 /* Drains the admitted and waiting requests, then stops the worker. */
@@ -465,9 +525,14 @@ phe_status phe_matmul_wire(phe_ctx* ctx, const phe_weights* w, const phe_ksk* k,
  * (at N = 4096, L = 1: up to 512 tokens per call).  It calls no cudaMalloc,
  * cudaFree or other allocating routine and records no trace events.
  *
- * The first call on a device looks up the array's device address
- * (cudaGetSymbolAddress, once per device, with that device current); make
- * that first call before any stream capture.  All calls share the one array
+ * phe_ctx_create loads the array on its device (with that device current),
+ * so its memory is reserved when a context is set up, never inside this
+ * call.  Each call looks up the array's address in the current CUDA context
+ * (cudaGetSymbolAddress, which allocates nothing once the array is loaded),
+ * so a device reset or another context does not leave a stale address.
+ * Unlike phe_matmul, the bodies are computed by a dot product fused into the
+ * mask kernel (no tensor-core digit rows, which would need more scratch);
+ * the results are the same bit for bit.  All calls share the one array
  * and it keeps the last call's contents (each call overwrites every word it
  * reads, so nothing needs clearing): calls whose work overlaps on the GPU --
  * concurrent streams, or several host threads -- race on it and must be

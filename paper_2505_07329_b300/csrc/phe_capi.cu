@@ -164,36 +164,45 @@ cudaError_t matmul_device(phe_ctx* c, const phe_weights::Dir& D, u32 T, const u6
                           void* out_mask, void* out_body, int mode, cudaStream_t s, const u64* in_seeds = nullptr) {
   const u32 N = c->prm.N;
   Span call(c, phe::kKCall, s);
-  u64* ahat = nullptr;
-  cudaError_t e = phe::ctx_malloc_async(c, &ahat, (size_t)T * D.L * N * sizeof(u64), s);
+  phe::LweJobTable jt{};
+  jt.n = 1;
+  phe::LweJob& J = jt.j[0];
+  J.what = D.what;
+  J.out = out_mask;
+  J.wrow = D.wrow;
+  J.wbf = D.wbf;
+  J.bin = in_body;
+  J.out_body = out_body;
+  J.rows = D.rows;
+  J.cols = D.cols;
+  J.T = T;
+  J.L = D.L;
+  J.tok_chunk = phe::kDefaultTokChunk;
+  phe::set_lwe_tiles(J, c->logn);
+  jt.prefix[0] = 0;
+  jt.prefix[1] = J.tiles;
+  // one scratch allocation: A_hat, then the bodies' digit rows
+  const size_t ahat_bytes = ((size_t)T * D.L * N * sizeof(u64) + 255) & ~(size_t)255;
+  char* scratch = nullptr;
+  cudaError_t e = phe::ctx_malloc_async(c, &scratch, ahat_bytes + phe::body_scratch_bytes(jt), s);
   if (e != cudaSuccess) return e;
+  u64* ahat = reinterpret_cast<u64*>(scratch);
+  J.ahat = ahat;
+  phe::assign_body_scratch(jt, scratch + ahat_bytes);
   {
     Span sp(c, phe::kKInputNtt, s);
     phe::NttJob nj{in_mask, ahat, T * D.L, in_seeds};
     e = phe::launch_input_ntt(c, &nj, 1, s);
   }
   if (e == cudaSuccess) {
-    phe::LweJobTable jt{};
-    jt.n = 1;
-    phe::LweJob& J = jt.j[0];
-    J.what = D.what;
-    J.ahat = ahat;
-    J.out = out_mask;
-    J.wrow = D.wrow;
-    J.bin = in_body;
-    J.out_body = out_body;
-    J.rows = D.rows;
-    J.cols = D.cols;
-    J.T = T;
-    J.L = D.L;
-    J.tok_chunk = phe::kDefaultTokChunk;
-    phe::set_lwe_tiles(J, c->logn);
-    jt.prefix[0] = 0;
-    jt.prefix[1] = J.tiles;
-    Span sp(c, phe::kKLwedot, s);
-    e = phe::launch_lwedot(c, jt, mode, 0, s);
+    Span sp(c, phe::kKBodyGemm, s);
+    e = phe::launch_body(c, jt, mode == phe::kOutRaw, c->rc, c->rk, s);
   }
-  cudaError_t ef = cudaFreeAsync(ahat, s);
+  if (e == cudaSuccess) {
+    Span sp(c, phe::kKLwedot, s);
+    e = phe::launch_lwedot(c, jt, mode | phe::kBodyGemm, 0, s);
+  }
+  cudaError_t ef = cudaFreeAsync(scratch, s);
   return e != cudaSuccess ? e : ef;
 }
 
@@ -331,6 +340,15 @@ phe_status phe_ctx_create(const phe_params* prm, int device, phe_ctx** out) {
       return cuda_fail(e, "cudaMemPoolCreate");
     }
   }
+  e = cudaMalloc(&c->d_status, sizeof(uint32_t));
+  if (e == cudaSuccess) e = cudaMemset(c->d_status, 0, sizeof(uint32_t));
+  if (e == cudaSuccess) e = phe::noalloc_setup();
+  if (e != cudaSuccess) {
+    cudaFree(c->d_status);
+    cudaMemPoolDestroy(c->pool);
+    delete c;
+    return cuda_fail(e, "phe_ctx_create: status word");
+  }
 
   phe::RingConst& rc = c->rc;
   rc.q = q;
@@ -364,12 +382,12 @@ phe_status phe_ctx_create(const phe_params* prm, int device, phe_ctx** out) {
   if (rns_modulus) {
     psi1 = (u32)primitive_root_2n(p1, N);
     psi2 = (u32)primitive_root_2n(p2, N);
-    if (!psi1 || !psi2) { cudaMemPoolDestroy(c->pool); delete c; return fail(PHE_EINVAL, "no primitive 2N-th root of unity mod p1 or p2"); }
+    if (!psi1 || !psi2) { cudaFree(c->d_status); cudaMemPoolDestroy(c->pool); delete c; return fail(PHE_EINVAL, "no primitive 2N-th root of unity mod p1 or p2"); }
     if (!pow2) psi = crt2(psi1, p1, psi2, p2);
   } else {
     psi = primitive_root_2n(q, N);
   }
-  if (!psi && !pow2) { cudaMemPoolDestroy(c->pool); delete c; return fail(PHE_EINVAL, "no primitive 2N-th root of unity found for q"); }
+  if (!psi && !pow2) { cudaFree(c->d_status); cudaMemPoolDestroy(c->pool); delete c; return fail(PHE_EINVAL, "no primitive 2N-th root of unity found for q"); }
 
   // 64-bit tables mod q (none for q = 2^k: everything runs through p1 p2)
   phe_status st = pow2 ? PHE_OK : build_tables(c, [&](u32 br, bool inverse) -> ulonglong2 {
@@ -413,6 +431,7 @@ phe_status phe_ctx_create(const phe_params* prm, int device, phe_ctx** out) {
   if (st != PHE_OK) {
     free_tables(c->tab);
     free_tables(c->tab32);
+    cudaFree(c->d_status);
     cudaMemPoolDestroy(c->pool);
     delete c;
     return st;
@@ -434,6 +453,7 @@ void phe_ctx_destroy(phe_ctx* c) {
   for (auto e : c->tracer.pool) cudaEventDestroy(e);
   free_tables(c->tab);
   free_tables(c->tab32);
+  cudaFree(c->d_status);
   // a pool with frees still in flight is released once they complete
   if (c->pool) cudaMemPoolDestroy(c->pool);
   delete c;
@@ -486,10 +506,13 @@ phe_status phe_weights_upload(phe_ctx* c, const int8_t* h_W, uint32_t d_out, uin
     const size_t what_bytes = (size_t)D.rows * D.L * N * sizeof(ulonglong2);
     if ((e = cudaMalloc(&D.what, what_bytes)) != cudaSuccess) break;
     if ((e = cudaMalloc(&D.wrow, wbytes)) != cudaSuccess) break;
-    w->bytes += what_bytes + wbytes;
+    const size_t bf_bytes = (size_t)D.rows * phe::digit_pitch(D.cols) * 2;
+    if ((e = cudaMalloc(&D.wbf, bf_bytes)) != cudaSuccess) break;
+    w->bytes += what_bytes + wbytes + bf_bytes;
     const int8_t* src = dir == PHE_FWD ? h_W : WT.data();
     if ((e = cudaMemcpyAsync(D.wrow, src, wbytes, cudaMemcpyHostToDevice, s)) != cudaSuccess) break;
     if ((e = phe::launch_weight_ntt(c, D.wrow, D.rows, D.cols, D.cols, 1, D.L, 1, D.what, s)) != cudaSuccess) break;
+    if ((e = phe::launch_weights_bf16(c, D.wrow, D.rows, D.cols, D.wbf, s)) != cudaSuccess) break;
   }
   if (e == cudaSuccess) e = cudaStreamSynchronize(s);
   if (e != cudaSuccess) {
@@ -506,6 +529,7 @@ void phe_weights_free(phe_weights* w) {
   for (auto& D : w->dir) {
     cudaFree(D.what);
     cudaFree(D.wrow);
+    cudaFree(D.wbf);
   }
   delete w;
 }
@@ -693,57 +717,6 @@ phe_status phe_modswitch(phe_ctx* c, const uint64_t* d_in, uint32_t* d_out, size
   Span sp(c, phe::kKModswitch, (cudaStream_t)stream);
   cudaError_t e = phe::launch_modswitch(c, reinterpret_cast<const u64*>(d_in), d_out, n, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "phe_modswitch launch");
-  return PHE_OK;
-}
-
-phe_status phe_client_encrypt(phe_ctx* c, uint32_t T, uint32_t d, const uint64_t* d_A, const int8_t* d_S,
-                              const int32_t* d_E, const int8_t* d_x, uint64_t delta, uint64_t* d_B, void* stream) {
-  if (!c) return fail(PHE_EINVAL, "phe_client_encrypt: null context");
-  if (c->pow2) return fail(PHE_EUNSUPPORTED, "phe_client_encrypt: no NTT mod q = 2^%u (encrypt on the client)",
-                           c->rk.p2k);
-  if (T == 0) return PHE_OK;
-  if (d < 1 || d > 16384) return fail(PHE_EINVAL, "phe_client_encrypt: d=%u not in [1, 16384]", d);
-  if (!d_A || !d_S || !d_E || !d_x || !d_B) return fail(PHE_EINVAL, "phe_client_encrypt: null buffer");
-  if (delta >= c->prm.q) return fail(PHE_EINVAL, "phe_client_encrypt: delta must be < q");
-  DeviceGuard g(c->device);
-  if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
-  cudaStream_t s = (cudaStream_t)stream;
-  const u32 N = c->prm.N;
-  const u32 L = (d + N - 1) / N;
-  const u32 blocks = T * L;
-  u64* ahat = nullptr;
-  ulonglong2* shat = nullptr;
-  cudaError_t e = phe::ctx_malloc_async(c, &ahat, (size_t)blocks * N * sizeof(u64), s);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaMallocAsync(A_hat)");
-  e = phe::ctx_malloc_async(c, &shat, (size_t)N * sizeof(ulonglong2), s);
-  if (e == cudaSuccess) {
-    phe::NttJob nj{reinterpret_cast<const u64*>(d_A), ahat, blocks};
-    e = phe::launch_input_ntt(c, &nj, 1, s, /*force64=*/true);
-  }
-  if (e == cudaSuccess) e = phe::launch_weight_ntt(c, d_S, 1, N, 0, 1, 1, 0, shat, s, /*force64=*/true);
-  if (e == cudaSuccess) {
-    phe::LweJobTable jt{};
-    jt.n = 1;
-    phe::LweJob& J = jt.j[0];
-    J.what = shat;
-    J.ahat = ahat;
-    J.out = d_B;
-    J.err = d_E;
-    J.msg = d_x;
-    J.delta = delta;
-    J.delta_p = shoup(delta, c->prm.q);
-    J.rows = 1;
-    J.T = blocks;
-    J.L = 1;
-    J.tok_chunk = 16;
-    J.msg_d = d;
-    phe::set_lwe_tiles(J, c->logn);
-    jt.prefix[1] = J.tiles;
-    e = phe::launch_lwedot(c, jt, phe::kOutRing, 0, s, /*force64=*/true);
-  }
-  if (shat) cudaFreeAsync(shat, s);
-  cudaFreeAsync(ahat, s);
-  if (e != cudaSuccess) return cuda_fail(e, "phe_client_encrypt launch");
   return PHE_OK;
 }
 

@@ -20,6 +20,12 @@ constexpr int kMaxJobs = 32;      // jobs in one batched launch (passed by value
 // of the autotuner's best and 4% above 2-token tiles).
 constexpr unsigned kDefaultTokChunk = 8;
 constexpr int kMinLogN = 8;
+// Columns per exact fp32 accumulation of the body GEMM: |w beta| <= 127*128,
+// so a chunk's partial sums stay below 2^24 (phe_body.cu).
+constexpr u32 kBodyChunk = 1024;
+// Row pitch (elements) of the bf16 weight and digit rows: 16-byte aligned rows for TMA.
+inline u32 digit_pitch(u32 cols) { return (cols + 7) & ~7u; }
+inline size_t digit_bytes(u32 T, u32 cols) { return (size_t)T * 8 * digit_pitch(cols) * 2; }
 constexpr int kMaxLogN = 13;
 
 // One matrix product of the hot path, as the lwedot kernel sees it.
@@ -35,6 +41,13 @@ struct LweJob {
   u64 delta, delta_p;       // client encryption only: delta and its Shoup quotient
   u32 rows, cols, T, L, tok_chunk, tiles, msg_d;
   u32 row_group;             // rows per tile (set_lwe_tiles)
+  // Bodies on the tensor cores (phe_body.cu): the direction's weights as
+  // bf16 rows [rows][digit_pitch(cols)], and scratch for the bodies' digit
+  // rows [T*8][digit_pitch(cols)] (assign_body_scratch), written by the
+  // first job of a table that reads these bodies (digits_owner).
+  const void* wbf = nullptr;
+  void* digits = nullptr;
+  u32 digits_owner = 0;
 };
 struct LweJobTable {
   u32 n;
@@ -54,19 +67,20 @@ struct NttJob {             // forward transform of T*L input blocks
 // Decomp reads) and bodies raw mod q (uint64), the inputs of the packing.
 enum OutMode : int {
   kOutSwitched = 0, kOutRaw = 1, kOutRing = 2, kOutPackIn = 3, kPow2 = 4 /* flag: q = 2^k via the RNS form */,
-  kK32 = 8 /* flag: switched outputs at q' = 2^32, the shift and mask known at compile time */
+  kK32 = 8 /* flag: switched outputs at q' = 2^32, the shift and mask known at compile time */,
+  kBodyGemm = 16 /* flag: the bodies come from the tensor-core GEMM (launch_body), not from lwedot */
 };
 
 // Kernel names for tracing; kKCall brackets a whole phe_matmul call.
 enum KernelId : int {
   kKInputNtt = 0, kKLwedot, kKModswitch, kKWeightNtt, kKExpand, kKCall, kKPlan, kKGraph,
-  kKPackDecompose, kKPackMac, kKPackFinish, kKPackCall, kKCount
+  kKPackDecompose, kKPackMac, kKPackFinish, kKPackCall, kKBodyGemm, kKCount
 };
 inline const char* kernel_name(int k) {
   static const char* names[kKCount] = {"input_ntt_kernel", "lwedot_kernel", "modswitch_kernel", "weight_ntt_kernel",
                                        "expand_masks_kernel", "phe_matmul", "phe_plan_run", "phe_plan_graph",
                                        "pack_decompose_kernel", "pack_mac_kernel", "pack_finish_kernel",
-                                       "phe_pack"};
+                                       "phe_pack", "body_gemm_kernel"};
   return (k >= 0 && k < kKCount) ? names[k] : "?";
 }
 struct TraceRec {
@@ -115,6 +129,9 @@ struct phe_ctx {
   // a call stays mapped for the next one (the device's default pool would
   // release it at every synchronization and map it again).
   cudaMemPool_t pool = nullptr;
+  // Status word the kernels with bounded waits set bits in (phe_body.cu):
+  // nonzero means a wait timed out and that launch's outputs are not valid.
+  uint32_t* d_status = nullptr;
   phe::Tracer tracer;
 };
 
@@ -124,6 +141,7 @@ struct phe_weights {
   struct Dir {
     ulonglong2* what = nullptr;  // [rows][L][N] pairs
     int8_t* wrow = nullptr;      // [rows][cols] clear weights of the direction
+    void* wbf = nullptr;         // [rows][digit_pitch(cols)] the same weights as bf16 (body GEMM)
     uint32_t rows = 0, cols = 0, L = 0;
   } dir[2];
   uint64_t bytes = 0;
@@ -185,6 +203,24 @@ cudaError_t launch_lwedot_packin(const phe_ctx* c, const LweJobTable& jt, const 
 cudaError_t launch_modswitch(const phe_ctx* c, const u64* in, u32* out, size_t n, cudaStream_t s);
 cudaError_t launch_expand_masks(const phe_ctx* c, const u64* seeds, u32 n, u64* masks, cudaStream_t s);
 int lwedot_threads(int logn);
+
+// Bodies on the tensor cores (phe_body.cu).
+// int8 rows [rows][cols] -> bf16 rows [rows][digit_pitch(cols)].
+cudaError_t launch_weights_bf16(const phe_ctx* c, const int8_t* W, u32 rows, u32 cols, void* out, cudaStream_t s);
+// Scratch bytes for the digit rows of every distinct body input of jt, and
+// the assignment of that scratch to the jobs (sets digits / digits_owner).
+size_t body_scratch_bytes(const LweJobTable& jt);
+cudaError_t assign_body_scratch(LweJobTable& jt, void* scratch);
+// Digit rows of each distinct body input, then the body GEMM of every job:
+// out_body[t][j] switched to 2^k (raw = false) or raw mod q (raw = true).
+cudaError_t launch_body(const phe_ctx* c, const LweJobTable& jt, bool raw, const RingConst& rc, const RnsConst& rk,
+                        cudaStream_t s);
+cudaError_t prepare_body_launches();
+// Loads the allocation-free entry point's scratch array on the current device (phe_noalloc.cu).
+cudaError_t noalloc_setup();
+// The full hot path of a job table: launch_body, then lwedot for the masks
+// (mode | kBodyGemm).  Jobs must carry wbf and digits.
+cudaError_t launch_lwe(const phe_ctx* c, const LweJobTable& jt, int mode, int grid_limit, cudaStream_t s);
 
 // Tiles of an lwedot job: (a group of row_group adjacent rows) x (a chunk of
 // tok_chunk tokens).  A block holds SLOTS = threads / (N/16) transforms; when

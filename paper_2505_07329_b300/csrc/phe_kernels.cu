@@ -4,8 +4,11 @@
 //   weight_ntt_kernel  w_hat_ij (reversed weight blocks, Sec. 4.3.1) -> NTT domain, x N^-1
 //   lwedot_kernel      Eq. (LWEdot): pointwise sum over blocks, inverse NTT,
 //                      SampleExtract at N-1 (index reversal), ModulusSwitch --
-//                      one fused pass per (token, row) for the masks
-//                      and the bodies b'_tj = sum_k W[j,k] B_t[k] (mod q)
+//                      one fused pass per (token, row) for the masks; the
+//                      bodies b'_tj = sum_k W[j,k] B_t[k] (mod q) come from
+//                      the tensor-core GEMM of phe_body.cu (kBodyGemm), or,
+//                      in the allocation-free entry point, from a dp4a dot
+//                      product fused into this kernel
 //   modswitch_kernel   unfused ModulusSwitch
 //   expand_masks_kernel seeded masks written out
 //
@@ -306,7 +309,7 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, lwedot_min_blocks<Shape<LOGN
   constexpr int N = S::N;
   constexpr int P = S::P;
   constexpr int NP = S::NPASS;
-  constexpr bool BODY = OUT != kOutRing;
+  constexpr bool BODY = OUT != kOutRing && (MODE & kBodyGemm) == 0;  // body fused here
   constexpr int GW = (P < 32) ? P : 32;   // lanes of one body-reduction group
   constexpr int NGRP = P / GW;            // groups per transform
   extern __shared__ u64 smem[];
@@ -604,7 +607,8 @@ cudaError_t launch_weight_ntt(const phe_ctx* c, const int8_t* W, u32 rows, u32 c
 }
 
 template <int LOGN, int MODE, bool RNS>
-static cudaError_t lwedot_impl(const phe_ctx* c, const LweJobTable& jt, int grid_limit, cudaStream_t s) {
+static cudaError_t lwedot_impl(const phe_ctx* c, const LweJobTable& jt, int grid_limit, const RingConst& rc,
+                               const RnsConst& rk, cudaStream_t s) {
   using S = Shape<LOGN>;
   const size_t smem = (size_t)S::SLOTS * S::PADN * sizeof(u64);
   cudaError_t e = set_smem(lwedot_kernel<LOGN, MODE, RNS>, smem);
@@ -613,83 +617,85 @@ static cudaError_t lwedot_impl(const phe_ctx* c, const LweJobTable& jt, int grid
   if (total == 0) return cudaSuccess;
   u32 grid = total;
   if (grid_limit > 0 && grid > (u32)grid_limit) grid = (u32)grid_limit;
-  lwedot_kernel<LOGN, MODE, RNS><<<grid, S::TPB, smem, s>>>(jt, c->rc, c->rk, tw0_of(c, RNS, true),
-                                                            twc_of(c, RNS, true));
+  lwedot_kernel<LOGN, MODE, RNS><<<grid, S::TPB, smem, s>>>(jt, rc, rk, tw0_of(c, RNS, true), twc_of(c, RNS, true));
   return cudaGetLastError();
+}
+
+// The instantiated (mode, form) pairs.  Bodies fused in lwedot (no kBodyGemm)
+// serve the allocation-free entry point; every other call takes its bodies
+// from the tensor-core GEMM.
+#define PHE_LWEDOT_MODES(X)                                                                           \
+  X(kOutSwitched, false) X(kOutRaw, false) X(kOutRing, false) X(kOutSwitched, true)                  \
+  X(kOutSwitched | kK32, true) X(kOutRaw, true) X(kOutSwitched | kPow2, true) X(kOutRaw | kPow2, true) \
+  X(kOutSwitched | kBodyGemm, false) X(kOutRaw | kBodyGemm, false) X(kOutSwitched | kBodyGemm, true) \
+  X(kOutSwitched | kK32 | kBodyGemm, true) X(kOutRaw | kBodyGemm, true)                               \
+  X(kOutSwitched | kPow2 | kBodyGemm, true) X(kOutRaw | kPow2 | kBodyGemm, true)                      \
+  X(kOutPackIn | kBodyGemm, false) X(kOutPackIn | kBodyGemm, true) X(kOutPackIn | kPow2 | kBodyGemm, true)
+
+template <int LOGN>
+static cudaError_t lwedot_dispatch(const phe_ctx* c, const LweJobTable& jt, int mode, bool rns, int grid_limit,
+                                   const RingConst& rc, const RnsConst& rk, cudaStream_t s) {
+  const int key = mode | (rns ? 64 : 0);
+#define PHE_CASE(M, R) \
+  if (key == ((M) | ((R) ? 64 : 0))) return lwedot_impl<LOGN, (M), (R)>(c, jt, grid_limit, rc, rk, s);
+  PHE_LWEDOT_MODES(PHE_CASE)
+#undef PHE_CASE
+  return cudaErrorInvalidValue;
+}
+
+// Adds the form flags (kPow2, kK32) the context implies to a call's mode
+// (kOutSwitched / kOutRaw / kOutRing / kOutPackIn, optionally | kBodyGemm).
+static int full_mode(const phe_ctx* c, int mode, bool rns) {
+  const int out = mode & 3;
+  if (rns && c->pow2) return mode | kPow2;
+  if (rns && out == kOutSwitched && c->prm.log2_qout == 32) return mode | kK32;
+  return mode;
 }
 
 cudaError_t launch_lwedot(const phe_ctx* c, const LweJobTable& jt, int mode, int grid_limit, cudaStream_t s,
                           bool force64) {
-  const bool rns = c->rns && !force64 && mode != kOutRing;
+  const bool rns = c->rns && !force64 && (mode & 3) != kOutRing;
   return by_logn(c->logn, [&](auto lg) -> cudaError_t {
-    constexpr int LOGN = decltype(lg)::value;
-    if (rns && c->pow2) {
-      if (mode == kOutSwitched) return lwedot_impl<LOGN, kOutSwitched | kPow2, true>(c, jt, grid_limit, s);
-      if (mode == kOutRaw) return lwedot_impl<LOGN, kOutRaw | kPow2, true>(c, jt, grid_limit, s);
-      return cudaErrorInvalidValue;
-    }
-    if (rns) {
-      if (mode == kOutSwitched && c->prm.log2_qout == 32)
-        return lwedot_impl<LOGN, kOutSwitched | kK32, true>(c, jt, grid_limit, s);
-      if (mode == kOutSwitched) return lwedot_impl<LOGN, kOutSwitched, true>(c, jt, grid_limit, s);
-      if (mode == kOutRaw) return lwedot_impl<LOGN, kOutRaw, true>(c, jt, grid_limit, s);
-      return cudaErrorInvalidValue;
-    }
-    if (mode == kOutSwitched) return lwedot_impl<LOGN, kOutSwitched, false>(c, jt, grid_limit, s);
-    if (mode == kOutRaw) return lwedot_impl<LOGN, kOutRaw, false>(c, jt, grid_limit, s);
-    if (mode == kOutRing) return lwedot_impl<LOGN, kOutRing, false>(c, jt, grid_limit, s);
-    return cudaErrorInvalidValue;
+    return lwedot_dispatch<decltype(lg)::value>(c, jt, full_mode(c, mode, rns), rns, grid_limit, c->rc, c->rk, s);
   });
 }
 
 cudaError_t launch_lwedot_packin(const phe_ctx* c, const LweJobTable& jt, const RingConst& rcK, const RnsConst& rkK,
                                  cudaStream_t s) {
-  const u32 total = jt.prefix[jt.n];
-  if (total == 0) return cudaSuccess;
+  if (jt.prefix[jt.n] == 0) return cudaSuccess;
+  cudaError_t e = launch_body(c, jt, /*raw=*/true, c->rc, c->rk, s);
+  if (e != cudaSuccess) return e;
   return by_logn(c->logn, [&](auto lg) -> cudaError_t {
-    constexpr int LOGN = decltype(lg)::value;
-    using S = Shape<LOGN>;
-    const size_t smem = (size_t)S::SLOTS * S::PADN * sizeof(u64);
-    if (c->rns && c->pow2) {
-      cudaError_t e = set_smem(lwedot_kernel<LOGN, kOutPackIn | kPow2, true>, smem);
-      if (e != cudaSuccess) return e;
-      lwedot_kernel<LOGN, kOutPackIn | kPow2, true><<<total, S::TPB, smem, s>>>(jt, rcK, rkK, tw0_of(c, true, true),
-                                                                               twc_of(c, true, true));
-    } else if (c->rns) {
-      cudaError_t e = set_smem(lwedot_kernel<LOGN, kOutPackIn, true>, smem);
-      if (e != cudaSuccess) return e;
-      lwedot_kernel<LOGN, kOutPackIn, true><<<total, S::TPB, smem, s>>>(jt, rcK, rkK, tw0_of(c, true, true),
-                                                                       twc_of(c, true, true));
-    } else {
-      cudaError_t e = set_smem(lwedot_kernel<LOGN, kOutPackIn, false>, smem);
-      if (e != cudaSuccess) return e;
-      lwedot_kernel<LOGN, kOutPackIn, false><<<total, S::TPB, smem, s>>>(jt, rcK, rkK, tw0_of(c, false, true),
-                                                                        twc_of(c, false, true));
-    }
-    return cudaGetLastError();
+    const int mode = kOutPackIn | kBodyGemm | ((c->rns && c->pow2) ? kPow2 : 0);
+    return lwedot_dispatch<decltype(lg)::value>(c, jt, mode, c->rns, 0, rcK, rkK, s);
   });
 }
 
+cudaError_t launch_lwe(const phe_ctx* c, const LweJobTable& jt, int mode, int grid_limit, cudaStream_t s) {
+  if (jt.prefix[jt.n] == 0) return cudaSuccess;
+  cudaError_t e = launch_body(c, jt, mode == kOutRaw, c->rc, c->rk, s);
+  if (e != cudaSuccess) return e;
+  return launch_lwedot(c, jt, mode | kBodyGemm, grid_limit, s);
+}
+
 cudaError_t prepare_launches(const phe_ctx* c) {
-  return by_logn(c->logn, [&](auto lg) -> cudaError_t {
+  cudaError_t e = by_logn(c->logn, [&](auto lg) -> cudaError_t {
     constexpr int LOGN = decltype(lg)::value;
     using S = Shape<LOGN>;
     const size_t smem = (size_t)S::SLOTS * S::PADN * sizeof(u64);
-    cudaError_t e = set_smem(input_ntt_kernel<LOGN, false>, smem);
-    if (e == cudaSuccess) e = set_smem(input_ntt_kernel<LOGN, true>, smem);
-    if (e == cudaSuccess) e = set_smem(weight_ntt_kernel<LOGN, false>, smem);
-    if (e == cudaSuccess) e = set_smem(weight_ntt_kernel<LOGN, true>, smem);
-    if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutSwitched, false>, smem);
-    if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutRaw, false>, smem);
-    if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutRing, false>, smem);
-    if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutSwitched, true>, smem);
-    if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutSwitched | kK32, true>, smem);
-    if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutRaw, true>, smem);
-    if (e == cudaSuccess) e = set_smem(input_ntt_kernel<LOGN, true, true>, smem);
-    if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutSwitched | kPow2, true>, smem);
-    if (e == cudaSuccess) e = set_smem(lwedot_kernel<LOGN, kOutRaw | kPow2, true>, smem);
-    return e;
+    cudaError_t e2 = set_smem(input_ntt_kernel<LOGN, false>, smem);
+    if (e2 == cudaSuccess) e2 = set_smem(input_ntt_kernel<LOGN, true>, smem);
+    if (e2 == cudaSuccess) e2 = set_smem(input_ntt_kernel<LOGN, true, true>, smem);
+    if (e2 == cudaSuccess) e2 = set_smem(weight_ntt_kernel<LOGN, false>, smem);
+    if (e2 == cudaSuccess) e2 = set_smem(weight_ntt_kernel<LOGN, true>, smem);
+#define PHE_PREP(M, R) \
+  if (e2 == cudaSuccess) e2 = set_smem(lwedot_kernel<LOGN, (M), (R)>, smem);
+    PHE_LWEDOT_MODES(PHE_PREP)
+#undef PHE_PREP
+    return e2;
   });
+  if (e == cudaSuccess) e = prepare_body_launches();
+  return e;
 }
 
 cudaError_t launch_expand_masks(const phe_ctx* c, const u64* seeds, u32 n, u64* masks, cudaStream_t s) {

@@ -11,7 +11,6 @@
 // engineering variant of phe_matmul.
 #include <cstdarg>
 #include <cstdio>
-#include <mutex>
 
 #include "phe_host.hpp"
 
@@ -28,23 +27,15 @@ namespace {
 constexpr size_t kScratchWords = PHE_NOALLOC_MAX_SCRATCH_BYTES / sizeof(phe::u64);
 static __device__ __align__(256) phe::u64 g_scratch[kScratchWords];
 
-constexpr int kMaxDevices = 64;
-std::mutex g_mutex;
-phe::u64* g_scratch_ptr[kMaxDevices] = {};
-
-
-// Device address of the scratch array on `device` (which must be current),
-// looked up once per device.
-phe_status scratch_for(int device, phe::u64** out) {
-  if (device < 0 || device >= kMaxDevices) return fail(PHE_EUNSUPPORTED, "phe_matmul_noalloc: device id too large");
-  std::lock_guard<std::mutex> lk(g_mutex);
-  if (!g_scratch_ptr[device]) {
-    void* p = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
-    if (e != cudaSuccess) return fail(PHE_ECUDA, "phe_matmul_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
-    g_scratch_ptr[device] = static_cast<phe::u64*>(p);
-  }
-  *out = g_scratch_ptr[device];
+// Device address of the scratch array in the current context.  Once the
+// array's module is loaded (phe_ctx_create loads it on its device), the
+// lookup allocates nothing; asking every call, rather than caching the
+// address, keeps it right after a device reset or under another context.
+phe_status scratch_address(phe::u64** out) {
+  void* p = nullptr;
+  cudaError_t e = cudaGetSymbolAddress(&p, g_scratch);
+  if (e != cudaSuccess) return fail(PHE_ECUDA, "phe_matmul_noalloc: cudaGetSymbolAddress: %s", cudaGetErrorString(e));
+  *out = static_cast<phe::u64*>(p);
   return PHE_OK;
 }
 
@@ -72,7 +63,7 @@ extern "C" phe_status phe_matmul_noalloc(phe_ctx* c, const phe_weights* w, int d
   if (e == cudaSuccess && prev != c->device) e = cudaSetDevice(c->device);
   if (e != cudaSuccess) return fail(PHE_ECUDA, "phe_matmul_noalloc: cudaSetDevice: %s", cudaGetErrorString(e));
   phe::u64* ahat = nullptr;
-  phe_status st = scratch_for(c->device, &ahat);
+  phe_status st = scratch_address(&ahat);
   if (st == PHE_OK) {
     cudaStream_t s = (cudaStream_t)stream;
     // The input transform overwrites every scratch word this call reads, so
@@ -103,3 +94,14 @@ extern "C" phe_status phe_matmul_noalloc(phe_ctx* c, const phe_weights* w, int d
   if (prev >= 0 && prev != c->device) cudaSetDevice(prev);
   return st;
 }
+
+namespace phe {
+// Loads the scratch array's module on the current device (called by
+// phe_ctx_create with the context's device current), so that the array's
+// memory is reserved at set-up and no phe_matmul_noalloc call loads code or
+// reserves memory itself.
+cudaError_t noalloc_setup() {
+  void* p = nullptr;
+  return cudaGetSymbolAddress(&p, g_scratch);
+}
+}  // namespace phe

@@ -630,15 +630,17 @@ cudaError_t matmul_packed_device(phe_ctx* c, const phe_weights::Dir& D, const ph
   const u32 N = c->prm.N, G = (D.rows + N - 1) / N;
   const size_t osz = mode == phe::kOutRaw ? sizeof(u64) : sizeof(u32);
   const u64 ahat_tok = (u64)D.L * N * sizeof(u64), atil_tok = (u64)D.rows * N * sizeof(u32);
-  const u64 tok_bytes = ahat_tok + atil_tok + (u64)D.rows * sizeof(u64);
+  const u64 dig_tok = phe::digit_bytes(1, D.cols);  // the bodies' digit rows (body GEMM)
+  const u64 tok_bytes = ahat_tok + atil_tok + (u64)D.rows * sizeof(u64) + dig_tok;
   const u32 per = (u32)std::max<u64>(1, std::min<u64>(T, kPackScratchBytes / tok_bytes));
   Span call(c, phe::kKCall, s);
   char* scratch = nullptr;
-  cudaError_t e = phe::ctx_malloc_async(c, &scratch, (size_t)per * tok_bytes, s);
+  cudaError_t e = phe::ctx_malloc_async(c, &scratch, (size_t)per * tok_bytes + 256, s);
   if (e != cudaSuccess) return e;
   u64* ahat = reinterpret_cast<u64*>(scratch);
   u32* atil = reinterpret_cast<u32*>(scratch + (size_t)per * ahat_tok);
   u64* rawb = reinterpret_cast<u64*>(scratch + (size_t)per * (ahat_tok + atil_tok));
+  char* digits = scratch + (((size_t)per * (ahat_tok + atil_tok + (u64)D.rows * sizeof(u64)) + 255) & ~(size_t)255);
   for (u32 t0 = 0; t0 < T && e == cudaSuccess; t0 += per) {
     const u32 tn = std::min(per, T - t0);
     {
@@ -655,6 +657,7 @@ cudaError_t matmul_packed_device(phe_ctx* c, const phe_weights::Dir& D, const ph
       J.ahat = ahat;
       J.out = atil;
       J.wrow = D.wrow;
+      J.wbf = D.wbf;
       J.bin = in_body + (size_t)t0 * D.L * N;
       J.out_body = rawb;
       J.rows = D.rows;
@@ -665,6 +668,7 @@ cudaError_t matmul_packed_device(phe_ctx* c, const phe_weights::Dir& D, const ph
       phe::set_lwe_tiles(J, c->logn);
       jt.prefix[0] = 0;
       jt.prefix[1] = J.tiles;
+      phe::assign_body_scratch(jt, digits);
       Span sp(c, phe::kKLwedot, s);
       e = phe::launch_lwedot_packin(c, jt, k->rcK, k->rkK, s);
     }

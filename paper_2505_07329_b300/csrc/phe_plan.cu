@@ -31,6 +31,7 @@ struct phe_plan {
   };
   std::vector<Input> inputs;
   std::vector<phe::LweJobTable> tables;
+  std::vector<void*> body_scratch;  // digit rows of the bodies, one buffer per table
   std::vector<u32> grids;
   u64 scratch_bytes = 0;
   u64 modmuls = 0;
@@ -72,6 +73,7 @@ void destroy_plan(phe_plan* p) {
     cudaEventDestroy(r.b);
   }
   for (auto& in : p->inputs) cudaFree(in.ahat);
+  for (void* b : p->body_scratch) cudaFree(b);
   delete p;
 }
 
@@ -91,21 +93,30 @@ cudaError_t run_plan(phe_plan* p, cudaStream_t s, bool trace, bool capture_event
     if (e != cudaSuccess) return e;
   }
   const int mode = p->flags == PHE_OUT_RAW ? phe::kOutRaw : phe::kOutSwitched;
-  for (size_t t = 0; t < p->tables.size(); ++t) {
+  const bool raw = mode == phe::kOutRaw;
+  // Runs one launch group (the bodies' digit rows and GEMM, or the masks'
+  // lwedot) bracketed by a span or by captured event-record nodes.
+  auto bracket = [&](int kid, auto&& launch) -> cudaError_t {
     if (trace) {
-      phe::Span sp(c, phe::kKLwedot, s);
-      e = phe::launch_lwedot(c, p->tables[t], mode, (int)p->grids[t], s);
-    } else if (capture_events) {
-      phe::TraceRec r{phe::kKLwedot, nullptr, nullptr, true};
-      e = cudaEventCreate(&r.a);
-      if (e == cudaSuccess) e = cudaEventCreate(&r.b);
-      if (e == cudaSuccess) e = cudaEventRecordWithFlags(r.a, s, cudaEventRecordExternal);
-      if (e == cudaSuccess) e = phe::launch_lwedot(c, p->tables[t], mode, (int)p->grids[t], s);
-      if (e == cudaSuccess) e = cudaEventRecordWithFlags(r.b, s, cudaEventRecordExternal);
-      if (r.a || r.b) p->graph_recs.push_back(r);
-    } else {
-      e = phe::launch_lwedot(c, p->tables[t], mode, (int)p->grids[t], s);
+      phe::Span sp(c, kid, s);
+      return launch();
     }
+    if (!capture_events) return launch();
+    phe::TraceRec r{kid, nullptr, nullptr, true};
+    cudaError_t e2 = cudaEventCreate(&r.a);
+    if (e2 == cudaSuccess) e2 = cudaEventCreate(&r.b);
+    if (e2 == cudaSuccess) e2 = cudaEventRecordWithFlags(r.a, s, cudaEventRecordExternal);
+    if (e2 == cudaSuccess) e2 = launch();
+    if (e2 == cudaSuccess) e2 = cudaEventRecordWithFlags(r.b, s, cudaEventRecordExternal);
+    if (r.a || r.b) p->graph_recs.push_back(r);
+    return e2;
+  };
+  for (size_t t = 0; t < p->tables.size(); ++t) {
+    const phe::LweJobTable& jt = p->tables[t];
+    e = bracket(phe::kKBodyGemm, [&] { return phe::launch_body(c, jt, raw, c->rc, c->rk, s); });
+    if (e == cudaSuccess)
+      e = bracket(phe::kKLwedot,
+                  [&] { return phe::launch_lwedot(c, jt, mode | phe::kBodyGemm, (int)p->grids[t], s); });
     if (e != cudaSuccess) return e;
   }
   return e;
@@ -188,6 +199,7 @@ phe_status phe_plan_create(phe_ctx* c, const phe_job* jobs, uint32_t n_jobs, uin
     J.ahat = p->inputs[k].ahat;
     J.out = j.d_out_mask;
     J.wrow = D.wrow;
+    J.wbf = D.wbf;
     J.bin = reinterpret_cast<const u64*>(j.d_in_body);
     J.out_body = j.d_out_body;
     J.rows = D.rows;
@@ -205,6 +217,19 @@ phe_status phe_plan_create(phe_ctx* c, const phe_job* jobs, uint32_t n_jobs, uin
     }
   }
   if (cur.n) p->tables.push_back(cur);
+  for (auto& t : p->tables) {
+    // digit rows of each distinct body input of the table, resident with the plan
+    void* b = nullptr;
+    const size_t bytes = phe::body_scratch_bytes(t);
+    e = cudaMalloc(&b, bytes ? bytes : 256);
+    if (e != cudaSuccess) {
+      destroy_plan(p);
+      return cuda_fail(e, "phe_plan_create: cudaMalloc(body digit rows)");
+    }
+    p->body_scratch.push_back(b);
+    p->scratch_bytes += bytes;
+    phe::assign_body_scratch(t, b);
+  }
   for (auto& t : p->tables) {
     const u32 tiles = t.prefix[t.n];
     const u32 persistent = tn.blocks_per_sm ? (u32)c->num_sms * tn.blocks_per_sm : tiles;
@@ -260,7 +285,13 @@ phe_status phe_plan_graph(phe_plan* p, void* stream) {
 
 phe_status phe_plan_info(const phe_plan* p, phe_plan_stats* st) {
   if (!p || !st) return fail(PHE_EINVAL, "phe_plan_info: null argument");
-  st->launches = (uint32_t)(p->inputs.size() + p->tables.size());
+  // per table: one digit-row kernel per distinct body input, the body GEMM, lwedot
+  uint32_t launches = (uint32_t)p->inputs.size();
+  for (const auto& t : p->tables) {
+    launches += 2;
+    for (u32 i = 0; i < t.n; ++i) launches += t.j[i].digits_owner;
+  }
+  st->launches = launches;
   st->lwedot_launches = (uint32_t)p->tables.size();
   st->scratch_bytes = p->scratch_bytes;
   st->modmuls = p->modmuls;

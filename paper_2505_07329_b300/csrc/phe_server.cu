@@ -49,7 +49,10 @@ struct Req {
   u32 rows = 0, cols = 0, L = 0;
   u32 next_token = 0;   // first token not yet scheduled
   u32 done_tokens = 0;  // tokens whose results are complete
-  int state = 0;        // 0 waiting, 1 active, 2 done, 3 failed
+  u32 skips = 0;        // iterations in a row whose budget had no room for its next chunk
+  // 0 waiting, 1 active, 2 done, 3 failed, 4 failing: the server failed but
+  // work that may still read or write this request's buffers is in flight
+  int state = 0;
   Clock::time_point t_submit, t_done;
 };
 
@@ -97,8 +100,14 @@ namespace {
 size_t chunk_bytes(const phe_server* s, const Req& q, u32 tn) {
   const size_t N = s->ctx ? s->ctx->prm.N : 1;  // the simulated backend may run without a context
   const size_t osz = s->cfg.flags == PHE_OUT_RAW ? 8 : 4;
-  return (size_t)tn * q.L * N * 8 + (size_t)tn * q.rows * N * osz + (size_t)tn * q.rows * osz;
+  // A_hat, mask and body outputs, and the bodies' digit rows for the body GEMM
+  return (size_t)tn * q.L * N * 8 + (size_t)tn * q.rows * N * osz + (size_t)tn * q.rows * osz +
+         (q.cols ? phe::digit_bytes(tn, q.cols) : 0);
 }
+
+// Iterations in a row a request may be passed over for lack of budget before
+// younger requests stop being admitted ahead of it.
+constexpr u32 kMaxSkips = 4;
 
 // Build the next iteration (called with the lock held).
 void schedule(phe_server* s, Iteration& it) {
@@ -114,11 +123,29 @@ void schedule(phe_server* s, Iteration& it) {
     if (q.next_token >= q.r.T) continue;
     const u32 tn = std::min(s->cfg.chunk_tokens, q.r.T - q.next_token);
     const size_t need = chunk_bytes(s, q, tn);
-    if (s->reserved + need > s->cfg.mem_budget_bytes) continue;  // a smaller chunk may still fit
+    if (s->reserved + need > s->cfg.mem_budget_bytes) {
+      // A smaller chunk of a younger request may still fit, unless this
+      // request has been passed over too often: then nothing younger is
+      // admitted until its chunk fits, so its wait stays bounded.
+      if (++q.skips >= kMaxSkips) break;
+      continue;
+    }
+    q.skips = 0;
     s->reserved += need;
     s->peak_reserved = std::max(s->peak_reserved, s->reserved);
     it.jobs.push_back({id, q.next_token, tn, need, (uint64_t)tn * q.rows});
     q.next_token += tn;
+  }
+}
+
+// Frees the chunk buffers of an iteration that could not be launched whole.
+void release_jobs(phe_server* s, Iteration& it) {
+  for (auto& j : it.jobs) {
+    if (j.ahat) cudaFreeAsync(j.ahat, s->stream);
+    if (j.om) cudaFreeAsync(j.om, s->stream);
+    if (j.ob) cudaFreeAsync(j.ob, s->stream);
+    j.ahat = nullptr;
+    j.om = j.ob = nullptr;
   }
 }
 
@@ -135,16 +162,16 @@ cudaError_t launch_iteration(phe_server* s, Iteration& it) {
       q = &s->reqs[j.id];
     }
     const phe_weights::Dir& D = q->r.w->dir[q->r.dir];
-    if ((e = phe::ctx_malloc_async(s->ctx, &j.ahat, (size_t)j.tn * D.L * N * 8, s->stream)) != cudaSuccess) return e;
-    if ((e = phe::ctx_malloc_async(s->ctx, &j.om, (size_t)j.tn * D.rows * N * osz, s->stream)) != cudaSuccess) return e;
-    if ((e = phe::ctx_malloc_async(s->ctx, &j.ob, (size_t)j.tn * D.rows * osz, s->stream)) != cudaSuccess) return e;
+    if ((e = phe::ctx_malloc_async(s->ctx, &j.ahat, (size_t)j.tn * D.L * N * 8, s->stream)) != cudaSuccess) break;
+    if ((e = phe::ctx_malloc_async(s->ctx, &j.om, (size_t)j.tn * D.rows * N * osz, s->stream)) != cudaSuccess) break;
+    if ((e = phe::ctx_malloc_async(s->ctx, &j.ob, (size_t)j.tn * D.rows * osz, s->stream)) != cudaSuccess) break;
     const size_t tok_words = (size_t)D.L * N;
     phe::NttJob nj{nullptr, j.ahat, j.tn * D.L};
     if (q->r.d_in_seeds)
       nj.seeds = reinterpret_cast<const u64*>(q->r.d_in_seeds) + (size_t)j.t0 * D.L;
     else
       nj.src = reinterpret_cast<const u64*>(q->r.d_in_mask) + (size_t)j.t0 * tok_words;
-    if ((e = phe::launch_input_ntt(c, &nj, 1, s->stream)) != cudaSuccess) return e;
+    if ((e = phe::launch_input_ntt(c, &nj, 1, s->stream)) != cudaSuccess) break;
     phe::LweJobTable& t = tables.back();
     phe::LweJob& J = t.j[t.n];
     J = phe::LweJob{};
@@ -152,6 +179,7 @@ cudaError_t launch_iteration(phe_server* s, Iteration& it) {
     J.ahat = j.ahat;
     J.out = j.om;
     J.wrow = D.wrow;
+    J.wbf = D.wbf;
     J.bin = reinterpret_cast<const u64*>(q->r.d_in_body) + (size_t)j.t0 * tok_words;
     J.out_body = j.ob;
     J.rows = D.rows;
@@ -165,10 +193,21 @@ cudaError_t launch_iteration(phe_server* s, Iteration& it) {
   }
   const int mode = s->cfg.flags == PHE_OUT_RAW ? phe::kOutRaw : phe::kOutSwitched;
   for (auto& t : tables) {
+    if (e != cudaSuccess) break;
     if (!t.n) continue;
     const u32 tiles = t.prefix[t.n];
     const u32 grid = s->cfg.blocks_per_sm ? std::min(tiles, (u32)c->num_sms * s->cfg.blocks_per_sm) : tiles;
-    if ((e = phe::launch_lwedot(c, t, mode, (int)grid, s->stream)) != cudaSuccess) return e;
+    // the bodies' digit rows live for this table's launches only
+    void* dig = nullptr;
+    if ((e = phe::ctx_malloc_async(s->ctx, &dig, phe::body_scratch_bytes(t), s->stream)) != cudaSuccess) break;
+    phe::assign_body_scratch(t, dig);
+    e = phe::launch_body(c, t, mode == phe::kOutRaw, c->rc, c->rk, s->stream);
+    if (e == cudaSuccess) e = phe::launch_lwedot(c, t, mode | phe::kBodyGemm, (int)grid, s->stream);
+    cudaFreeAsync(dig, s->stream);
+  }
+  if (e != cudaSuccess) {
+    release_jobs(s, it);
+    return e;
   }
   // deliver: results of each chunk to the request's host buffers (if any)
   for (auto& j : it.jobs) {
@@ -182,15 +221,14 @@ cudaError_t launch_iteration(phe_server* s, Iteration& it) {
       char* hb = static_cast<char*>(q->r.h_out_body) + (size_t)j.t0 * q->rows * osz;
       if ((e = cudaMemcpyAsync(hm, j.om, (size_t)j.tn * q->rows * N * osz, cudaMemcpyDeviceToHost, s->stream)) !=
           cudaSuccess)
-        return e;
+        break;
       if ((e = cudaMemcpyAsync(hb, j.ob, (size_t)j.tn * q->rows * osz, cudaMemcpyDeviceToHost, s->stream)) !=
           cudaSuccess)
-        return e;
+        break;
     }
-    cudaFreeAsync(j.ahat, s->stream);
-    cudaFreeAsync(j.om, s->stream);
-    cudaFreeAsync(j.ob, s->stream);
   }
+  release_jobs(s, it);
+  if (e != cudaSuccess) return e;
   if ((e = cudaEventCreateWithFlags(&it.done, cudaEventDisableTiming)) != cudaSuccess) return e;
   return cudaEventRecord(it.done, s->stream);
 }
@@ -244,16 +282,59 @@ void complete_iteration(phe_server* s, Iteration& it) {
   s->cv_done.notify_all();
 }
 
-void fail_all(phe_server* s, phe_status st) {
+// The server failed: no request is admitted or scheduled any more.  Requests
+// not yet done become "failing"; they are reported failed only once the work
+// in flight -- which may still read their inputs and write their host
+// buffers -- has drained (drain_and_fail).
+void begin_failure(phe_server* s, phe_status st) {
   std::lock_guard<std::mutex> lk(s->mu);
   s->worker_status = st;
   for (auto& kv : s->reqs)
-    if (kv.second.state < 2) {
-      kv.second.state = 3;
-      s->failed++;
-    }
+    if (kv.second.state < 2) kv.second.state = 4;
   s->waiting.clear();
   s->active.clear();
+}
+
+// Waits, with a bound, until every iteration in flight has finished on the
+// device (the simulated backend: until its finishing time), then reports
+// the failing requests failed.  If the work does not drain within the bound
+// the requests stay failing: their waits time out, and their buffers must
+// stay valid until phe_server_destroy, which synchronises the stream.
+void drain_and_fail(phe_server* s, std::deque<Iteration>& inflight) {
+  const auto limit = std::chrono::milliseconds(std::max<uint64_t>(4ull * s->cfg.wait_timeout_ms, 3000));
+  const auto deadline = Clock::now() + limit;
+  bool drained = true;
+  if (s->cfg.simulate) {
+    for (auto& it : inflight) {
+      if (it.t_ready > deadline) {
+        drained = false;
+        break;
+      }
+      std::this_thread::sleep_until(it.t_ready);
+    }
+  } else {
+    for (;;) {
+      const cudaError_t e = cudaStreamQuery(s->stream);
+      if (e != cudaErrorNotReady) break;  // drained, or the stream itself failed (nothing runs any more)
+      if (Clock::now() > deadline) {
+        drained = false;
+        break;
+      }
+      std::this_thread::sleep_for(std::chrono::microseconds(500));
+    }
+    if (drained)
+      for (auto& it : inflight)
+        if (it.done) cudaEventDestroy(it.done);
+  }
+  inflight.clear();
+  std::lock_guard<std::mutex> lk(s->mu);
+  if (drained) {
+    for (auto& kv : s->reqs)
+      if (kv.second.state == 4) {
+        kv.second.state = 3;
+        s->failed++;
+      }
+  }
   s->cv_done.notify_all();
 }
 
@@ -285,7 +366,8 @@ void worker_main(phe_server* s) {
       } else {
         cudaError_t e = launch_iteration(s, it);
         if (e != cudaSuccess) {
-          fail_all(s, fail(PHE_ECUDA, "phe_server: launch: %s", cudaGetErrorString(e)));
+          begin_failure(s, fail(PHE_ECUDA, "phe_server: launch: %s", cudaGetErrorString(e)));
+          drain_and_fail(s, inflight);
           return;
         }
       }
@@ -295,7 +377,8 @@ void worker_main(phe_server* s) {
     if (inflight.size() >= 2 || (!inflight.empty() && !launched)) {
       phe_status st = PHE_OK;
       if (!wait_iteration(s, inflight.front(), &st)) {
-        fail_all(s, st);
+        begin_failure(s, st);
+        drain_and_fail(s, inflight);
         return;
       }
       complete_iteration(s, inflight.front());
@@ -388,7 +471,7 @@ phe_status phe_server_wait(phe_server* s, uint64_t id, uint32_t timeout_ms, doub
   auto it = s->reqs.find(id);
   if (it == s->reqs.end()) return fail(PHE_EINVAL, "phe_server_wait: unknown request %llu", (unsigned long long)id);
   const bool ok = s->cv_done.wait_for(lk, std::chrono::milliseconds(timeout_ms),
-                                      [&] { return it->second.state >= 2; });
+                                      [&] { return it->second.state == 2 || it->second.state == 3; });
   if (!ok) return fail(PHE_ETIMEOUT, "phe_server_wait: request %llu not done after %u ms", (unsigned long long)id,
                        timeout_ms);
   if (it->second.state == 3) return fail(s->worker_status, "phe_server_wait: request failed");

@@ -12,7 +12,10 @@ import os
 import threading
 
 PKG = os.path.dirname(os.path.abspath(__file__))
-LIB_PATH = os.path.join(PKG, "libphe.so")
+LIB_PATH = os.path.join(PKG, "libphe.so")            # production library
+TEST_LIB_PATH = os.path.join(PKG, "libphe_test.so")  # plus the client-side calls (-DPHE_TESTING)
+# Calls only the test library exports (they take or make a secret key).
+TEST_ONLY = ("phe_client_encrypt", "phe_test_keygen")
 
 PHE_OK, PHE_EINVAL, PHE_ENOMEM, PHE_EBUSY, PHE_ETIMEOUT, PHE_ECUDA, PHE_EUNSUPPORTED = range(7)
 PHE_FWD, PHE_BWD = 0, 1
@@ -95,6 +98,7 @@ SIGNATURES = {
     "phe_matmul": (_i32, [_vp, _vp, _i32, _u32, _vp, _vp, _vp, _vp, _u32, _vp]),
     "phe_modswitch": (_i32, [_vp, _vp, _vp, _sz, _vp]),
     "phe_client_encrypt": (_i32, [_vp, _u32, _u32, _vp, _vp, _vp, _vp, _u64, _vp, _vp]),
+    "phe_test_keygen": (_i32, [_vp, _u64, _u32, _vp]),
     "phe_matmul_host": (_i32, [_vp, _vp, _i32, _u32, _vp, _vp, _vp, _vp, _u32, _u64, _vp]),
     "phe_trace_enable": (_i32, [_vp, _i32]),
     "phe_trace_read": (_i32, [_vp, ctypes.POINTER(phe_trace_entry), _u32, ctypes.POINTER(_u32)]),
@@ -126,26 +130,46 @@ SIGNATURES = {
     "phe_wire_pack": (_i32, [_vp, _vp, _u32, _vp, _u32, _u64, _vp, _vp]),
     "phe_wire_unpack_inputs": (_i32, [_vp, _vp, _u64, _vp, _vp, _vp]),
     "phe_matmul_wire": (_i32, [_vp, _vp, _vp, _i32, _u32, _vp, _vp, _vp]),
+    "phe_ctx_status": (_i32, [_vp, ctypes.POINTER(_u32), _i32]),
+    "phe_probe_alu": (_i32, [_i32, _i32, _u32, ctypes.POINTER(ctypes.c_double)]),
+    "phe_probe_tensor": (_i32, [_i32, _u32, ctypes.POINTER(ctypes.c_double)]),
 }
 
 _lib = None
+_lib_path = None
+_want_test = os.environ.get("PHE_LIBRARY", "") == "test"
 _lock = threading.Lock()
 
 
+def use_test_library() -> None:
+    """Load libphe_test.so instead of libphe.so (call before the first call
+    into the library; one process uses one of the two: handles of one are
+    not valid in the other).  Tests and the benchmark use it to make their
+    encrypted inputs with phe_client_encrypt."""
+    global _want_test
+    with _lock:
+        if _lib is not None and _lib_path != TEST_LIB_PATH:
+            raise RuntimeError("libphe.so is already loaded in this process")
+        _want_test = True
+
+
 def lib() -> ctypes.CDLL:
-    """Load libphe.so (raises if it has not been built)."""
-    global _lib
+    """Load the library (raises if it has not been built)."""
+    global _lib, _lib_path
     with _lock:
         if _lib is None:
-            if not os.path.exists(LIB_PATH):
-                raise RuntimeError(f"{LIB_PATH} is missing: build it with "
+            path = TEST_LIB_PATH if _want_test else LIB_PATH
+            if not os.path.exists(path):
+                raise RuntimeError(f"{path} is missing: build it with "
                                    "`python -m paper_2505_07329_b300.build` (or __graft_entry__.build())")
-            L = ctypes.CDLL(LIB_PATH)
+            L = ctypes.CDLL(path)
             for name, (res, args) in SIGNATURES.items():
+                if name in TEST_ONLY and path != TEST_LIB_PATH:
+                    continue
                 f = getattr(L, name)
                 f.restype = res
                 f.argtypes = args
-            _lib = L
+            _lib, _lib_path = L, path
     return _lib
 
 
@@ -234,6 +258,17 @@ def phe_modswitch(ctx, d_in, d_out, n: int, stream=None) -> None:
     _check(lib().phe_modswitch(ctx, _dptr(d_in), _dptr(d_out), n, _stream(stream)))
 
 
+PHE_KEY_BINARY, PHE_KEY_TERNARY = 0, 1
+
+
+def phe_test_keygen(ctx, N: int, seed: int, kind: int = PHE_KEY_TERNARY):
+    """Test library only: a seeded secret key for a context of ring degree N, int8 numpy array [N]."""
+    import numpy as np
+    out = np.zeros(N, dtype=np.int8)
+    _check(lib().phe_test_keygen(ctx, seed, kind, out.ctypes.data))
+    return out
+
+
 def phe_client_encrypt(ctx, T: int, d: int, A, S, E, x, delta: int, B, stream=None) -> None:
     _check(lib().phe_client_encrypt(ctx, T, d, _dptr(A), _dptr(S), _dptr(E), _dptr(x), delta, _dptr(B),
                                     _stream(stream)))
@@ -269,6 +304,27 @@ def phe_trace_read(ctx) -> dict:
     return {arr[i].name.decode(): {"launches": int(arr[i].launches), "total_ms": arr[i].total_ms,
                                    "p50_ms": arr[i].p50_ms, "p99_ms": arr[i].p99_ms, "max_ms": arr[i].max_ms}
             for i in range(n.value)}
+
+
+def phe_ctx_status(ctx, clear: bool = True) -> int:
+    """Status word of the context's bounded-wait kernels (0 = every wait completed)."""
+    v = _u32()
+    _check(lib().phe_ctx_status(ctx, ctypes.byref(v), 1 if clear else 0))
+    return v.value
+
+
+def phe_probe_alu(device: int = 0, form: int = 0, iters: int = 0) -> float:
+    """Register-only butterflies per second (form 0: 32-bit residues; 1: 64-bit words)."""
+    v = ctypes.c_double()
+    _check(lib().phe_probe_alu(device, form, iters, ctypes.byref(v)))
+    return v.value
+
+
+def phe_probe_tensor(device: int = 0, iters: int = 0) -> float:
+    """tcgen05.mma kind::f16 (bf16, fp32 accumulate) flop/s, M 128 N 256 K 16."""
+    v = ctypes.c_double()
+    _check(lib().phe_probe_tensor(device, iters, ctypes.byref(v)))
+    return v.value
 
 
 PHE_NOALLOC_MAX_SCRATCH_BYTES = 16 << 20

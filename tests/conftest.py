@@ -7,6 +7,12 @@ ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 if ROOT not in sys.path:
     sys.path.insert(0, ROOT)
 
+# The tests make encrypted inputs with the client-side calls, which only the
+# test build of the library exports (libphe_test.so, -DPHE_TESTING).
+from paper_2505_07329_b300 import phe as _phe  # noqa: E402
+
+_phe.use_test_library()
+
 
 def pytest_configure(config):
     config.addinivalue_line("markers", "gpu: needs a CUDA GPU (B300, sm_103a); run with -m gpu")

@@ -31,9 +31,21 @@ def test_layer_work_and_bytes():
     assert len(keys) == 11
 
 
-def test_alu_peaks_follow_the_probe_figures():
-    assert abs(bench.alu_peak_gmodmul("rns") - 148 * bench.BFLY32_PER_SM_CLK / 2 * 2.032) < 1e-9
-    assert abs(bench.alu_peak_gmodmul("prime") - 148 * bench.BFLY64_PER_SM_CLK * 2.032) < 1e-9
+def test_unit_count_bound_and_body_flops():
+    # 148 SMs x 64 FMA-heavy lanes / 4 lane-slots per 32-bit Shoup butterfly
+    # / 2 residues per coefficient, at 2032 MHz
+    assert abs(bench.unit_bound_gmodmul(2032.0) - 148 * 64 / 4 / 2 * 2.032) < 1e-9
+    wl = synth.WORKLOADS["layer"]
+    macs = sum(rows * cols for _, _, _, rows, cols, _ in bench.matmuls(wl))
+    assert macs == 2 * (2048 * 2048 * 2 + 2048 * 512 * 2 + 2048 * 8192 * 3)   # both directions
+    assert bench.body_flops_per_token(wl) == 2 * 8 * macs
+
+
+def test_int8_tensor_kind_is_refused_for_sm103a():
+    # the toolchain of this image: tcgen05.mma kind::i8 does not assemble for
+    # sm_103a (it does for sm_100a); the body GEMM uses kind::f16 with bf16 digits
+    assert bench.tensor_kind_check("i8").startswith("kind::i8 refused by ptxas for sm_103a")
+    assert bench.tensor_kind_check("f16") == "kind::f16 accepted by ptxas for sm_103a"
 
 
 def test_client_decryption_product_matches_the_oracle(orc):

@@ -13,13 +13,22 @@ from paper_2505_07329_b300 import build, phe
 ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
 
 
-def header_functions():
+def header_functions(testing=None):
+    """Function names include/*.h declares: testing=None all of them, True
+    those inside #ifdef PHE_TESTING blocks, False the others."""
     names = set()
     for hdr in os.listdir(os.path.join(ROOT, "include")):
         if hdr.endswith(".h"):
             text = open(os.path.join(ROOT, "include", hdr)).read()
             text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
-            names |= set(re.findall(r"^[A-Za-z_][\w\s\*]*?\b(phe_\w+)\s*\(", text, flags=re.M))
+            test_blocks = re.findall(r"#ifdef PHE_TESTING(.*?)#endif", text, flags=re.S)
+            prod = re.sub(r"#ifdef PHE_TESTING.*?#endif", "", text, flags=re.S)
+            pat = r"^[A-Za-z_][\w\s\*]*?\b(phe_\w+)\s*\("
+            if testing is not True:
+                names |= set(re.findall(pat, prod, flags=re.M))
+            if testing is not False:
+                for b in test_blocks:
+                    names |= set(re.findall(pat, b, flags=re.M))
     return names
 
 
@@ -33,7 +42,27 @@ def test_library_exports_every_declared_symbol(L):
     names = header_functions()
     assert len(names) >= 10
     for n in sorted(names):
-        assert hasattr(L, n), f"libphe.so does not export {n}"
+        assert hasattr(L, n), f"{phe.TEST_LIB_PATH} does not export {n}"
+
+
+def test_production_library_exports_no_secret_key_call():
+    # the server never holds the key (Sec. 5): libphe.so exports every
+    # production call and none of the client-side ones
+    build.build()
+    prod = ctypes.CDLL(phe.LIB_PATH)
+    for n in sorted(header_functions(testing=False)):
+        assert hasattr(prod, n), f"libphe.so does not export {n}"
+    test_only = header_functions(testing=True)
+    assert test_only == set(phe.TEST_ONLY)
+    for n in sorted(test_only):
+        assert not hasattr(prod, n), f"libphe.so exports the client-side call {n}"
+    tl = ctypes.CDLL(phe.TEST_LIB_PATH)
+    for n in sorted(test_only):
+        assert hasattr(tl, n), f"libphe_test.so does not export {n}"
+
+
+def test_test_keygen_rejects_null_arguments(L):
+    assert L.phe_test_keygen(None, 1, 1, None) == phe.PHE_EINVAL
 
 
 def test_binding_covers_the_header():

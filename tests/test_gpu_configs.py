@@ -136,3 +136,45 @@ def test_model_config_sixteen_layers_uneven_tokens(orc, ctx):
                 phe.phe_weights_free(w)
         outs = None
         torch.cuda.empty_cache()
+
+
+def test_model_sequence_at_full_length(orc, ctx):
+    # the longest sequence the model workload draws, at its full length, cut
+    # into the model step's 128-token calls (the last one ragged), for three
+    # products with one and two input blocks; every call's outputs are
+    # sampled before the next call overwrites them
+    import torch
+    counts = [int(c) for c in synth.model_token_counts()]
+    T = max(counts)
+    chunk = 128
+    picks = [(0, phe.PHE_FWD), (6, phe.PHE_FWD), (4, phe.PHE_BWD)]   # q fwd, down fwd (L=2), gate bwd (L=2)
+    for k, (pi, d) in enumerate(picks):
+        _, d_in, d_out = synth.LLAMA_PROJECTIONS[pi]
+        W = synth.weights(d_out, d_in, seed=synth.SEED_W + 700 + pi)
+        rows, cols = (d_out, d_in) if d == phe.PHE_FWD else (d_in, d_out)
+        L = synth.blocks(cols, N)
+        A = synth.uniform_words((T, L, N), Q, 3 * 10 ** 6 + k)
+        B = synth.uniform_words((T, L, N), Q, 4 * 10 ** 6 + k)
+        dA, dB = to_dev_u64(A), to_dev_u64(B)
+        w = phe.phe_weights_upload(ctx, W, phe.PHE_DIR_FWD_BIT if d == phe.PHE_FWD else phe.PHE_DIR_BWD_BIT)
+        om = torch.empty((chunk, rows, N), dtype=torch.int32, device="cuda")
+        ob = torch.empty((chunk, rows), dtype=torch.int32, device="cuda")
+        try:
+            got, pairs = [], []
+            for c, t0 in enumerate(range(0, T, chunk)):
+                tn = min(chunk, T - t0)
+                phe.phe_matmul(ctx, w, d, tn, dA[t0:t0 + tn], dB[t0:t0 + tn], om, ob)
+                torch.cuda.synchronize()
+                for t, j in ((tn - 1, (37 * c) % rows), (tn // 2, rows - 1 - (11 * c) % rows)):
+                    got.append((om[t, j].cpu().numpy().view(np.uint32).astype(np.uint64),
+                                int(ob[t, j].item()) & 0xffffffff))
+                    pairs.append((t0 + t, j))
+            assert phe.phe_ctx_status(ctx) == 0
+        finally:
+            phe.phe_weights_free(w)
+        Wd = W if d == phe.PHE_FWD else np.ascontiguousarray(W.T)
+        ea, eb = orc.lwedot_pairs(Wd, A, B, np.array(pairs), Q)
+        for x, (ga, gb) in enumerate(got):
+            assert np.array_equal(ga, orc.modswitch(ea[x], Q, 32)), (pi, d, pairs[x])
+            assert gb == orc.modswitch_one(int(eb[x]), Q, 32), (pi, d, pairs[x])
+    assert T >= 1024  # the drawn batch has a long sequence

@@ -86,7 +86,9 @@ def test_plan_run_matches_oracle(orc, env, tune):
         info = phe.phe_plan_info(plan)
         assert info["tune"] == tune
         assert info["lwedot_launches"] == 1
-        assert info["launches"] == 4  # x shared by three products: 3 distinct inputs + 1 persistent launch
+        # x shared by three products: per distinct input (3) an input transform and
+        # a body digit-row kernel, then one body GEMM and one lwedot launch
+        assert info["launches"] == 8
         phe.phe_plan_run(plan, stream)
         stream.synchronize()
         _check(orc, outs, refs, flags)

@@ -155,3 +155,81 @@ def test_destroy_drains_pending_work():
     ids = [phe.phe_server_submit(srv, None, 0, 9, sim_rows=4) for _ in range(5)]
     phe.phe_server_destroy(srv)  # returns after the work is done
     assert len(ids) == 5
+
+
+def test_failed_request_is_reported_only_after_its_work_drains():
+    # the iteration in flight "runs" for 1.5 s; the 50 ms bound fails the
+    # server at once, but the request may still be read and written until
+    # the iteration finishes, so it is failing, not failed, until then
+    srv = _server(chunk_tokens=100, wait_timeout_ms=50, sim_ns_per_item=1.5e7)
+    try:
+        t0 = time.monotonic()
+        rid = phe.phe_server_submit(srv, None, 0, 100, sim_rows=1)
+        time.sleep(0.4)
+        done, _ = phe.phe_server_poll(srv, rid)
+        assert done == 0 and time.monotonic() - t0 < 1.3
+        assert phe.phe_server_stats(srv)["failed"] == 0
+        with pytest.raises(phe.PheError) as ei:
+            phe.phe_server_wait(srv, rid, 100)
+        assert ei.value.status == phe.PHE_ETIMEOUT
+        with pytest.raises(phe.PheError):
+            phe.phe_server_wait(srv, rid, 10000)
+        assert time.monotonic() - t0 >= 1.45
+        done, _ = phe.phe_server_poll(srv, rid)
+        assert done == -1
+        assert phe.phe_server_stats(srv)["failed"] == 1
+    finally:
+        phe.phe_server_destroy(srv)
+
+
+def test_work_that_never_drains_leaves_requests_pending():
+    # an iteration far longer than the drain bound (3 s): the request is
+    # never reported failed, its waits time out, and destroy still returns
+    srv = _server(chunk_tokens=100, wait_timeout_ms=50, sim_ns_per_item=6e8)
+    try:
+        rid = phe.phe_server_submit(srv, None, 0, 100, sim_rows=1)
+        time.sleep(0.5)
+        done, _ = phe.phe_server_poll(srv, rid)
+        assert done == 0
+        with pytest.raises(phe.PheError) as ei:
+            phe.phe_server_wait(srv, rid, 100)
+        assert ei.value.status == phe.PHE_ETIMEOUT
+        with pytest.raises(phe.PheError):
+            phe.phe_server_submit(srv, None, 0, 1, sim_rows=1)
+    finally:
+        t0 = time.monotonic()
+        phe.phe_server_destroy(srv)
+        assert time.monotonic() - t0 < 2.0
+
+
+def test_large_request_is_not_starved_by_small_ones():
+    # 100 ms large chunks need 80 kB of a 100 kB budget; 1 ms small chunks
+    # (880 B) arrive at 2.5x the served rate.  Without aging, small chunks
+    # in flight keep the budget above 20 kB and the large request waits for
+    # the whole small backlog (about 3.5 s); with it, it runs within a few
+    # iterations of reaching the head of the queue.
+    srv = _server(mem_budget_bytes=100_000, chunk_tokens=10, max_active=4096, max_jobs_per_iteration=64,
+                  max_queue=100_000, sim_ns_per_item=1e4)
+    stop = threading.Event()
+    small = []
+
+    def feeder():
+        while not stop.is_set():
+            small.append(phe.phe_server_submit(srv, None, 0, 50, sim_rows=10))
+            time.sleep(0.002)
+    try:
+        th = threading.Thread(target=feeder)
+        th.start()
+        time.sleep(0.3)
+        t_large = time.monotonic()
+        big = phe.phe_server_submit(srv, None, 0, 10, sim_rows=1000)
+        phe.phe_server_wait(srv, big, 20000)
+        waited = time.monotonic() - t_large
+        stop.set()
+        th.join()
+        assert waited < 2.0, f"large request waited {waited:.2f} s"
+        for i in small:
+            phe.phe_server_wait(srv, i, 60000)
+    finally:
+        stop.set()
+        phe.phe_server_destroy(srv)
