@@ -97,6 +97,8 @@ def parse():
     ap.add_argument("--chunk", type=int, default=32, help="tokens per plain-form call")
     ap.add_argument("--batch-chunk", type=int, default=128, help="tokens per batched-form plan")
     ap.add_argument("--no-compare", action="store_true", help="skip the secondary measurement of the other form")
+    ap.add_argument("--tune", default="",
+                    help="fixed plan tuning 'tok_chunk,blocks_per_sm' instead of the autotuner's pick (profiling)")
     ap.add_argument("--small-batches", default="1,8,32",
                     help="token counts at which both forms run the layer's 14 products ('' to skip)")
     ap.add_argument("--tokens", type=int, default=0, help="override tokens per GPU (0 = the workload's)")
@@ -572,7 +574,10 @@ def main():
     if uses_plans:
         # autotune on the first chunk's products (a 32-token sample), then one
         # plan per chunk: pointers into the resident inputs, shared outputs
-        tuning, tune_ms = phe.phe_autotune(ctx, chunk_jobs(0, bchunk), phe.PHE_OUT_SWITCHED, 32, side)
+        if args.tune:
+            tuning, tune_ms = tuple(int(x) for x in args.tune.split(",")), None
+        else:
+            tuning, tune_ms = phe.phe_autotune(ctx, chunk_jobs(0, bchunk), phe.PHE_OUT_SWITCHED, 32, side)
         for t0 in range(0, T, bchunk):
             plans.append(phe.phe_plan_create(ctx, chunk_jobs(t0, min(bchunk, T - t0)), phe.PHE_OUT_SWITCHED, tuning))
         plan_modmuls = sum(phe.phe_plan_info(pl)["modmuls"] for pl in plans)

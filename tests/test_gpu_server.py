@@ -102,8 +102,10 @@ def test_same_result_alone_and_in_the_mix(orc, env):
 def test_tight_budget_serialises_but_completes(env):
     ctx, Ws, ws = env
     r = _request(Ws, ws, 1, phe.PHE_FWD, 16, seed=90)
-    # room for exactly one 4-token chunk of this request
-    one = 4 * 2 * N * 8 + 4 * 200 * N * 4 + 4 * 200 * 4
+    # room for exactly one 4-token chunk of this request: transformed masks
+    # (L = 2), mask and body outputs, and the bodies' bf16 digit rows (8 per
+    # token, 1500 columns)
+    one = 4 * 2 * N * 8 + 4 * 200 * N * 4 + 4 * 200 * 4 + 4 * 8 * 1504 * 2
     srv = phe.phe_server_create(ctx, one, chunk_tokens=4)
     try:
         phe.phe_server_wait(srv, _submit(srv, ws, r), 60000)

@@ -71,7 +71,8 @@ def test_noalloc_matches_the_oracle(env, orc):
     raw_m, raw_b = _run(phe.phe_matmul_noalloc, ctx, w, phe.PHE_FWD, dA, dB, phe.PHE_OUT_RAW, T)
     sw_m, sw_b = _run(phe.phe_matmul_noalloc, ctx, w, phe.PHE_FWD, dA, dB, phe.PHE_OUT_SWITCHED, T)
     pairs = np.array([[t, j] for t in (0, T - 1) for j in (0, 151, 299)], dtype=np.int64)
-    ea, eb = orc.lwedot_pairs(W, A, B, pairs, q, method=1)
+    # the oracle's NTT products need a prime q; the RNS q takes the schoolbook definition
+    ea, eb = orc.lwedot_pairs(W, A, B, pairs, q, method=1 if q == synth.Q60 else 0)
     for n, (t, j) in enumerate(pairs):
         assert np.array_equal(raw_m[t, j].view(np.uint64), ea[n])
         assert int(raw_b[t, j].view(np.uint64)) == int(eb[n])
