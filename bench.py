@@ -38,14 +38,29 @@ import synth  # noqa: E402
 
 METRIC = "encrypted W·[x] tokens/s per Llama-1B layer; p50/p99 latency; % of roofline"
 # DRAM bytes (read + write) of one lwedot_kernel launch of the batched form
-# (128 tokens x all 14 products of the layer workload, RNS modulus), measured
-# with ncu, and the algorithmic bytes of that launch.  Valid only for the
-# kernel sources the counters were taken on (kernel_source_hash) and the
-# tuning the captured run picked.
-TRAFFIC_KERNEL_HASH = "db470b93556616b3"
+# (all 14 products of the layer workload, RNS modulus, tuning (16, 0)) as a
+# function of the launch's tokens T: a + b T, from ncu captures of the same
+# launch at T = 2 and T = 4 (dram__bytes_read.sum + dram__bytes_write.sum:
+# 4.749 and 6.222 GB).  a is what a launch reads once whatever its tokens
+# (the encoded weights), b what each token adds (its transformed masks and
+# its outputs).  Valid only for the kernel sources the counters were taken
+# on (kernel_source_hash) and that tuning.
+TRAFFIC_KERNEL_HASH = "f97d7ed5d41f7f37"
 TRAFFIC_TUNING = (16, 0)
-TRAFFIC_BYTES_PER_LAUNCH = 96899.7e6
-TRAFFIC_ALG_BYTES_PER_LAUNCH = 95891.8e6
+TRAFFIC_FIT = (3276.48e6, 736.465e6)
+
+
+def lwedot_alg_bytes(wl, T: int) -> float:
+    """Algorithmic DRAM bytes of one batched lwedot launch over T tokens: the
+    encoded weights once (16 bytes per word), each token's transformed input
+    masks once (8 bytes per word, inputs shared across products counted
+    once) and its switched output masks (4 bytes per word; the bodies come
+    from the body GEMM)."""
+    N = wl.ring.N
+    what = sum(rows * L * N * 16 for _, _, _, rows, _, L in matmuls(wl))
+    out = sum(rows * N * 4 for _, _, _, rows, _, _ in matmuls(wl))
+    ahat = {key: L * N * 8 for (key, cols, L) in input_keys(wl).values()}
+    return what + T * (out + sum(ahat.values()))
 
 
 # The source text lwedot_kernel is built and launched from: the device header,
@@ -53,7 +68,7 @@ TRAFFIC_ALG_BYTES_PER_LAUNCH = 95891.8e6
 # its launcher to the next one.
 KERNEL_SOURCE_REGIONS = (
     ("// Resident threads per SM the register budget is sized for", "// Seeded masks written out in natural order"),
-    ("template <int LOGN, int MODE, bool RNS>\nstatic cudaError_t lwedot_impl", "cudaError_t launch_lwedot("),
+    ("template <int LOGN, int MODE, bool RNS>\nstatic cudaError_t lwedot_impl", "// The instantiated (mode, form) pairs"),
 )
 
 
@@ -668,13 +683,15 @@ def main():
     achieved = modmuls / (kernel_ms / 1e3) / 1e9 if kernel_ms else None
     peak = alu["gmodmul"]
     unit_bound = unit_bound_gmodmul(clk.get("sm_max_mhz") or 2032.0) if args.modulus == "rns" else None
-    traffic_ok = (kernel_source_hash() == TRAFFIC_KERNEL_HASH and wl.name == "layer" and bchunk == 128
+    traffic_ok = (kernel_source_hash() == TRAFFIC_KERNEL_HASH and wl.name == "layer"
                   and args.form == "batched" and args.modulus == "rns" and T % bchunk == 0
                   and tuning is not None and tuple(tuning) == TRAFFIC_TUNING)
     roof = {"bound": "alu", "unit": "Gmodmul/s", "achieved": achieved, "peak": peak,
             "frac": (achieved / peak) if achieved and peak else None,
-            "traffic": TRAFFIC_BYTES_PER_LAUNCH if traffic_ok else None,
-            "traffic_alg_bytes": TRAFFIC_ALG_BYTES_PER_LAUNCH if traffic_ok else None,
+            "traffic": (TRAFFIC_FIT[0] + TRAFFIC_FIT[1] * bchunk) if traffic_ok else None,
+            "traffic_alg_bytes": lwedot_alg_bytes(wl, bchunk),
+            "traffic_basis": ("per launch of --batch-chunk tokens: a + b T from ncu DRAM counters of the same launch "
+                              "at T = 2 and 4 (profiles/lwedot_kernel_rns_llama1b_layer_dram_traffic.md)"),
             "peak_basis": (f"measured in this run by phe_probe_alu: {alu['bfly_per_s'] / 1e9:.1f} G "
                            f"{alu['bfly']} register-only butterflies/s"
                            + (" / 2 residues per coefficient" if args.modulus == "rns" else "")

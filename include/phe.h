@@ -201,6 +201,20 @@ typedef struct phe_trace_entry {
 phe_status phe_trace_enable(phe_ctx* ctx, int on);
 phe_status phe_trace_read(phe_ctx* ctx, phe_trace_entry* out, uint32_t cap, uint32_t* n_out);
 
+/* Where the bodies b'_tj = sum_k W[j,k] B_t[k] run (results are identical
+ * bit for bit):
+ *   PHE_BODY_AUTO    (default) on the tensor cores when a launch group has at
+ *                    least 16384 (token, row) outputs, else fused in the mask
+ *                    kernel (a dp4a dot product), which has the lower latency
+ *                    at one-token sizes;
+ *   PHE_BODY_TENSOR  always on the tensor cores;
+ *   PHE_BODY_FUSED   always fused (no digit-row scratch).
+ * Applies to calls made after it.  Errors: PHE_EINVAL. */
+#define PHE_BODY_AUTO 0u
+#define PHE_BODY_TENSOR 1u
+#define PHE_BODY_FUSED 2u
+phe_status phe_ctx_set_body_path(phe_ctx* ctx, uint32_t path);
+
 /* Status word of the context's kernels with bounded waits (the body GEMM):
  * 0 when every wait completed since the last clear; otherwise bit 0 = a
  * tensor-memory operand load, bit 1 = an MMA issue wait, bit 2 = the

@@ -181,26 +181,29 @@ cudaError_t matmul_device(phe_ctx* c, const phe_weights::Dir& D, u32 T, const u6
   phe::set_lwe_tiles(J, c->logn);
   jt.prefix[0] = 0;
   jt.prefix[1] = J.tiles;
-  // one scratch allocation: A_hat, then the bodies' digit rows
+  // one scratch allocation: A_hat, then (bodies on the tensor cores) the
+  // bodies' digit rows
+  const bool gemm = phe::body_on_tensor_cores(c, jt);
   const size_t ahat_bytes = ((size_t)T * D.L * N * sizeof(u64) + 255) & ~(size_t)255;
   char* scratch = nullptr;
-  cudaError_t e = phe::ctx_malloc_async(c, &scratch, ahat_bytes + phe::body_scratch_bytes(jt), s);
+  cudaError_t e =
+      phe::ctx_malloc_async(c, &scratch, ahat_bytes + (gemm ? phe::body_scratch_bytes(jt) : 0), s);
   if (e != cudaSuccess) return e;
   u64* ahat = reinterpret_cast<u64*>(scratch);
   J.ahat = ahat;
-  phe::assign_body_scratch(jt, scratch + ahat_bytes);
+  if (gemm) phe::assign_body_scratch(jt, scratch + ahat_bytes);
   {
     Span sp(c, phe::kKInputNtt, s);
     phe::NttJob nj{in_mask, ahat, T * D.L, in_seeds};
     e = phe::launch_input_ntt(c, &nj, 1, s);
   }
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && gemm) {
     Span sp(c, phe::kKBodyGemm, s);
     e = phe::launch_body(c, jt, mode == phe::kOutRaw, c->rc, c->rk, s);
   }
   if (e == cudaSuccess) {
     Span sp(c, phe::kKLwedot, s);
-    e = phe::launch_lwedot(c, jt, mode | phe::kBodyGemm, 0, s);
+    e = phe::launch_lwedot(c, jt, mode | (gemm ? phe::kBodyGemm : 0), 0, s);
   }
   cudaError_t ef = cudaFreeAsync(scratch, s);
   return e != cudaSuccess ? e : ef;
@@ -659,6 +662,14 @@ phe_status phe_matmul_host(phe_ctx* c, const phe_weights* w, int dir, uint32_t T
   }
   cudaEventDestroy(ev);
   if (e != cudaSuccess) return cuda_fail(e, "phe_matmul_host");
+  return PHE_OK;
+}
+
+phe_status phe_ctx_set_body_path(phe_ctx* c, uint32_t path) {
+  if (!c) return fail(PHE_EINVAL, "phe_ctx_set_body_path: null context");
+  if (path != PHE_BODY_AUTO && path != PHE_BODY_TENSOR && path != PHE_BODY_FUSED)
+    return fail(PHE_EINVAL, "phe_ctx_set_body_path: path=%u", path);
+  c->body_path = path;
   return PHE_OK;
 }
 

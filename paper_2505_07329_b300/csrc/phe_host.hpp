@@ -26,6 +26,12 @@ constexpr u32 kBodyChunk = 1024;
 // Row pitch (elements) of the bf16 weight and digit rows: 16-byte aligned rows for TMA.
 inline u32 digit_pitch(u32 cols) { return (cols + 7) & ~7u; }
 inline size_t digit_bytes(u32 T, u32 cols) { return (size_t)T * 8 * digit_pitch(cols) * 2; }
+// Below this many (token, row) outputs in one launch group the bodies stay
+// fused in lwedot (a dp4a dot product): the body GEMM's two extra launches
+// and its cold pipeline cost more than the ~11% of lwedot time the fused body
+// takes.  One token of a 2048x8192 product (8192 outputs) is faster fused;
+// one token of a whole layer (44 032 outputs) on the tensor cores.
+constexpr unsigned long long kBodyGemmMinItems = 16384;
 constexpr int kMaxLogN = 13;
 
 // One matrix product of the hot path, as the lwedot kernel sees it.
@@ -132,6 +138,7 @@ struct phe_ctx {
   // Status word the kernels with bounded waits set bits in (phe_body.cu):
   // nonzero means a wait timed out and that launch's outputs are not valid.
   uint32_t* d_status = nullptr;
+  uint32_t body_path = PHE_BODY_AUTO;  // phe_ctx_set_body_path
   phe::Tracer tracer;
 };
 
@@ -197,9 +204,7 @@ cudaError_t launch_weight_ntt(const phe_ctx* c, const int8_t* W, u32 rows, u32 c
                               u32 col_stride, u32 L, int rev, void* what, cudaStream_t s, bool force64 = false);
 cudaError_t launch_lwedot(const phe_ctx* c, const LweJobTable& jt, int mode, int grid_limit, cudaStream_t s,
                           bool force64 = false);
-// lwedot in kOutPackIn mode, with the switch constants rcK / rkK of 2^(base_log*ell).
-cudaError_t launch_lwedot_packin(const phe_ctx* c, const LweJobTable& jt, const RingConst& rcK, const RnsConst& rkK,
-                                 cudaStream_t s);
+
 cudaError_t launch_modswitch(const phe_ctx* c, const u64* in, u32* out, size_t n, cudaStream_t s);
 cudaError_t launch_expand_masks(const phe_ctx* c, const u64* seeds, u32 n, u64* masks, cudaStream_t s);
 int lwedot_threads(int logn);
@@ -216,11 +221,22 @@ cudaError_t assign_body_scratch(LweJobTable& jt, void* scratch);
 cudaError_t launch_body(const phe_ctx* c, const LweJobTable& jt, bool raw, const RingConst& rc, const RnsConst& rk,
                         cudaStream_t s);
 cudaError_t prepare_body_launches();
+// Whether a launch group's bodies run on the tensor cores (the GEMM) or fused
+// in lwedot: the context's body path, else the group's size.
+inline bool body_on_tensor_cores(const phe_ctx* c, const LweJobTable& jt) {
+  if (c->body_path == PHE_BODY_TENSOR) return true;
+  if (c->body_path == PHE_BODY_FUSED) return false;
+  unsigned long long items = 0;
+  for (u32 i = 0; i < jt.n; ++i) items += (unsigned long long)jt.j[i].rows * jt.j[i].T;
+  return items >= kBodyGemmMinItems;
+}
 // Loads the allocation-free entry point's scratch array on the current device (phe_noalloc.cu).
 cudaError_t noalloc_setup();
-// The full hot path of a job table: launch_body, then lwedot for the masks
-// (mode | kBodyGemm).  Jobs must carry wbf and digits.
-cudaError_t launch_lwe(const phe_ctx* c, const LweJobTable& jt, int mode, int grid_limit, cudaStream_t s);
+// lwedot in kOutPackIn mode, with the switch constants rcK / rkK of
+// 2^(base_log*ell), and the bodies of the GEMM (launch_body first; jobs carry
+// wbf and digits) or fused (gemm = false).
+cudaError_t launch_lwedot_packin2(const phe_ctx* c, const LweJobTable& jt, const RingConst& rcK, const RnsConst& rkK,
+                                  bool gemm, cudaStream_t s);
 
 // Tiles of an lwedot job: (a group of row_group adjacent rows) x (a chunk of
 // tok_chunk tokens).  A block holds SLOTS = threads / (N/16) transforms; when

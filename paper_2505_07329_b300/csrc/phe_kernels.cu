@@ -621,16 +621,17 @@ static cudaError_t lwedot_impl(const phe_ctx* c, const LweJobTable& jt, int grid
   return cudaGetLastError();
 }
 
-// The instantiated (mode, form) pairs.  Bodies fused in lwedot (no kBodyGemm)
-// serve the allocation-free entry point; every other call takes its bodies
-// from the tensor-core GEMM.
+// The instantiated (mode, form) pairs: bodies fused in lwedot (no kBodyGemm:
+// small launch groups, and the allocation-free entry point) or from the
+// tensor-core GEMM (kBodyGemm).
 #define PHE_LWEDOT_MODES(X)                                                                           \
   X(kOutSwitched, false) X(kOutRaw, false) X(kOutRing, false) X(kOutSwitched, true)                  \
   X(kOutSwitched | kK32, true) X(kOutRaw, true) X(kOutSwitched | kPow2, true) X(kOutRaw | kPow2, true) \
   X(kOutSwitched | kBodyGemm, false) X(kOutRaw | kBodyGemm, false) X(kOutSwitched | kBodyGemm, true) \
   X(kOutSwitched | kK32 | kBodyGemm, true) X(kOutRaw | kBodyGemm, true)                               \
   X(kOutSwitched | kPow2 | kBodyGemm, true) X(kOutRaw | kPow2 | kBodyGemm, true)                      \
-  X(kOutPackIn | kBodyGemm, false) X(kOutPackIn | kBodyGemm, true) X(kOutPackIn | kPow2 | kBodyGemm, true)
+  X(kOutPackIn | kBodyGemm, false) X(kOutPackIn | kBodyGemm, true) X(kOutPackIn | kPow2 | kBodyGemm, true) \
+  X(kOutPackIn, false) X(kOutPackIn, true) X(kOutPackIn | kPow2, true)
 
 template <int LOGN>
 static cudaError_t lwedot_dispatch(const phe_ctx* c, const LweJobTable& jt, int mode, bool rns, int grid_limit,
@@ -660,22 +661,17 @@ cudaError_t launch_lwedot(const phe_ctx* c, const LweJobTable& jt, int mode, int
   });
 }
 
-cudaError_t launch_lwedot_packin(const phe_ctx* c, const LweJobTable& jt, const RingConst& rcK, const RnsConst& rkK,
-                                 cudaStream_t s) {
+cudaError_t launch_lwedot_packin2(const phe_ctx* c, const LweJobTable& jt, const RingConst& rcK, const RnsConst& rkK,
+                                  bool gemm, cudaStream_t s) {
   if (jt.prefix[jt.n] == 0) return cudaSuccess;
-  cudaError_t e = launch_body(c, jt, /*raw=*/true, c->rc, c->rk, s);
-  if (e != cudaSuccess) return e;
+  if (gemm) {
+    cudaError_t e = launch_body(c, jt, /*raw=*/true, c->rc, c->rk, s);
+    if (e != cudaSuccess) return e;
+  }
   return by_logn(c->logn, [&](auto lg) -> cudaError_t {
-    const int mode = kOutPackIn | kBodyGemm | ((c->rns && c->pow2) ? kPow2 : 0);
+    const int mode = kOutPackIn | (gemm ? kBodyGemm : 0) | ((c->rns && c->pow2) ? kPow2 : 0);
     return lwedot_dispatch<decltype(lg)::value>(c, jt, mode, c->rns, 0, rcK, rkK, s);
   });
-}
-
-cudaError_t launch_lwe(const phe_ctx* c, const LweJobTable& jt, int mode, int grid_limit, cudaStream_t s) {
-  if (jt.prefix[jt.n] == 0) return cudaSuccess;
-  cudaError_t e = launch_body(c, jt, mode == kOutRaw, c->rc, c->rk, s);
-  if (e != cudaSuccess) return e;
-  return launch_lwedot(c, jt, mode | kBodyGemm, grid_limit, s);
 }
 
 cudaError_t prepare_launches(const phe_ctx* c) {

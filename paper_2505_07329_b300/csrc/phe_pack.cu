@@ -668,9 +668,10 @@ cudaError_t matmul_packed_device(phe_ctx* c, const phe_weights::Dir& D, const ph
       phe::set_lwe_tiles(J, c->logn);
       jt.prefix[0] = 0;
       jt.prefix[1] = J.tiles;
-      phe::assign_body_scratch(jt, digits);
+      const bool gemm = phe::body_on_tensor_cores(c, jt);
+      if (gemm) phe::assign_body_scratch(jt, digits);
       Span sp(c, phe::kKLwedot, s);
-      e = phe::launch_lwedot_packin(c, jt, k->rcK, k->rkK, s);
+      e = phe::launch_lwedot_packin2(c, jt, k->rcK, k->rkK, gemm, s);
     }
     if (e == cudaSuccess)
       e = pack_device(c, k, tn, D.rows, atil, true, rawb, static_cast<char*>(oa) + (size_t)t0 * G * N * osz,

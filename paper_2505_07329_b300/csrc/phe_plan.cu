@@ -31,7 +31,8 @@ struct phe_plan {
   };
   std::vector<Input> inputs;
   std::vector<phe::LweJobTable> tables;
-  std::vector<void*> body_scratch;  // digit rows of the bodies, one buffer per table
+  std::vector<void*> body_scratch;  // digit rows of the bodies, one buffer per table (tensor-core bodies)
+  std::vector<char> gemm;           // per table: bodies on the tensor cores, else fused in lwedot
   std::vector<u32> grids;
   u64 scratch_bytes = 0;
   u64 modmuls = 0;
@@ -113,10 +114,12 @@ cudaError_t run_plan(phe_plan* p, cudaStream_t s, bool trace, bool capture_event
   };
   for (size_t t = 0; t < p->tables.size(); ++t) {
     const phe::LweJobTable& jt = p->tables[t];
-    e = bracket(phe::kKBodyGemm, [&] { return phe::launch_body(c, jt, raw, c->rc, c->rk, s); });
+    const bool gemm = p->gemm[t] != 0;
+    if (gemm) e = bracket(phe::kKBodyGemm, [&] { return phe::launch_body(c, jt, raw, c->rc, c->rk, s); });
     if (e == cudaSuccess)
-      e = bracket(phe::kKLwedot,
-                  [&] { return phe::launch_lwedot(c, jt, mode | phe::kBodyGemm, (int)p->grids[t], s); });
+      e = bracket(phe::kKLwedot, [&] {
+        return phe::launch_lwedot(c, jt, mode | (gemm ? phe::kBodyGemm : 0), (int)p->grids[t], s);
+      });
     if (e != cudaSuccess) return e;
   }
   return e;
@@ -219,6 +222,12 @@ phe_status phe_plan_create(phe_ctx* c, const phe_job* jobs, uint32_t n_jobs, uin
   if (cur.n) p->tables.push_back(cur);
   for (auto& t : p->tables) {
     // digit rows of each distinct body input of the table, resident with the plan
+    const bool gemm = phe::body_on_tensor_cores(c, t);
+    p->gemm.push_back(gemm ? 1 : 0);
+    if (!gemm) {
+      p->body_scratch.push_back(nullptr);
+      continue;
+    }
     void* b = nullptr;
     const size_t bytes = phe::body_scratch_bytes(t);
     e = cudaMalloc(&b, bytes ? bytes : 256);
@@ -285,10 +294,14 @@ phe_status phe_plan_graph(phe_plan* p, void* stream) {
 
 phe_status phe_plan_info(const phe_plan* p, phe_plan_stats* st) {
   if (!p || !st) return fail(PHE_EINVAL, "phe_plan_info: null argument");
-  // per table: one digit-row kernel per distinct body input, the body GEMM, lwedot
+  // per table: lwedot; with tensor-core bodies also one digit-row kernel per
+  // distinct body input and the body GEMM
   uint32_t launches = (uint32_t)p->inputs.size();
-  for (const auto& t : p->tables) {
-    launches += 2;
+  for (size_t k = 0; k < p->tables.size(); ++k) {
+    const auto& t = p->tables[k];
+    launches += 1;
+    if (!p->gemm[k]) continue;
+    launches += 1;
     for (u32 i = 0; i < t.n; ++i) launches += t.j[i].digits_owner;
   }
   st->launches = launches;

@@ -3,10 +3,12 @@
 //
 //   * ALU: register-only Gentleman-Sande butterflies -- the same gs_bfly32 /
 //     gs_bfly the inverse transforms use (Shoup products with Harvey's lazy
-//     reduction) -- in 8 independent chains per thread, at the occupancy of
-//     lwedot_kernel (3 blocks of 256 threads per SM).  Nothing but
-//     butterflies is issued, so this is the rate a transform kernel could
-//     reach if it did nothing else.
+//     reduction) -- in independent chains, over a sweep of chains per thread
+//     (4 to 16) and resident blocks per SM (2 to 8, one full wave), so that
+//     neither dependency latency nor occupancy caps the rate; the best
+//     configuration's rate is reported.  Nothing but butterflies is issued,
+//     so this is the rate a transform kernel could reach if it did nothing
+//     else.
 //   * Tensor: back-to-back tcgen05.mma kind::f16 (bf16 in, fp32 accumulate,
 //     M = 128, N = 256, K = 16) on shared-memory operands into tensor memory,
 //     one CTA per SM -- the instruction shape of the body GEMM.
@@ -19,49 +21,53 @@ namespace phe {
 
 namespace {
 
-constexpr int kProbeChains = 8;
-
-template <bool RNS>
-__global__ void __launch_bounds__(256, 3) bfly_probe_kernel(u32 iters, const uint4* __restrict__ tw, u64 q,
-                                                            u32 p1, u32 p2, u64* __restrict__ sink) {
+// CHAINS independent butterfly chains per thread, NTW distinct twiddles
+// shared round-robin by the chains (the transforms reuse a twiddle across
+// 2^stage butterflies too), at MINB blocks of 256 threads per SM.
+template <bool RNS, int CHAINS, int NTW, int MINB>
+__global__ void __launch_bounds__(256, MINB) bfly_probe_kernel(u32 iters, const uint4* __restrict__ tw, u64 q,
+                                                               u32 p1, u32 p2, u64* __restrict__ sink) {
   const u32 tid = blockIdx.x * blockDim.x + threadIdx.x;
   if constexpr (RNS) {
     const Ring2x32 ring{p1, p2};
-    uint2 X[kProbeChains], Y[kProbeChains];
-    uint4 w[kProbeChains];
+    uint2 X[CHAINS], Y[CHAINS];
+    uint4 w[NTW];
 #pragma unroll
-    for (int c = 0; c < kProbeChains; ++c) {
-      w[c] = __ldg(&tw[(tid + c) & 255]);
+    for (int c = 0; c < NTW; ++c) w[c] = __ldg(&tw[(tid + c) & 255]);
+#pragma unroll
+    for (int c = 0; c < CHAINS; ++c) {
       X[c] = make_uint2((tid * 7u + c) % p1, (tid * 5u + c) % p2);
       Y[c] = make_uint2((tid * 3u + c) % p1, (tid * 11u + c) % p2);
     }
     for (u32 i = 0; i < iters; ++i) {
 #pragma unroll
-      for (int c = 0; c < kProbeChains; ++c) ring.gs(X[c], Y[c], w[c]);
+      for (int c = 0; c < CHAINS; ++c) ring.gs(X[c], Y[c], w[c % NTW]);
     }
     u64 acc = 0;
 #pragma unroll
-    for (int c = 0; c < kProbeChains; ++c) acc ^= ((u64)X[c].x << 32 | Y[c].x) ^ ((u64)X[c].y << 32 | Y[c].y);
+    for (int c = 0; c < CHAINS; ++c) acc ^= ((u64)X[c].x << 32 | Y[c].x) ^ ((u64)X[c].y << 32 | Y[c].y);
     sink[tid] = acc;
   } else {
     const Ring64 ring{q, 4 * q};
-    u64 X[kProbeChains], Y[kProbeChains];
-    ulonglong2 w[kProbeChains];
+    u64 X[CHAINS], Y[CHAINS];
+    ulonglong2 w[NTW];
 #pragma unroll
-    for (int c = 0; c < kProbeChains; ++c) {
+    for (int c = 0; c < NTW; ++c) {
       const uint4 t = __ldg(&tw[(tid + c) & 255]);
-      w[c] = make_ulonglong2(((u64)t.y << 32 | t.x) % q, 0);
-      w[c].y = (u64)t.z << 32 | t.w;  // floor(w 2^64 / q), set on the host
+      w[c] = make_ulonglong2(((u64)t.y << 32 | t.x) % q, (u64)t.z << 32 | t.w);  // (w, floor(w 2^64 / q))
+    }
+#pragma unroll
+    for (int c = 0; c < CHAINS; ++c) {
       X[c] = ((u64)tid * 7 + c) % q;
       Y[c] = ((u64)tid * 3 + c) % q;
     }
     for (u32 i = 0; i < iters; ++i) {
 #pragma unroll
-      for (int c = 0; c < kProbeChains; ++c) ring.gs(X[c], Y[c], w[c]);
+      for (int c = 0; c < CHAINS; ++c) ring.gs(X[c], Y[c], w[c % NTW]);
     }
     u64 acc = 0;
 #pragma unroll
-    for (int c = 0; c < kProbeChains; ++c) acc ^= X[c] ^ Y[c];
+    for (int c = 0; c < CHAINS; ++c) acc ^= X[c] ^ Y[c];
     sink[tid] = acc;
   }
 }
@@ -147,11 +153,11 @@ phe_status phe_probe_alu(int device, int form, uint32_t iters, double* per_s) {
   int sms = 0;
   cudaError_t e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, device);
   if (e != cudaSuccess) return cuda_fail(e, "cudaDeviceGetAttribute");
-  const u32 blocks = (u32)sms * 3, threads = blocks * 256;
+  const u32 max_threads = (u32)sms * 8 * 256;
   uint4* tw = nullptr;
   u64* sink = nullptr;
   e = cudaMalloc(&tw, 256 * sizeof(uint4));
-  if (e == cudaSuccess) e = cudaMalloc(&sink, threads * sizeof(u64));
+  if (e == cudaSuccess) e = cudaMalloc(&sink, max_threads * sizeof(u64));
   // twiddles (w, w') mod p1, p2: any w below p with its Shoup quotient
   const u32 p1 = 1073643521u, p2 = 1073692673u;
   const u64 q = 1152921504606830593ull;  // 2^60 - 2^14 + 1
@@ -168,21 +174,44 @@ phe_status phe_probe_alu(int device, int form, uint32_t iters, double* per_s) {
     }
     e = cudaMemcpy(tw, h, sizeof(h), cudaMemcpyHostToDevice);
   }
-  float ms = 0.f;
-  if (e == cudaSuccess)
-    e = best_ms(
+  // Sweep (chains per thread, blocks per SM): the best rate is the peak.
+  // Threads per launch: blocks per SM x 256 x SMs, one full wave.
+  double best = 0.0;
+  auto run = [&](auto kern, int chains, int minb) -> cudaError_t {
+    const u32 blocks = (u32)sms * minb, threads = blocks * 256;
+    float ms = 0.f;
+    cudaError_t e2 = best_ms(
         [&] {
-          if (form == 0) bfly_probe_kernel<true><<<blocks, 256>>>(iters, tw, q, p1, p2, sink);
-          else bfly_probe_kernel<false><<<blocks, 256>>>(iters, tw, q, p1, p2, sink);
+          kern<<<blocks, 256>>>(iters, tw, q, p1, p2, sink);
           return cudaGetLastError();
         },
         4, &ms);
+    if (e2 == cudaSuccess) {
+      // RNS form: two 32-bit butterflies per chain step; 64-bit form: one
+      const double rate = (double)threads * chains * iters * (form == 0 ? 2.0 : 1.0) / (ms * 1e-3);
+      if (rate > best) best = rate;
+    }
+    return e2;
+  };
+  if (e == cudaSuccess) {
+    // (chains, twiddles, blocks per SM): every configuration fits its
+    // register budget without spilling (ptxas -v)
+    if (form == 0) {
+      e = run(bfly_probe_kernel<true, 8, 8, 3>, 8, 3);
+      if (e == cudaSuccess) e = run(bfly_probe_kernel<true, 10, 2, 3>, 10, 3);
+      if (e == cudaSuccess) e = run(bfly_probe_kernel<true, 8, 4, 4>, 8, 4);
+      if (e == cudaSuccess) e = run(bfly_probe_kernel<true, 6, 2, 5>, 6, 5);
+      if (e == cudaSuccess) e = run(bfly_probe_kernel<true, 4, 2, 6>, 4, 6);
+    } else {
+      e = run(bfly_probe_kernel<false, 8, 4, 2>, 8, 2);
+      if (e == cudaSuccess) e = run(bfly_probe_kernel<false, 6, 2, 3>, 6, 3);
+      if (e == cudaSuccess) e = run(bfly_probe_kernel<false, 4, 4, 4>, 4, 4);
+    }
+  }
   cudaFree(tw);
   cudaFree(sink);
   if (e != cudaSuccess) return cuda_fail(e, "phe_probe_alu");
-  // RNS form: two 32-bit butterflies per chain step; 64-bit form: one
-  const double bfly = (double)threads * kProbeChains * iters * (form == 0 ? 2.0 : 1.0);
-  *per_s = bfly / (ms * 1e-3);
+  *per_s = best;
   return PHE_OK;
 }
 

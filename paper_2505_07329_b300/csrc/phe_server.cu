@@ -197,6 +197,11 @@ cudaError_t launch_iteration(phe_server* s, Iteration& it) {
     if (!t.n) continue;
     const u32 tiles = t.prefix[t.n];
     const u32 grid = s->cfg.blocks_per_sm ? std::min(tiles, (u32)c->num_sms * s->cfg.blocks_per_sm) : tiles;
+    const bool gemm = phe::body_on_tensor_cores(c, t);
+    if (!gemm) {
+      if ((e = phe::launch_lwedot(c, t, mode, (int)grid, s->stream)) != cudaSuccess) break;
+      continue;
+    }
     // the bodies' digit rows live for this table's launches only
     void* dig = nullptr;
     if ((e = phe::ctx_malloc_async(s->ctx, &dig, phe::body_scratch_bytes(t), s->stream)) != cudaSuccess) break;

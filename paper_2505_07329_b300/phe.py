@@ -131,6 +131,7 @@ SIGNATURES = {
     "phe_wire_unpack_inputs": (_i32, [_vp, _vp, _u64, _vp, _vp, _vp]),
     "phe_matmul_wire": (_i32, [_vp, _vp, _vp, _i32, _u32, _vp, _vp, _vp]),
     "phe_ctx_status": (_i32, [_vp, ctypes.POINTER(_u32), _i32]),
+    "phe_ctx_set_body_path": (_i32, [_vp, _u32]),
     "phe_probe_alu": (_i32, [_i32, _i32, _u32, ctypes.POINTER(ctypes.c_double)]),
     "phe_probe_tensor": (_i32, [_i32, _u32, ctypes.POINTER(ctypes.c_double)]),
 }
@@ -311,6 +312,14 @@ def phe_ctx_status(ctx, clear: bool = True) -> int:
     v = _u32()
     _check(lib().phe_ctx_status(ctx, ctypes.byref(v), 1 if clear else 0))
     return v.value
+
+
+PHE_BODY_AUTO, PHE_BODY_TENSOR, PHE_BODY_FUSED = 0, 1, 2
+
+
+def phe_ctx_set_body_path(ctx, path: int) -> None:
+    """Where the bodies run: PHE_BODY_AUTO (by size), PHE_BODY_TENSOR, PHE_BODY_FUSED."""
+    _check(lib().phe_ctx_set_body_path(ctx, path))
 
 
 def phe_probe_alu(device: int = 0, form: int = 0, iters: int = 0) -> float:

@@ -1,7 +1,7 @@
 """GPU parity of the bodies b'_tj = sum_k W[j,k] B_t[k] (mod q), which run on
 the tensor cores as an exact bf16 digit GEMM (tcgen05.mma, fp32 accumulation
 in chunks of 1024 columns), against the CPU oracle's Eq. (LWEdot), word for
-word.  The cases push the fp32 accumulators to their largest magnitude, cross
+word; the fused dp4a bodies (small launch groups) must give the same words.  The cases push the fp32 accumulators to their largest magnitude, cross
 the chunk boundaries, and leave ragged row, token and column tails."""
 import numpy as np
 import pytest
@@ -42,19 +42,26 @@ def _extreme_body(q):
 
 
 def _check(orc, ctx, q, W, A, B, direction=phe.PHE_FWD, Wdir=None):
+    """Bodies on the tensor cores (forced, whatever the size) against the
+    oracle, raw and switched; the fused bodies must give the same words."""
     Wdir = W if Wdir is None else Wdir
     rows = Wdir.shape[0]
     w = phe.phe_weights_upload(ctx, W, phe.PHE_DIR_FWD_BIT | phe.PHE_DIR_BWD_BIT)
     try:
         # the oracle's NTT products need a prime q; the RNS q takes the schoolbook definition
         ea, eb = orc.lwedot_all(Wdir, A, B, q, 1 if q == synth.Q60 else 0)
+        phe.phe_ctx_set_body_path(ctx, phe.PHE_BODY_TENSOR)
         ga, gb = gpu_matmul(ctx, w, direction, A, B, rows, phe.PHE_OUT_RAW)
         assert np.array_equal(gb, eb), "raw bodies differ"
         assert np.array_equal(ga, ea), "raw masks differ"
         sa, sb = gpu_matmul(ctx, w, direction, A, B, rows, phe.PHE_OUT_SWITCHED)
         assert np.array_equal(sb.astype(np.uint64), orc.modswitch(eb, q, 32)), "switched bodies differ"
         assert phe.phe_ctx_status(ctx) == 0
+        phe.phe_ctx_set_body_path(ctx, phe.PHE_BODY_FUSED)
+        fa, fb = gpu_matmul(ctx, w, direction, A, B, rows, phe.PHE_OUT_SWITCHED)
+        assert np.array_equal(fb, sb) and np.array_equal(fa, sa), "fused bodies differ"
     finally:
+        phe.phe_ctx_set_body_path(ctx, phe.PHE_BODY_AUTO)
         phe.phe_weights_free(w)
 
 

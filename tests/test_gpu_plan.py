@@ -76,19 +76,25 @@ def _check(orc, outs, refs, flags):
         assert np.array_equal(ga, ea) and np.array_equal(gb, eb)
 
 
+@pytest.mark.parametrize("path", [phe.PHE_BODY_TENSOR, phe.PHE_BODY_FUSED])
 @pytest.mark.parametrize("tune", [(16, 3), (4, 0), (64, 1), (1, 3)])
-def test_plan_run_matches_oracle(orc, env, tune):
+def test_plan_run_matches_oracle(orc, env, tune, path):
     ctx, Ws, ws, stream = env
     flags = phe.PHE_OUT_RAW if tune[0] == 4 else phe.PHE_OUT_SWITCHED
     jobs, outs, refs, _ = _make_jobs(Ws, ws, flags, seed=100 + tune[0])
-    plan = phe.phe_plan_create(ctx, jobs, flags, tune)
+    phe.phe_ctx_set_body_path(ctx, path)
+    try:
+        plan = phe.phe_plan_create(ctx, jobs, flags, tune)
+    finally:
+        phe.phe_ctx_set_body_path(ctx, phe.PHE_BODY_AUTO)
     try:
         info = phe.phe_plan_info(plan)
         assert info["tune"] == tune
         assert info["lwedot_launches"] == 1
-        # x shared by three products: per distinct input (3) an input transform and
-        # a body digit-row kernel, then one body GEMM and one lwedot launch
-        assert info["launches"] == 8
+        # x shared by three products: 3 distinct inputs, each with an input
+        # transform (and, with tensor-core bodies, a digit-row kernel), then
+        # the body GEMM (tensor-core bodies) and one lwedot launch
+        assert info["launches"] == (8 if path == phe.PHE_BODY_TENSOR else 4)
         phe.phe_plan_run(plan, stream)
         stream.synchronize()
         _check(orc, outs, refs, flags)
