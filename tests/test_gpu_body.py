@@ -1,8 +1,9 @@
 """GPU parity of the bodies b'_tj = sum_k W[j,k] B_t[k] (mod q), which run on
 the tensor cores as an exact bf16 digit GEMM (tcgen05.mma, fp32 accumulation
 in chunks of 1024 columns), against the CPU oracle's Eq. (LWEdot), word for
-word; the fused dp4a bodies (small launch groups) must give the same words.  The cases push the fp32 accumulators to their largest magnitude, cross
-the chunk boundaries, and leave ragged row, token and column tails."""
+word; the fused dp4a bodies (small launch groups) must give the same words.
+The cases push the fp32 accumulators to their largest magnitude, cross the
+chunk boundaries, and leave ragged row, token and column tails."""
 import numpy as np
 import pytest
 
