@@ -120,3 +120,32 @@ def test_sixteen_chunks(orc, ctxs):
     B = synth.uniform_words((T, L, N), q, 17)
     B[:, :, :] = np.where(np.arange(N) % 2 == 0, _extreme_body(q), B)
     _check(orc, ctxs("rns"), q, W, A, B)
+
+
+@pytest.mark.parametrize("d_in,rows,T", [(2048, 130, 3), (3000, 64, 9), (8192, 33, 2)])
+def test_power_of_two_modulus(orc, d_in, rows, T):
+    # the paper's q = 2^39 (N = 2048, computed exactly through p1 p2): bodies
+    # reduced mod 2^39 before the digit split and recombined mod 2^39, the
+    # switch a rounding shift to 2^26
+    q, k, Np = 1 << 39, 26, 2048
+    ctx = phe.phe_ctx_create(Np, q, k, 0, rns=(synth.RNS_P1, synth.RNS_P2))
+    L = synth.blocks(d_in, Np)
+    W = synth.weights(rows, d_in, seed=d_in)
+    W[0] = -127
+    A = synth.uniform_words((T, L, Np), q, 21)
+    B = synth.uniform_words((T, L, Np), q, 22)
+    w = phe.phe_weights_upload(ctx, W, phe.PHE_DIR_FWD_BIT)
+    try:
+        ea, eb = orc.lwedot_all(W, A, B, q, 0)
+        phe.phe_ctx_set_body_path(ctx, phe.PHE_BODY_TENSOR)
+        ga, gb = gpu_matmul(ctx, w, phe.PHE_FWD, A, B, rows, phe.PHE_OUT_RAW)
+        assert np.array_equal(gb, eb) and np.array_equal(ga, ea)
+        sa, sb = gpu_matmul(ctx, w, phe.PHE_FWD, A, B, rows, phe.PHE_OUT_SWITCHED)
+        assert np.array_equal(sb.astype(np.uint64), orc.modswitch(eb, q, k))
+        assert phe.phe_ctx_status(ctx) == 0
+        phe.phe_ctx_set_body_path(ctx, phe.PHE_BODY_FUSED)
+        fa, fb = gpu_matmul(ctx, w, phe.PHE_FWD, A, B, rows, phe.PHE_OUT_SWITCHED)
+        assert np.array_equal(fb, sb) and np.array_equal(fa, sa)
+    finally:
+        phe.phe_weights_free(w)
+        phe.phe_ctx_destroy(ctx)
