@@ -211,8 +211,11 @@ __global__ void __launch_bounds__(128, 1)
     mma_commit(done_bar);  // arrives when every MMA above has completed
   }
   __syncthreads();
-  const bool ok = mbar_wait(done_bar, 0);
-  if (!ok) atomicOr(status, kErrEpilogue);
+  const bool ok_self = mbar_wait(done_bar, 0);
+  if (!ok_self) atomicOr(status, kErrEpilogue);
+  // tcgen05.ld is warp-collective: a warp reads tensor memory only if every
+  // one of its threads saw the MMAs complete
+  const bool ok = __all_sync(0xffffffffu, ok_self);
   tc_fence_after();
   if (ok && !*abort_flag) {
     // epilogue: thread = row row0 + threadIdx.x (tensor-memory lane)

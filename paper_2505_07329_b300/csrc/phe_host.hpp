@@ -59,6 +59,11 @@ struct LweJobTable {
   u32 n;
   u32 prefix[kMaxJobs + 1];  // tile prefix sums
   LweJob j[kMaxJobs];
+  // Persistent launches (a grid smaller than the tiles): a device counter,
+  // zero at the launch, from which each CTA takes its next tile, so that
+  // tiles of unequal cost balance across the CTAs.  Null: a CTA takes tiles
+  // blockIdx.x, + gridDim.x, ...
+  u32* tile_counter = nullptr;
 };
 
 struct NttJob {             // forward transform of T*L input blocks

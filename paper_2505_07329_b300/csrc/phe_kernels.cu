@@ -322,8 +322,18 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, lwedot_min_blocks<Shape<LOGN
   const u64 q = rc.q, q4 = rc.q4;
   const u32 total = jt.prefix[jt.n];
   u32 seq = 0;
+  // Dynamic tiles (persistent launches): thread 0 takes the next tile from
+  // the launch's counter; two slots, so that the slot a thread reads is not
+  // the one thread 0 overwrites for the following tile.
+  __shared__ u32 next_tile[2];
+  u32 tile = blockIdx.x;
+  if (jt.tile_counter) {
+    if (threadIdx.x == 0) next_tile[0] = atomicAdd(jt.tile_counter, 1u);
+    __syncthreads();
+    tile = next_tile[0];
+  }
 
-  for (u32 tile = blockIdx.x; tile < total; tile += gridDim.x) {
+  for (u32 round = 1; tile < total; ++round) {
     u32 k = 0;
     while (tile >= jt.prefix[k + 1]) ++k;
     const LweJob& J = jt.j[k];
@@ -473,6 +483,13 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, lwedot_min_blocks<Shape<LOGN
         }
       }
     }
+    if (jt.tile_counter) {
+      if (threadIdx.x == 0) next_tile[round & 1] = atomicAdd(jt.tile_counter, 1u);
+      __syncthreads();
+      tile = next_tile[round & 1];
+    } else {
+      tile += gridDim.x;
+    }
   }
 }
 
@@ -617,7 +634,17 @@ static cudaError_t lwedot_impl(const phe_ctx* c, const LweJobTable& jt, int grid
   if (total == 0) return cudaSuccess;
   u32 grid = total;
   if (grid_limit > 0 && grid > (u32)grid_limit) grid = (u32)grid_limit;
-  lwedot_kernel<LOGN, MODE, RNS><<<grid, S::TPB, smem, s>>>(jt, rc, rk, tw0_of(c, RNS, true), twc_of(c, RNS, true));
+  if (jt.tile_counter && grid < total) {
+    // persistent: CTAs take tiles from the counter, zeroed for this launch
+    e = cudaMemsetAsync(jt.tile_counter, 0, sizeof(u32), s);
+    if (e != cudaSuccess) return e;
+    lwedot_kernel<LOGN, MODE, RNS><<<grid, S::TPB, smem, s>>>(jt, rc, rk, tw0_of(c, RNS, true), twc_of(c, RNS, true));
+  } else {
+    LweJobTable one_per_tile = jt;  // a CTA per tile: no counter
+    one_per_tile.tile_counter = nullptr;
+    lwedot_kernel<LOGN, MODE, RNS><<<grid, S::TPB, smem, s>>>(one_per_tile, rc, rk, tw0_of(c, RNS, true),
+                                                              twc_of(c, RNS, true));
+  }
   return cudaGetLastError();
 }
 

@@ -33,6 +33,7 @@ struct phe_plan {
   std::vector<phe::LweJobTable> tables;
   std::vector<void*> body_scratch;  // digit rows of the bodies, one buffer per table (tensor-core bodies)
   std::vector<char> gemm;           // per table: bodies on the tensor cores, else fused in lwedot
+  u32* tile_counters = nullptr;     // persistent grids: one tile counter per table
   std::vector<u32> grids;
   u64 scratch_bytes = 0;
   u64 modmuls = 0;
@@ -75,6 +76,7 @@ void destroy_plan(phe_plan* p) {
   }
   for (auto& in : p->inputs) cudaFree(in.ahat);
   for (void* b : p->body_scratch) cudaFree(b);
+  cudaFree(p->tile_counters);
   delete p;
 }
 
@@ -239,10 +241,19 @@ phe_status phe_plan_create(phe_ctx* c, const phe_job* jobs, uint32_t n_jobs, uin
     p->scratch_bytes += bytes;
     phe::assign_body_scratch(t, b);
   }
-  for (auto& t : p->tables) {
+  if (tn.blocks_per_sm && !p->tables.empty()) {
+    e = cudaMalloc(&p->tile_counters, p->tables.size() * sizeof(u32));
+    if (e != cudaSuccess) {
+      destroy_plan(p);
+      return cuda_fail(e, "phe_plan_create: cudaMalloc(tile counters)");
+    }
+  }
+  for (size_t i = 0; i < p->tables.size(); ++i) {
+    auto& t = p->tables[i];
     const u32 tiles = t.prefix[t.n];
     const u32 persistent = tn.blocks_per_sm ? (u32)c->num_sms * tn.blocks_per_sm : tiles;
     p->grids.push_back(std::min(tiles, persistent));
+    if (p->tile_counters) t.tile_counter = p->tile_counters + i;
   }
   *out = p;
   return PHE_OK;
@@ -346,7 +357,9 @@ phe_status phe_autotune(phe_ctx* c, const phe_job* jobs, uint32_t n_jobs, uint32
   if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
   cudaStream_t s = (cudaStream_t)stream;
   const uint32_t chunks[] = {2, 4, 8, 16, 32, 64};
-  const uint32_t bps[] = {0, 3};
+  // persistent grids first: a tie (their tiles balance through the counter)
+  // keeps the single persistent launch
+  const uint32_t bps[] = {3, 0};
   cudaEvent_t e0 = nullptr, e1 = nullptr;
   cudaError_t e = cudaEventCreate(&e0);
   if (e == cudaSuccess) e = cudaEventCreate(&e1);

@@ -86,6 +86,7 @@ struct phe_server {
   bool stop = false;
   std::thread worker;
   cudaStream_t stream = nullptr;
+  u32* tile_counters = nullptr;  // persistent grids: one per launch group of an iteration
   // accounting
   uint64_t reserved = 0, peak_reserved = 0;
   uint64_t submitted = 0, completed = 0, tokens_completed = 0, iterations = 0, failed = 0;
@@ -197,6 +198,7 @@ cudaError_t launch_iteration(phe_server* s, Iteration& it) {
     if (!t.n) continue;
     const u32 tiles = t.prefix[t.n];
     const u32 grid = s->cfg.blocks_per_sm ? std::min(tiles, (u32)c->num_sms * s->cfg.blocks_per_sm) : tiles;
+    t.tile_counter = s->tile_counters ? s->tile_counters + (&t - tables.data()) : nullptr;
     const bool gemm = phe::body_on_tensor_cores(c, t);
     if (!gemm) {
       if ((e = phe::launch_lwedot(c, t, mode, (int)grid, s->stream)) != cudaSuccess) break;
@@ -413,11 +415,16 @@ phe_status phe_server_create(phe_ctx* c, const phe_server_config* cfg, phe_serve
     cudaSetDevice(c->device);
     cudaError_t e = phe::prepare_launches(c);
     if (e == cudaSuccess) e = cudaStreamCreateWithFlags(&s->stream, cudaStreamNonBlocking);
-    if (prev >= 0) cudaSetDevice(prev);
+    // launch groups of up to kMaxJobs chunks: counters for every group an iteration can have
+    const size_t groups = cfg->max_jobs_per_iteration / phe::kMaxJobs + 1;
+    if (e == cudaSuccess && cfg->blocks_per_sm) e = cudaMalloc(&s->tile_counters, groups * sizeof(u32));
     if (e != cudaSuccess) {
+      if (s->stream) cudaStreamDestroy(s->stream);
+      if (prev >= 0) cudaSetDevice(prev);
       delete s;
       return fail(PHE_ECUDA, "phe_server_create: %s", cudaGetErrorString(e));
     }
+    if (prev >= 0) cudaSetDevice(prev);
   }
   s->worker = std::thread(worker_main, s);
   *out = s;
@@ -537,6 +544,7 @@ void phe_server_destroy(phe_server* s) {
     cudaStreamSynchronize(s->stream);
     cudaStreamDestroy(s->stream);
   }
+  if (s->tile_counters) cudaFree(s->tile_counters);
   delete s;
 }
 

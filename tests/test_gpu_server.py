@@ -165,3 +165,22 @@ def test_served_and_batched_forms_for_the_rns_and_power_of_two_moduli(q, rns, Nr
         for w in ws:
             phe.phe_weights_free(w)
         phe.phe_ctx_destroy(ctx)
+
+
+def test_persistent_grid_serves_the_same_words(env):
+    # one CTA per SM walking the iteration's tiles from a counter: the same
+    # words as the per-call path, for two requests of different shapes
+    ctx, Ws, ws = env
+    reqs = [_request(Ws, ws, 1, phe.PHE_FWD, 13, seed=70), _request(Ws, ws, 0, phe.PHE_BWD, 9, seed=71)]
+    srv = phe.phe_server_create(ctx, 256 << 20, chunk_tokens=4, tok_chunk=2, blocks_per_sm=1)
+    try:
+        ids = [_submit(srv, ws, r) for r in reqs]
+        for i in ids:
+            phe.phe_server_wait(srv, i, 60000)
+    finally:
+        phe.phe_server_destroy(srv)
+    for r in reqs:
+        rows = r["W"].shape[0]
+        ga, gb = gpu_matmul(ctx, ws[r["pi"]], r["dir"], r["A"], r["B"], rows)
+        got = _result(r)
+        assert np.array_equal(got[0], ga) and np.array_equal(got[1], gb)
