@@ -38,16 +38,15 @@ import synth  # noqa: E402
 
 METRIC = "encrypted W·[x] tokens/s per Llama-1B layer; p50/p99 latency; % of roofline"
 # DRAM bytes (read + write) of one lwedot_kernel launch of the batched form
-# (all 14 products of the layer workload, RNS modulus, tuning (16, 0)) as a
-# function of the launch's tokens T: a + b T, from ncu captures of the same
-# launch at T = 2 and T = 4 (dram__bytes_read.sum + dram__bytes_write.sum:
-# 4.749 and 6.222 GB).  a is what a launch reads once whatever its tokens
-# (the encoded weights), b what each token adds (its transformed masks and
-# its outputs).  Valid only for the kernel sources the counters were taken
-# on (kernel_source_hash) and that tuning.
-TRAFFIC_KERNEL_HASH = "f97d7ed5d41f7f37"
-TRAFFIC_TUNING = (16, 0)
-TRAFFIC_FIT = (3276.48e6, 736.465e6)
+# (all 14 products of the layer workload, RNS modulus) as a function of the
+# launch's tokens T: a + b T, from ncu captures of the same launch at T = 2
+# and T = 4 (dram__bytes_read.sum + dram__bytes_write.sum), one fit per
+# tuning (tokens per tile, blocks per SM).  a is what a launch reads once
+# whatever its tokens (the encoded weights), b what each token adds (its
+# transformed masks and its outputs).  Valid only for the kernel sources the
+# counters were taken on (kernel_source_hash) and those tunings.
+TRAFFIC_KERNEL_HASH = "448bd42d009c5ec2"
+TRAFFIC_FITS = {(16, 0): (3274.74e6, 736.938e6), (16, 3): (3262.17e6, 741.483e6)}
 
 
 def lwedot_alg_bytes(wl, T: int) -> float:
@@ -683,12 +682,12 @@ def main():
     achieved = modmuls / (kernel_ms / 1e3) / 1e9 if kernel_ms else None
     peak = alu["gmodmul"]
     unit_bound = unit_bound_gmodmul(clk.get("sm_max_mhz") or 2032.0) if args.modulus == "rns" else None
+    fit = TRAFFIC_FITS.get(tuple(tuning)) if tuning is not None else None
     traffic_ok = (kernel_source_hash() == TRAFFIC_KERNEL_HASH and wl.name == "layer"
-                  and args.form == "batched" and args.modulus == "rns" and T % bchunk == 0
-                  and tuning is not None and tuple(tuning) == TRAFFIC_TUNING)
+                  and args.form == "batched" and args.modulus == "rns" and T % bchunk == 0 and fit is not None)
     roof = {"bound": "alu", "unit": "Gmodmul/s", "achieved": achieved, "peak": peak,
             "frac": (achieved / peak) if achieved and peak else None,
-            "traffic": (TRAFFIC_FIT[0] + TRAFFIC_FIT[1] * bchunk) if traffic_ok else None,
+            "traffic": (fit[0] + fit[1] * bchunk) if traffic_ok else None,
             "traffic_alg_bytes": lwedot_alg_bytes(wl, bchunk),
             "traffic_basis": ("per launch of --batch-chunk tokens: a + b T from ncu DRAM counters of the same launch "
                               "at T = 2 and 4 (profiles/lwedot_kernel_rns_llama1b_layer_dram_traffic.md)"),
