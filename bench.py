@@ -132,6 +132,8 @@ def parse():
     ap.add_argument("--serve-light-load", type=float, default=0.6,
                     help="second serving measurement, below capacity: arrival rate as this fraction of the rate "
                          "served in the saturated run (same request count; 0 = skip)")
+    ap.add_argument("--serve-bps", type=int, default=-1,
+                    help="served form's persistent grid, blocks per SM (-1: the autotuned plans' choice)")
     ap.add_argument("--serving-only", action="store_true",
                     help="skip the timed layer steps' side measurements and run only the serving measurements")
     return ap.parse_args()
@@ -777,14 +779,15 @@ def main():
         for pl in plans:
             phe.phe_plan_destroy(pl)
         plans = []
+        sbps = args.serve_bps if args.serve_bps >= 0 else (tuning[1] if tuning else 0)
         serving = measure_serving(phe, ctx, weights, wl, inputs, keys, args.serve_requests, args.serve_rate, T,
-                                  tuning[0] if tuning else 8)
+                                  tuning[0] if tuning else 8, sbps)
         if args.serve_light_load > 0:
             # the same request mix below the capacity the saturated run
             # measured: latency without a standing queue
             light = args.serve_light_load * serving["served_req_s"]
             serving["light_load"] = measure_serving(phe, ctx, weights, wl, inputs, keys, args.serve_requests, light,
-                                                    T, tuning[0] if tuning else 8)
+                                                    T, tuning[0] if tuning else 8, sbps)
             serving["light_load"]["rate_basis"] = (f"{args.serve_light_load} x the saturated run's served "
                                                    f"{serving['served_req_s']:.2f} req/s")
         # the plain per-call form on the first requests of the same stream
@@ -948,7 +951,7 @@ def sanity_decrypt(wl, mm, inputs, keys, outs, S, T, chunk):
     return f"{ok}/{tot}"
 
 
-def measure_serving(phe, ctx, weights, wl, inputs, keys, n_requests, rate, T_avail, tok_chunk=8):
+def measure_serving(phe, ctx, weights, wl, inputs, keys, n_requests, rate, T_avail, tok_chunk=8, blocks_per_sm=0):
     """The served form: requests from 64 clients arrive as a Poisson process
     (mean `rate` per second); each is one projection of the layer in one
     direction with U{64..2048} tokens (its inputs are slices of the resident
@@ -961,7 +964,8 @@ def measure_serving(phe, ctx, weights, wl, inputs, keys, n_requests, rate, T_ava
     dirs = r.integers(0, 2, size=n_requests)
     toks = r.integers(64, 2049, size=n_requests)
     N = wl.ring.N
-    srv = phe.phe_server_create(ctx, 24 << 30, chunk_tokens=32, tok_chunk=tok_chunk, blocks_per_sm=0, max_active=64,
+    srv = phe.phe_server_create(ctx, 24 << 30, chunk_tokens=32, tok_chunk=tok_chunk, blocks_per_sm=blocks_per_sm,
+                                max_active=64,
                                 max_jobs_per_iteration=64, max_queue=4096, wait_timeout_ms=600000)
     ids = []
     items = 0
@@ -995,6 +999,7 @@ def measure_serving(phe, ctx, weights, wl, inputs, keys, n_requests, rate, T_ava
             "served_tokens_s": tokens / busy, "layer_equiv_tokens_s": items / busy / per_layer_token,
             "p50_ms": st["p50_ms"], "p99_ms": st["p99_ms"], "max_ms": st["max_ms"], "mean_ms": st["mean_ms"],
             "iterations": st["iterations"], "mem_budget_bytes": 24 << 30,
+            "grid": {"tok_chunk": tok_chunk, "blocks_per_sm": blocks_per_sm},
             "peak_reserved_bytes": st["peak_reserved_bytes"],
             # saturated: the queue takes long to drain after the last arrival
             "saturated": bool(wall - float(arrivals[-1]) > 0.25 * wall),

@@ -149,3 +149,19 @@ def test_power_of_two_modulus(orc, d_in, rows, T):
     finally:
         phe.phe_weights_free(w)
         phe.phe_ctx_destroy(ctx)
+
+
+@pytest.mark.parametrize("Nr,d_in,rows,T", [(256, 700, 130, 5), (8192, 9000, 40, 3)])
+def test_other_ring_degrees(orc, Nr, d_in, rows, T):
+    # the bodies' token stride is L*N words: ring degrees at both ends, with
+    # ragged last blocks, through the tensor cores and fused
+    q = synth.Q60
+    ctx = phe.phe_ctx_create(Nr, q, 32, 0)
+    L = synth.blocks(d_in, Nr)
+    W = synth.weights(rows, d_in, seed=Nr)
+    A = synth.uniform_words((T, L, Nr), q, 31)
+    B = synth.uniform_words((T, L, Nr), q, 32)
+    try:
+        _check(orc, ctx, q, W, A, B)
+    finally:
+        phe.phe_ctx_destroy(ctx)
