@@ -120,8 +120,10 @@ def parse():
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--paper-table", type=int, default=1,
                     help="1: also time the shapes of the paper's timing table at its parameter set (N=2048, q=2^39)")
-    ap.add_argument("--packed-tokens", type=int, default=16,
+    ap.add_argument("--packed-tokens", type=int, default=64,
                     help="tokens of the packed-output measurement (Eq. (pack_rotate) after each product; 0 = skip)")
+    ap.add_argument("--packed-chunk", type=int, default=32,
+                    help="tokens per chunk of the packed host-buffer call (its two streams overlap chunks)")
     ap.add_argument("--no-cpu", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--modulus", choices=["rns", "prime"], default="rns",
@@ -763,15 +765,19 @@ def main():
     packed = None
     if args.packed_tokens > 0:
         packed = measure_packed(phe, ctx, weights, wl, mm, keys, inputs, S, q, min(args.packed_tokens, T), stream,
-                                gen, dev, alu)
+                                gen, dev, alu, args.packed_chunk)
     # The end-to-end figure the line leads with is the paper's server path as
     # a client sees it: host buffers in, Eq. (LWEdot), the packing of
     # Eq. (pack_rotate) and the switch, packed RLWE results back to host.
     e2e = None
+    e2e_dense = None
     if packed is not None and not args.no_e2e:
         e2e = dict(packed["e2e"])
         e2e["path"] = ("phe_matmul_packed_host over the layer's 14 products: pinned host inputs -> device, "
-                       "Eq. (LWEdot), Eq. (pack_rotate), switch, packed RLWE results -> pinned host")
+                       "Eq. (LWEdot), Eq. (pack_rotate), switch, packed RLWE results (one token per RLWE) "
+                       "-> pinned host")
+        e2e_dense = dict(packed["dense"]["e2e"])
+        e2e_dense["path"] = "the same call with PHE_PACK_DENSE: floor(N/rows) tokens per RLWE where rows <= N/2"
 
     serving = None
     if args.serve_requests > 0 and wl.name == "layer":
@@ -827,7 +833,7 @@ def main():
                 "packed": packed,
                 "paper_table": paper_table,
                 "roofline": roof, "roofline_body": roof_body, "cpu_baseline": cpu, "e2e": e2e,
-                "e2e_unpacked": e2e_unpacked, "gpu_launches": gpu_launches,
+                "e2e_unpacked": e2e_unpacked, "e2e_packed_dense": e2e_dense, "gpu_launches": gpu_launches,
                 "kernels": {k: {"launches": v["launches"], "total_ms": v["total_ms"]} for k, v in trace.items()},
                 "clocks": clk, "sanity_decrypt": check}
         print(json.dumps(line))
@@ -1178,36 +1184,44 @@ def client_ksk(phe, ctx, S, N, q, base_log, gen, dev):
     return KA.cpu().numpy().view(np.uint64), KB.cpu().numpy().view(np.uint64)
 
 
-def measure_packed(phe, ctx, weights, wl, mm, keys, inputs, S, q, tokens, stream, gen, dev, alu):
+def measure_packed(phe, ctx, weights, wl, mm, keys, inputs, S, q, tokens, stream, gen, dev, alu, host_chunk=32):
     """The whole server path of the paper, Eq. (LWEdot) then the packing of
     Eq. (pack_rotate) and the switch: every product of the layer through
     phe_matmul_packed on `tokens` resident tokens (device-timed), then the
     same through the host-buffer call phe_matmul_packed_host (wall-clock,
-    copies included).  Decomp: one level of base 2^26."""
+    copies included).  Decomp: one level of base 2^26.  Two output layouts:
+    one token per RLWE (the paper's), and dense packing (PHE_PACK_DENSE:
+    floor(N/rows) tokens per RLWE for products of at most N/2 rows)."""
     import torch
     N = wl.ring.N
     base_log = 26
     KA, KB = client_ksk(phe, ctx, S, N, q, base_log, gen, dev)
     k = phe.phe_ksk_upload(ctx, KA, KB, base_log, 1)
     del KA, KB
-    try:
-        outs = []
-        for (pi, name, d, rows, cols, L) in mm:
-            G = (rows + N - 1) // N
-            outs.append((torch.empty((tokens, G, N), dtype=torch.int32, device=dev),
-                         torch.empty((tokens, G, N), dtype=torch.int32, device=dev)))
+    steps = 2
+    lg = int(math.log2(N))
+    host_in = {key: (A[:tokens].cpu().pin_memory(), B[:tokens].cpu().pin_memory())
+               for key, (A, B, X) in inputs.items()}
+    h2d = sum(2 * tokens * L * N * 8 for (_, _, _, _, _, L) in mm)
+
+    def layout(flags):
+        return [phe.phe_pack_layout(N, rows, tokens, flags)[0] for (_, _, _, rows, _, _) in mm]
+
+    def run(flags):
+        units = layout(flags)
+        outs = [(torch.empty((u, N), dtype=torch.int32, device=dev), torch.empty((u, N), dtype=torch.int32, device=dev))
+                for u in units]
 
         def step():
             for n, (pi, name, d, rows, cols, L) in enumerate(mm):
                 A, B, _ = inputs[keys[(pi, d)][0]]
                 phe.phe_matmul_packed(ctx, weights[pi], k, phe.PHE_FWD if d == "fwd" else phe.PHE_BWD, tokens,
-                                      A[:tokens], B[:tokens], outs[n][0], outs[n][1], phe.PHE_OUT_SWITCHED, stream)
+                                      A[:tokens], B[:tokens], outs[n][0], outs[n][1], flags, stream)
 
         step()
         torch.cuda.synchronize()
         phe.phe_trace_enable(ctx, True)
         phe.phe_trace_read(ctx)
-        steps = 2
         a = torch.cuda.Event(enable_timing=True)
         b = torch.cuda.Event(enable_timing=True)
         a.record(stream)
@@ -1218,43 +1232,41 @@ def measure_packed(phe, ctx, weights, wl, mm, keys, inputs, S, q, tokens, stream
         ms = a.elapsed_time(b)
         tr = phe.phe_trace_read(ctx)
         phe.phe_trace_enable(ctx, False)
-        kern = {n: round(v["total_ms"] / steps / tokens, 4) for n, v in tr.items()
-                if n.endswith("_kernel")}
+        kern = {n: round(v["total_ms"] / steps / tokens, 4) for n, v in tr.items() if n.endswith("_kernel")}
         # rooflines of the packing's two main kernels, per layer token: the
         # digit transforms (ALU: 32-bit butterflies, two residues) and the MAC
         # (HBM: transformed digits once, the key once per 8 units)
-        units = sum((rows + N - 1) // N for (_, _, _, rows, _, _) in mm)
-        lg = int(math.log2(N))
-        bfly = units * N * (N // 2) * lg * 2
-        mac_bytes = units * (N * N * 8 + 2 * N * N * 16 / 8)
-        pack_roof = []
+        upt = sum(units) / tokens   # units (output RLWEs) per layer token
+        bfly = upt * N * (N // 2) * lg * 2
+        mac_bytes = upt * (N * N * 8 + 2 * N * N * 16 / 8)
+        roof = []
         if kern.get("input_ntt_kernel"):
             ach = bfly / (kern["input_ntt_kernel"] / 1e3) / 1e9
             peak = alu["bfly_per_s"] / 1e9  # this run's probe (32-bit butterflies)
-            pack_roof.append({"kernel": "input_ntt_kernel (digit rows)", "bound": "alu", "unit": "G 32-bit bfly/s",
-                              "achieved": ach, "peak": peak, "frac": ach / peak,
-                              "note": "the kernel time also holds the 16 input-mask transforms, < 1%"})
+            roof.append({"kernel": "input_ntt_kernel (digit rows)", "bound": "alu", "unit": "G 32-bit bfly/s",
+                         "achieved": ach, "peak": peak, "frac": ach / peak,
+                         "note": "the kernel time also holds the 16 input-mask transforms, < 1%"})
         if kern.get("pack_mac_kernel"):
             ach = mac_bytes / (kern["pack_mac_kernel"] / 1e3) / 1e9
-            pack_roof.append({"kernel": "pack_mac_kernel", "bound": "hbm", "unit": "GB/s", "achieved": ach,
-                              "peak": HBM_GBPS, "frac": ach / HBM_GBPS})
-        # client-side check: RLWE of the first product, first token, first group
+            roof.append({"kernel": "pack_mac_kernel", "bound": "hbm", "unit": "GB/s", "achieved": ach,
+                         "peak": HBM_GBPS, "frac": ach / HBM_GBPS})
+        # client-side check: the first product's first RLWE, every token it holds
         pi, name, d, rows, cols, L = mm[0]
+        _, tpu = phe.phe_pack_layout(N, rows, tokens, flags)
         _, _, X = inputs[keys[(pi, d)][0]]
         W = synth.weights(wl.projections[pi][2], wl.projections[pi][1], seed=synth.SEED_W + pi)
         Wd = W if d == "fwd" else W.T
-        y = Wd[:min(rows, N)].astype(np.int64) @ X[0].cpu().numpy().astype(np.int64)
-        pa = outs[0][0][0, 0].cpu().numpy().view(np.uint32)
-        pb = outs[0][1][0, 0].cpu().numpy().view(np.uint32).astype(np.int64)
+        m = min(rows, N)
+        y = np.concatenate([Wd[:m].astype(np.int64) @ X[t].cpu().numpy().astype(np.int64)
+                            for t in range(min(tpu, tokens))])
+        pa = outs[0][0][0].cpu().numpy().view(np.uint32)
+        pb = outs[0][1][0].cpu().numpy().view(np.uint32).astype(np.int64)
         ph = (pb - _negacyclic_small(pa, S.cpu().numpy().astype(np.int64), 1 << 32)) % (1 << 32)
         t = synth.T_PLAIN
         dec = ((ph * t + (1 << 31)) >> 32) % t
         ok = int(np.sum((dec[:y.shape[0]] - y) % t == 0))
         zero = int(np.sum(dec[y.shape[0]:] == 0))
-        out_bytes = sum(2 * ((rows + N - 1) // N) * N * 4 for (_, _, _, rows, _, _) in mm)
         # end to end with host buffers
-        host_in = {key: (A[:tokens].cpu().pin_memory(), B[:tokens].cpu().pin_memory())
-                   for key, (A, B, X) in inputs.items()}
         houts = [(torch.empty(o[0].shape, dtype=torch.int32).pin_memory(),
                   torch.empty(o[1].shape, dtype=torch.int32).pin_memory()) for o in outs]
 
@@ -1262,7 +1274,7 @@ def measure_packed(phe, ctx, weights, wl, mm, keys, inputs, S, q, tokens, stream
             for n, (pi, name, d, rows, cols, L) in enumerate(mm):
                 hA, hB = host_in[keys[(pi, d)][0]]
                 phe.phe_matmul_packed_host(ctx, weights[pi], k, phe.PHE_FWD if d == "fwd" else phe.PHE_BWD, tokens,
-                                           hA, hB, houts[n][0], houts[n][1], phe.PHE_OUT_SWITCHED, 8, stream)
+                                           hA, hB, houts[n][0], houts[n][1], flags, host_chunk, stream)
 
         host_step()
         t0 = time.perf_counter()
@@ -1270,19 +1282,27 @@ def measure_packed(phe, ctx, weights, wl, mm, keys, inputs, S, q, tokens, stream
             host_step()
         torch.cuda.synchronize()
         dt = time.perf_counter() - t0
-        h2d = sum(2 * tokens * L * N * 8 for (_, _, _, _, _, L) in mm)
+        out_bytes = sum(units) * 2 * N * 4
+        return {"value": tokens * steps / (ms / 1e3), "unit": "tokens/s", "tokens": tokens,
+                "ms_per_token": ms / steps / tokens, "kernel_ms_per_token": kern, "rlwe_per_token": upt,
+                "roofline": roof, "out_bytes_per_token": out_bytes / tokens,
+                "sanity_decrypt": f"{ok}/{y.shape[0]} coefficients of {min(tpu, tokens)} token(s), "
+                                  f"{zero}/{N - y.shape[0]} unused zero",
+                "e2e": {"value": tokens * steps / dt, "unit": "tokens/s", "h2d_bytes_per_step": h2d,
+                        "d2h_bytes_per_step": out_bytes, "tokens_per_step": tokens, "tok_chunk": host_chunk}}
+
+    try:
+        res = run(phe.PHE_OUT_SWITCHED)
+        res["dense"] = run(phe.PHE_OUT_SWITCHED | phe.PHE_PACK_DENSE)
+        res["dense"]["layout"] = ("PHE_PACK_DENSE: floor(N/rows) consecutive tokens per RLWE for products of at "
+                                  "most N/2 rows (not in the paper, which packs one token per RLWE)")
         wire = measure_wire(phe, ctx, N, weights[mm[0][0]], k, mm[0], tokens, stream, dev)
     finally:
         phe.phe_ksk_free(k)
-    return {"value": tokens * steps / (ms / 1e3), "unit": "tokens/s", "tokens": tokens,
-            "ms_per_token": ms / steps / tokens, "kernel_ms_per_token": kern,
-            "ksk": {"base_log": base_log, "ell": 1, "device_bytes": 2 * N * N * 16},
-            "roofline": pack_roof,
-            "out_bytes_per_token": out_bytes, "unpacked_out_bytes_per_token": out_bytes_per_token(wl),
-            "sanity_decrypt": f"{ok}/{y.shape[0]} coefficients, {zero}/{N - y.shape[0]} unused zero",
-            "e2e": {"value": tokens * steps / dt, "unit": "tokens/s", "h2d_bytes_per_step": h2d,
-                    "d2h_bytes_per_step": out_bytes * tokens, "tokens_per_step": tokens},
-            "wire": wire}
+    res.update({"ksk": {"base_log": base_log, "ell": 1, "device_bytes": 2 * N * N * 16},
+                "layout": "one token per RLWE (Eq. (pack_rotate) over a token's outputs)",
+                "unpacked_out_bytes_per_token": out_bytes_per_token(wl), "wire": wire})
+    return res
 
 
 def measure_wire(phe, ctx, N, w, k, prod, tokens, stream, dev, reps=3):

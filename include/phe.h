@@ -99,6 +99,7 @@ typedef struct phe_params {
 
 #define PHE_OUT_SWITCHED 0u    /* outputs mod q' = 2^k as uint32 (the protocol's result) */
 #define PHE_OUT_RAW 1u         /* outputs mod q as uint64, no switch (testing, unfused use) */
+#define PHE_PACK_DENSE 2u      /* packing calls only: several tokens per output RLWE (phe_pack_layout) */
 
 /* Name of a status code.  Never fails. */
 const char* phe_status_string(phe_status s);
@@ -417,6 +418,16 @@ void phe_server_destroy(phe_server* srv);
  * j >= m).  This replaces rows*(N+1) words per token by G*2N,
  * G = ceil(rows/N).
  *
+ * Dense packing (flags | PHE_PACK_DENSE; not in the paper, which packs one
+ * token's outputs per RLWE): for rows <= N/2, the outputs of tpu =
+ * floor(N/rows) consecutive tokens share one RLWE, token t's row r at
+ * coefficient (t mod tpu)*rows + r of RLWE floor(t/tpu); the last RLWE holds
+ * the remaining T mod tpu tokens (if any) and zeros past them.  The same sum
+ * of Eq. (pack_rotate) over a longer list of LWE ciphertexts: ceil(T/tpu)
+ * RLWEs instead of T, and as many fewer key-switching contractions.  For
+ * rows > N/2 the flag changes nothing.  Output buffers hold units*N words
+ * (phe_pack_layout), unit-major.
+ *
  * KeySwitching of (a, b) under the LWE key s (dimension n = N: the RLWE key's
  * coefficients, as SampleExtract leaves them) to the RLWE key S' is
  *     (A', B') = (0, b) - sum_{i<n} sum_{l<ell} d_l(a_i) KSK_{i,l},
@@ -446,24 +457,34 @@ phe_status phe_ksk_upload(phe_ctx* ctx, const uint64_t* h_ka, const uint64_t* h_
 void phe_ksk_free(phe_ksk* k);
 uint64_t phe_ksk_device_bytes(const phe_ksk* k);
 
+/* Output RLWEs (units) of T tokens of `rows` outputs each at ring degree N,
+ * and the tokens each packs (1 unless flags has PHE_PACK_DENSE and
+ * 2*rows <= N).  Host only.  Errors: PHE_EINVAL (N not a power of two,
+ * rows = 0, unknown flags). */
+phe_status phe_pack_layout(uint32_t N, uint32_t rows, uint32_t T, uint32_t flags, uint64_t* units,
+                           uint32_t* tokens_per_unit);
+
 /* Packs T x rows given LWE ciphertexts of dimension N.
  *   d_lwe_mask  [T][rows][N] uint64 words below q (as phe_matmul writes with PHE_OUT_RAW;
  *               larger words give unspecified results, never a fault); 16-byte aligned
  *   d_lwe_body  [T][rows]    uint64 mod q
  *   d_out_a, d_out_b  [T][G][N]: uint32 words mod 2^log2_qout (PHE_OUT_SWITCHED)
  *               or uint64 mod q (PHE_OUT_RAW); RLWE_g of token t at (t*G + g)*N.
- * Allocates its scratch (at most 2 GiB of digit rows at a time) on `stream`
+ *               With PHE_PACK_DENSE: [units][N] (phe_pack_layout).
+ * Allocates its scratch (at most 4 GiB of digit rows at a time) on `stream`
  * from the context's memory pool.  Errors: PHE_EINVAL (handles, flags,
- * T*G > 2^24, unaligned masks), PHE_ENOMEM, PHE_ECUDA. */
+ * more than 2^24 output RLWEs, unaligned masks), PHE_ENOMEM, PHE_ECUDA. */
 phe_status phe_pack(phe_ctx* ctx, const phe_ksk* k, uint32_t T, uint32_t rows, const uint64_t* d_lwe_mask,
                      const uint64_t* d_lwe_body, void* d_out_a, void* d_out_b, uint32_t flags, void* stream);
 
 /* The paper's whole server path, Eq. (LWEdot) then Eq. (pack_rotate), token
  * chunk by token chunk: the product kernel switches the LWE masks straight to
  * the gadget modulus B^ell (all that Decomp reads) and keeps the bodies mod
- * q, in a scratch buffer of at most 2 GiB, then the packing runs on them.
- * The result equals phe_matmul (PHE_OUT_RAW) followed by phe_pack.  Inputs
- * as phe_matmul; outputs as phe_pack with rows of direction `dir`. */
+ * q, in a scratch buffer of at most 2 GiB (or one unit's tokens, if more),
+ * then the packing runs on them.  The result equals phe_matmul (PHE_OUT_RAW)
+ * followed by phe_pack with the same flags.  Inputs as phe_matmul; outputs
+ * and flags (PHE_OUT_RAW, PHE_PACK_DENSE) as phe_pack with rows of
+ * direction `dir`. */
 phe_status phe_matmul_packed(phe_ctx* ctx, const phe_weights* w, const phe_ksk* k, int dir, uint32_t T,
                              const uint64_t* d_in_mask, const uint64_t* d_in_body, void* d_out_a, void* d_out_b,
                              uint32_t flags, void* stream);
@@ -474,7 +495,8 @@ phe_status phe_matmul_packed_seeded(phe_ctx* ctx, const phe_weights* w, const ph
                                     void* d_out_b, uint32_t flags, void* stream);
 
 /* phe_matmul_packed with HOST buffers, `tok_chunk` tokens at a time (0
- * selects 8): inputs host->device, the packed path, packed outputs
+ * selects 8; with PHE_PACK_DENSE rounded down to whole units, at least
+ * one): inputs host->device, the packed path, packed outputs
  * device->host, double-buffered on two streams.  h_* have the layouts of the
  * device buffers above; page-locked host memory makes the copies
  * asynchronous.  Blocking: returns after the last result has reached the

@@ -10,6 +10,7 @@
 // products.  Kernels:
 //   pack_decompose_kernel  digits d_l(a_j[i]) of the masks, transposed so
 //                          that D_il is a row over j (natural order, mod q)
+// A unit is one output RLWE and the LWE ciphertexts it packs (PackGeom).
 //   input_ntt_kernel       D_il (int32 digits) -> NTT domain
 //   pack_mac_kernel        per NTT slot: sum over (i,l) of D_hat * KSK_hat
 //                          (the key carries -N^-1 and Shoup quotients)
@@ -72,28 +73,56 @@ __device__ __forceinline__ void signed_digits(u32 v, u32 base_log, int (&d)[ELL]
   }
 }
 
+// Which LWE ciphertexts each unit (one output RLWE) packs.  The LWE outputs
+// of a call are numbered f = t*rows + r (token t, output row r).  With
+// G = ceil(rows/N) > 1, unit u is group g = u % G of token t = u / G: rows
+// gN .. of that token.  With G = 1, unit u holds the outputs of `tpu`
+// consecutive tokens, f = u*tpu*rows onwards: tpu = 1 packs each token on
+// its own (Eq. (pack_rotate) per token), tpu = floor(N/rows) > 1 fills the
+// ring with several tokens (dense packing).  Coefficient j of the unit's
+// RLWE carries LWE f0 + j for j < m, and zero past m.
+struct PackGeom {
+  u32 rows;   // LWE outputs per token
+  u32 G;      // ceil(rows / N)
+  u32 tpu;    // tokens per unit (1 unless G = 1 and dense)
+  u64 nflat;  // T * rows: the LWE outputs in the buffers the kernels index
+};
+
+__device__ __forceinline__ void unit_span(const PackGeom& pg, u32 N, u32 u, u64& f0, u32& m) {
+  if (pg.G > 1) {
+    const u32 t = u / pg.G, g = u % pg.G;
+    f0 = (u64)t * pg.rows + (u64)g * N;
+    m = min(N, pg.rows - g * N);
+  } else {
+    f0 = (u64)u * pg.tpu * pg.rows;
+    m = (u32)min((u64)pg.tpu * pg.rows, pg.nflat - f0);
+  }
+}
+
 // Masks [T][rows][N] -> digit rows D[u][i*ell + l][j] of the units
-// u_base + u, unit = t*G + g, holding the signed digit d_l(a_{gN+j}[i]) for
-// gN + j < rows and 0 past the last row.  SWITCHED: the masks are already
+// u_base + u, holding the signed digit d_l(a_{f0+j}[i]) of the unit's LWE
+// f0 + j for j < m and 0 past it (unit_span).  SWITCHED: the masks are already
 // a~ (uint32, switched to B^ell by the product kernel's epilogue); otherwise
 // they are words below q, switched here with rcK (log2_qout = base_log*ell).
 // A block moves a 64 (i) x 32 (j) tile through shared memory, so that both
 // the load (two words of i per thread) and the store (along j) are coalesced.
 template <int ELL, bool SWITCHED>
 __global__ void __launch_bounds__(256)
-    pack_decompose_kernel(const void* __restrict__ maskv, u32 rows, u32 N, u32 G, u32 u_base, u32 base_log,
+    pack_decompose_kernel(const void* __restrict__ maskv, PackGeom pg, u32 N, u32 u_base, u32 base_log,
                           RingConst rcK, RnsConst rkK, int32_t* __restrict__ D) {
   __shared__ int tile[ELL][64][33];
   const u32 u = blockIdx.z;  // unit within the chunk; D holds the chunk's units
-  const u32 t = (u_base + u) / G, g = (u_base + u) % G;
+  u64 f0;
+  u32 mu;
+  unit_span(pg, N, u_base + u, f0, mu);
   const u32 i0 = blockIdx.x * 64, j0 = blockIdx.y * 32;
   const u32 tx = threadIdx.x, ty = threadIdx.y;
-  const size_t first = ((size_t)t * rows + (size_t)g * N + j0) * N + i0;  // mask word (row gN+j0, column i0)
+  const size_t first = ((size_t)f0 + j0) * N + i0;  // mask word (LWE f0+j0, column i0)
 #pragma unroll
   for (u32 m = 0; m < 4; ++m) {
     const u32 k = ty + 8 * m;
     int d0[ELL], d1[ELL];
-    if (g * N + j0 + k < rows) {
+    if (j0 + k < mu) {
       u32 v0, v1;
       if constexpr (SWITCHED) {
         const uint2 v = *reinterpret_cast<const uint2*>(static_cast<const u32*>(maskv) + first + (size_t)k * N + 2 * tx);
@@ -286,12 +315,12 @@ __global__ void __launch_bounds__(256, 2)
   cp_async_wait<0>();  // no copy outlives the block
 }
 
-// Inverse transform of P_hat[u][c] (c = 0: A, c = 1: B), + b_{gN+m} at
-// coefficient m of B for the group's rows, then the switch (or raw words).
+// Inverse transform of P_hat[u][c] (c = 0: A, c = 1: B), + b_{f0+j} at
+// coefficient j of B for the unit's LWEs, then the switch (or raw words).
 // Block b = u*2 + c of the chunk; u_base is the chunk's first unit.
 template <int LOGN, bool RNS, int MODE>
 __global__ void __launch_bounds__(Shape<LOGN>::TPB)
-    pack_finish_kernel(const u64* __restrict__ Phat, u32 nseg, const u64* __restrict__ body, u32 rows, u32 G,
+    pack_finish_kernel(const u64* __restrict__ Phat, u32 nseg, const u64* __restrict__ body, PackGeom pg,
                        u32 u_base, u32 units, void* __restrict__ out_a, void* __restrict__ out_b, RingConst rc,
                        RnsConst rk, const void* __restrict__ tw0v, const void* __restrict__ twcv) {
   using S = Shape<LOGN>;
@@ -345,18 +374,19 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB)
   }
   if (!active) return;
   const u32 u = u_base + b / 2, comp = b % 2;
-  const u32 t = u / G, g = u % G;
+  u64 f0;
+  u32 mu;
+  unit_span(pg, N, u, f0, mu);
   void* out = comp ? out_b : out_a;
 #pragma unroll
   for (int e = 0; e < 16; ++e) {
     const u32 pos = (u32)pass_pos<LOGN, NP - 1>(p, e);
-    const u32 row = g * N + pos;
-    const bool add_body = comp == 1 && row < rows;
+    const bool add_body = comp == 1 && pos < mu;
     const size_t o = (size_t)u * N + pos;
     if constexpr (RNS) {
       u32 c1 = sub_if32(x[e].x, rk.p1), c2 = sub_if32(x[e].y, rk.p2);
       if (add_body) {
-        const uint2 rb = to_residues(reduce_word(body[(size_t)t * rows + row], rc), rk);
+        const uint2 rb = to_residues(reduce_word(body[f0 + pos], rc), rk);
         c1 = sub_if32(sub_if32(c1 + rb.x, 2 * rk.p1), rk.p1);
         c2 = sub_if32(sub_if32(c2 + rb.y, 2 * rk.p2), rk.p2);
       }
@@ -365,7 +395,7 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB)
       else reinterpret_cast<u64*>(out)[o] = (u64)c1 + (u64)rk.p1 * h;
     } else {
       u64 c = reduce_4q(x[e], rc.q, rc.q2);
-      if (add_body) c = reduce_2q(c + reduce_word(body[(size_t)t * rows + row], rc), rc.q);
+      if (add_body) c = reduce_2q(c + reduce_word(body[f0 + pos], rc), rc.q);
       if constexpr (MODE == kOutSwitched) reinterpret_cast<u32*>(out)[o] = modswitch_word(c, rc);
       else reinterpret_cast<u64*>(out)[o] = c;
     }
@@ -375,13 +405,13 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB)
 // q = 2^K (the key in slices): per slice sl, the segments' partial sums are
 // inverse-transformed and the CRT value (exact, below (p1 p2)/2 in magnitude)
 // is lifted centred; the slices combine as sum_sl 2^(bits sl) value mod 2^64,
-// which is exact mod 2^K.  Then b_{gN+m} joins coefficient m of B and the
+// which is exact mod 2^K.  Then b_{f0+j} joins coefficient j of B and the
 // words are switched to 2^k (or left mod 2^K).  Block b = u*2 + c as above;
 // slice sl's partial sums start at Phat + sl * slice_stride.
 template <int LOGN, int MODE>
 __global__ void __launch_bounds__(Shape<LOGN>::TPB)
     pack_finish_pow2_kernel(const u64* __restrict__ Phat, u32 nseg, u32 slices, u32 bits, size_t slice_stride,
-                            const u64* __restrict__ body, u32 rows, u32 G, u32 u_base, u32 units,
+                            const u64* __restrict__ body, PackGeom pg, u32 u_base, u32 units,
                             void* __restrict__ out_a, void* __restrict__ out_b, RnsConst rk,
                             const void* __restrict__ tw0v, const void* __restrict__ twcv) {
   using S = Shape<LOGN>;
@@ -425,15 +455,16 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB)
   }
   if (!active) return;
   const u32 u = u_base + b / 2, comp = b % 2;
-  const u32 t = u / G, g = u % G;
+  u64 f0;
+  u32 mu;
+  unit_span(pg, N, u, f0, mu);
   void* out = comp ? out_b : out_a;
   const u64 qmask = (1ull << rk.p2k) - 1;
 #pragma unroll
   for (int e = 0; e < 16; ++e) {
     const u32 pos = (u32)pass_pos<LOGN, NP - 1>(p, e);
-    const u32 row = g * N + pos;
     u64 v = acc[e];
-    if (comp == 1 && row < rows) v += body[(size_t)t * rows + row];
+    if (comp == 1 && pos < mu) v += body[f0 + pos];
     v &= qmask;
     const size_t o = (size_t)u * N + pos;
     if constexpr (MODE == kOutSwitched) reinterpret_cast<u32*>(out)[o] = pow2_modswitch(v, rk);
@@ -456,17 +487,19 @@ using phe::Span;
 constexpr int kMacUnits = 8;                        // units per pack_mac_kernel block
 constexpr int kMacStages = 4;                       // rows in flight per pack_mac_kernel thread
 constexpr size_t kMacSmem = (size_t)kMacStages * 256 * (2 * 16 + kMacUnits * 8);
-constexpr uint64_t kPackScratchBytes = 2ull << 30;  // digit rows in flight per phe_pack chunk
+constexpr uint64_t kPackScratchBytes = 4ull << 30;  // digit rows in flight per phe_pack chunk
+constexpr uint64_t kLweScratchBytes = 2ull << 30;   // switched masks in flight per phe_matmul_packed chunk
+constexpr uint32_t kPackFlags = PHE_OUT_RAW | PHE_PACK_DENSE;
 
-cudaError_t launch_decompose(const phe_ctx* c, const phe_ksk* k, const void* mask, bool switched, u32 rows, u32 G,
-                             u32 u_base, u32 cu, int32_t* D, cudaStream_t s) {
+cudaError_t launch_decompose(const phe_ctx* c, const phe_ksk* k, const void* mask, bool switched,
+                             const phe::PackGeom& pg, u32 u_base, u32 cu, int32_t* D, cudaStream_t s) {
   const u32 N = c->prm.N;
   const dim3 grid(N / 64, N / 32, cu), block(32, 8);
 #define PHE_DECOMP(E)                                                                                       \
-  (switched ? phe::pack_decompose_kernel<E, true><<<grid, block, 0, s>>>(mask, rows, N, G, u_base, k->base_log, \
-                                                                          k->rcK, k->rkK, D)                        \
-            : phe::pack_decompose_kernel<E, false><<<grid, block, 0, s>>>(mask, rows, N, G, u_base, k->base_log, \
-                                                                           k->rcK, k->rkK, D))
+  (switched ? phe::pack_decompose_kernel<E, true><<<grid, block, 0, s>>>(mask, pg, N, u_base, k->base_log, k->rcK, \
+                                                                          k->rkK, D)                                 \
+            : phe::pack_decompose_kernel<E, false><<<grid, block, 0, s>>>(mask, pg, N, u_base, k->base_log, k->rcK, \
+                                                                           k->rkK, D))
   switch (k->ell) {
     case 1: PHE_DECOMP(1); break;
     case 2: PHE_DECOMP(2); break;
@@ -477,12 +510,13 @@ cudaError_t launch_decompose(const phe_ctx* c, const phe_ksk* k, const void* mas
   return cudaGetLastError();
 }
 
-// Segments of the n*ell contraction for a chunk of `cu` units: enough blocks
-// for about four per SM, each segment at least 16 rows long.
+// Segments of the n*ell contraction for a chunk of `cu` units: as many blocks
+// as fit in four per SM (two waves of two resident blocks), each segment at
+// least 16 rows long.
 u32 mac_segments(const phe_ctx* c, const phe_ksk* k, u32 cu) {
   const u32 nr = k->n * k->ell;
   const u32 base = (c->prm.N / 256) * ((cu + kMacUnits - 1) / kMacUnits);
-  const u32 want = (4u * (u32)c->num_sms + base - 1) / base;
+  const u32 want = (4u * (u32)c->num_sms) / base;
   return std::max(1u, std::min(want, nr / 16));
 }
 
@@ -501,8 +535,8 @@ cudaError_t launch_mac(const phe_ctx* c, const phe_ksk* k, const u64* Dhat, u32 
 }
 
 template <int LOGN, bool RNS, int MODE>
-cudaError_t finish_one(const phe_ctx* c, const u64* Phat, u32 nseg, const u64* body, u32 rows, u32 G, u32 u_base,
-                       u32 cu, void* oa, void* ob, cudaStream_t s) {
+cudaError_t finish_one(const phe_ctx* c, const u64* Phat, u32 nseg, const u64* body, const phe::PackGeom& pg,
+                       u32 u_base, u32 cu, void* oa, void* ob, cudaStream_t s) {
   using S = phe::Shape<LOGN>;
   const size_t smem = phe::lwedot_smem(LOGN);
   auto kern = phe::pack_finish_kernel<LOGN, RNS, MODE>;
@@ -512,14 +546,14 @@ cudaError_t finish_one(const phe_ctx* c, const u64* Phat, u32 nseg, const u64* b
   }
   const phe::Tables& tab = RNS ? c->tab32 : c->tab;
   const u32 blocks = (2 * cu + S::SLOTS - 1) / S::SLOTS;
-  kern<<<blocks, S::TPB, smem, s>>>(Phat, nseg, body, rows, G, u_base, cu, oa, ob, c->rc, c->rk, tab.inv_0,
-                                    tab.inv_c);
+  kern<<<blocks, S::TPB, smem, s>>>(Phat, nseg, body, pg, u_base, cu, oa, ob, c->rc, c->rk, tab.inv_0, tab.inv_c);
   return cudaGetLastError();
 }
 
 template <int LOGN, int MODE>
 cudaError_t finish_pow2(const phe_ctx* c, const phe_ksk* k, const u64* Phat, u32 nseg, size_t slice_stride,
-                        const u64* body, u32 rows, u32 G, u32 u_base, u32 cu, void* oa, void* ob, cudaStream_t s) {
+                        const u64* body, const phe::PackGeom& pg, u32 u_base, u32 cu, void* oa, void* ob,
+                        cudaStream_t s) {
   using S = phe::Shape<LOGN>;
   const size_t smem = phe::lwedot_smem(LOGN);
   auto kern = phe::pack_finish_pow2_kernel<LOGN, MODE>;
@@ -528,42 +562,42 @@ cudaError_t finish_pow2(const phe_ctx* c, const phe_ksk* k, const u64* Phat, u32
     if (e != cudaSuccess) return e;
   }
   const u32 blocks = (2 * cu + S::SLOTS - 1) / S::SLOTS;
-  kern<<<blocks, S::TPB, smem, s>>>(Phat, nseg, k->slices, k->slice_bits, slice_stride, body, rows, G, u_base, cu,
-                                    oa, ob, c->rk, c->tab32.inv_0, c->tab32.inv_c);
+  kern<<<blocks, S::TPB, smem, s>>>(Phat, nseg, k->slices, k->slice_bits, slice_stride, body, pg, u_base, cu, oa, ob,
+                                    c->rk, c->tab32.inv_0, c->tab32.inv_c);
   return cudaGetLastError();
 }
 
 template <int LOGN>
-cudaError_t finish_by_form(const phe_ctx* c, int mode, const u64* Phat, u32 nseg, const u64* body, u32 rows, u32 G,
-                           u32 u_base, u32 cu, void* oa, void* ob, cudaStream_t s) {
+cudaError_t finish_by_form(const phe_ctx* c, int mode, const u64* Phat, u32 nseg, const u64* body,
+                           const phe::PackGeom& pg, u32 u_base, u32 cu, void* oa, void* ob, cudaStream_t s) {
   if (c->rns) {
-    return mode == phe::kOutRaw ? finish_one<LOGN, true, phe::kOutRaw>(c, Phat, nseg, body, rows, G, u_base, cu, oa, ob, s)
-                                : finish_one<LOGN, true, phe::kOutSwitched>(c, Phat, nseg, body, rows, G, u_base, cu, oa, ob, s);
+    return mode == phe::kOutRaw ? finish_one<LOGN, true, phe::kOutRaw>(c, Phat, nseg, body, pg, u_base, cu, oa, ob, s)
+                                : finish_one<LOGN, true, phe::kOutSwitched>(c, Phat, nseg, body, pg, u_base, cu, oa, ob, s);
   }
-  return mode == phe::kOutRaw ? finish_one<LOGN, false, phe::kOutRaw>(c, Phat, nseg, body, rows, G, u_base, cu, oa, ob, s)
-                              : finish_one<LOGN, false, phe::kOutSwitched>(c, Phat, nseg, body, rows, G, u_base, cu, oa, ob, s);
+  return mode == phe::kOutRaw ? finish_one<LOGN, false, phe::kOutRaw>(c, Phat, nseg, body, pg, u_base, cu, oa, ob, s)
+                              : finish_one<LOGN, false, phe::kOutSwitched>(c, Phat, nseg, body, pg, u_base, cu, oa, ob, s);
 }
 
-cudaError_t launch_finish(const phe_ctx* c, int mode, const u64* Phat, u32 nseg, const u64* body, u32 rows, u32 G,
-                          u32 u_base, u32 cu, void* oa, void* ob, cudaStream_t s) {
+cudaError_t launch_finish(const phe_ctx* c, int mode, const u64* Phat, u32 nseg, const u64* body,
+                          const phe::PackGeom& pg, u32 u_base, u32 cu, void* oa, void* ob, cudaStream_t s) {
   switch (c->logn) {
-    case 8: return finish_by_form<8>(c, mode, Phat, nseg, body, rows, G, u_base, cu, oa, ob, s);
-    case 9: return finish_by_form<9>(c, mode, Phat, nseg, body, rows, G, u_base, cu, oa, ob, s);
-    case 10: return finish_by_form<10>(c, mode, Phat, nseg, body, rows, G, u_base, cu, oa, ob, s);
-    case 11: return finish_by_form<11>(c, mode, Phat, nseg, body, rows, G, u_base, cu, oa, ob, s);
-    case 12: return finish_by_form<12>(c, mode, Phat, nseg, body, rows, G, u_base, cu, oa, ob, s);
-    case 13: return finish_by_form<13>(c, mode, Phat, nseg, body, rows, G, u_base, cu, oa, ob, s);
+    case 8: return finish_by_form<8>(c, mode, Phat, nseg, body, pg, u_base, cu, oa, ob, s);
+    case 9: return finish_by_form<9>(c, mode, Phat, nseg, body, pg, u_base, cu, oa, ob, s);
+    case 10: return finish_by_form<10>(c, mode, Phat, nseg, body, pg, u_base, cu, oa, ob, s);
+    case 11: return finish_by_form<11>(c, mode, Phat, nseg, body, pg, u_base, cu, oa, ob, s);
+    case 12: return finish_by_form<12>(c, mode, Phat, nseg, body, pg, u_base, cu, oa, ob, s);
+    case 13: return finish_by_form<13>(c, mode, Phat, nseg, body, pg, u_base, cu, oa, ob, s);
     default: return cudaErrorInvalidValue;
   }
 }
 
 cudaError_t launch_finish_pow2(const phe_ctx* c, const phe_ksk* k, int mode, const u64* Phat, u32 nseg,
-                               size_t slice_stride, const u64* body, u32 rows, u32 G, u32 u_base, u32 cu, void* oa,
-                               void* ob, cudaStream_t s) {
-#define PHE_FIN2(L)                                                                                         \
-  return mode == phe::kOutRaw                                                                              \
-             ? finish_pow2<L, phe::kOutRaw>(c, k, Phat, nseg, slice_stride, body, rows, G, u_base, cu, oa, ob, s) \
-             : finish_pow2<L, phe::kOutSwitched>(c, k, Phat, nseg, slice_stride, body, rows, G, u_base, cu, oa, ob, s)
+                               size_t slice_stride, const u64* body, const phe::PackGeom& pg, u32 u_base, u32 cu,
+                               void* oa, void* ob, cudaStream_t s) {
+#define PHE_FIN2(L)                                                                                     \
+  return mode == phe::kOutRaw                                                                          \
+             ? finish_pow2<L, phe::kOutRaw>(c, k, Phat, nseg, slice_stride, body, pg, u_base, cu, oa, ob, s) \
+             : finish_pow2<L, phe::kOutSwitched>(c, k, Phat, nseg, slice_stride, body, pg, u_base, cu, oa, ob, s)
   switch (c->logn) {
     case 8: PHE_FIN2(8);
     case 9: PHE_FIN2(9);
@@ -576,15 +610,29 @@ cudaError_t launch_finish_pow2(const phe_ctx* c, const phe_ksk* k, int mode, con
 #undef PHE_FIN2
 }
 
+// Tokens per unit: floor(N / rows) for dense packing of rows <= N/2, else 1.
+u32 tokens_per_unit(u32 N, u32 rows, bool dense) { return (dense && 2 * rows <= N) ? N / rows : 1u; }
+
+phe::PackGeom pack_geom(u32 N, u32 rows, u32 T, bool dense) {
+  return phe::PackGeom{rows, (rows + N - 1) / N, tokens_per_unit(N, rows, dense), (u64)T * rows};
+}
+
+// Units (output RLWEs) of T tokens, and the units before token t0 (a
+// multiple of tpu).
+u64 pack_units(const phe::PackGeom& pg, u64 T) { return pg.G > 1 ? T * pg.G : (T + pg.tpu - 1) / pg.tpu; }
+u64 units_before(const phe::PackGeom& pg, u64 t0) { return pg.G > 1 ? t0 * pg.G : t0 / pg.tpu; }
+
 // The packing of T x rows LWE ciphertexts on `s`, in chunks of units.
-cudaError_t pack_device(phe_ctx* c, const phe_ksk* k, u32 T, u32 rows, const void* mask, bool switched,
+cudaError_t pack_device(phe_ctx* c, const phe_ksk* k, u32 T, u32 rows, bool dense, const void* mask, bool switched,
                         const u64* body, void* oa, void* ob, int mode, cudaStream_t s) {
   const u32 N = c->prm.N, nr = k->n * k->ell;
-  const u32 G = (rows + N - 1) / N;
-  const u64 units = (u64)T * G;
+  const phe::PackGeom pg = pack_geom(N, rows, T, dense);
+  const u64 units = pack_units(pg, T);
   // per unit: int32 digit rows, then their transforms (8 bytes per word)
   const u64 unit_bytes = (u64)nr * N * (sizeof(int32_t) + sizeof(u64));
-  const u32 per = (u32)std::max<u64>(1, std::min<u64>(units, kPackScratchBytes / unit_bytes));
+  // whole MAC blocks per chunk: each reads the key once for kMacUnits units
+  u32 per = (u32)std::max<u64>(1, std::min<u64>(units, kPackScratchBytes / unit_bytes));
+  if (per < units && per >= (u32)kMacUnits) per -= per % kMacUnits;
   Span call(c, phe::kKPackCall, s);
   u64* Dhat = nullptr;
   u64* Phat = nullptr;
@@ -597,7 +645,7 @@ cudaError_t pack_device(phe_ctx* c, const phe_ksk* k, u32 T, u32 rows, const voi
     const u32 cu = (u32)std::min<u64>(per, units - u0);
     {
       Span sp(c, phe::kKPackDecompose, s);
-      e = launch_decompose(c, k, mask, switched, rows, G, (u32)u0, cu, D, s);
+      e = launch_decompose(c, k, mask, switched, pg, (u32)u0, cu, D, s);
     }
     if (e == cudaSuccess) {
       Span sp(c, phe::kKInputNtt, s);
@@ -612,8 +660,8 @@ cudaError_t pack_device(phe_ctx* c, const phe_ksk* k, u32 T, u32 rows, const voi
     }
     if (e == cudaSuccess) {
       Span sp(c, phe::kKPackFinish, s);
-      e = c->pow2 ? launch_finish_pow2(c, k, mode, Phat, nseg, slice_stride, body, rows, G, (u32)u0, cu, oa, ob, s)
-                  : launch_finish(c, mode, Phat, nseg, body, rows, G, (u32)u0, cu, oa, ob, s);
+      e = c->pow2 ? launch_finish_pow2(c, k, mode, Phat, nseg, slice_stride, body, pg, (u32)u0, cu, oa, ob, s)
+                  : launch_finish(c, mode, Phat, nseg, body, pg, (u32)u0, cu, oa, ob, s);
     }
   }
   cudaError_t f1 = Phat ? cudaFreeAsync(Phat, s) : cudaSuccess;
@@ -623,16 +671,28 @@ cudaError_t pack_device(phe_ctx* c, const phe_ksk* k, u32 T, u32 rows, const voi
 }
 
 // Eq. (LWEdot) with the masks switched straight to B^ell (what Decomp
-// reads) and raw bodies, then the packing, token chunk by token chunk.
+// reads) and raw bodies, then the packing, token chunk by token chunk (a
+// chunk holds whole units).
 cudaError_t matmul_packed_device(phe_ctx* c, const phe_weights::Dir& D, const phe_ksk* k, u32 T, const u64* in_mask,
-                                 const u64* in_seeds, const u64* in_body, void* oa, void* ob, int mode,
+                                 const u64* in_seeds, const u64* in_body, void* oa, void* ob, int mode, bool dense,
                                  cudaStream_t s) {
-  const u32 N = c->prm.N, G = (D.rows + N - 1) / N;
+  const u32 N = c->prm.N;
+  const phe::PackGeom pg = pack_geom(N, D.rows, T, dense);
   const size_t osz = mode == phe::kOutRaw ? sizeof(u64) : sizeof(u32);
   const u64 ahat_tok = (u64)D.L * N * sizeof(u64), atil_tok = (u64)D.rows * N * sizeof(u32);
   const u64 dig_tok = phe::digit_bytes(1, D.cols);  // the bodies' digit rows (body GEMM)
   const u64 tok_bytes = ahat_tok + atil_tok + (u64)D.rows * sizeof(u64) + dig_tok;
-  const u32 per = (u32)std::max<u64>(1, std::min<u64>(T, kPackScratchBytes / tok_bytes));
+  u32 per = (u32)std::max<u64>(1, std::min<u64>(T, kLweScratchBytes / tok_bytes));
+  if (per < T) {
+    per = std::max(pg.tpu, per / pg.tpu * pg.tpu);  // whole units per chunk
+    // and, within 8 steps, whole MAC blocks (a key read per kMacUnits units)
+    for (u32 p2 = per, n = 0; p2 >= pg.tpu && n < (u32)kMacUnits; p2 -= pg.tpu, ++n)
+      if (pack_units(pg, p2) % kMacUnits == 0) {
+        per = p2;
+        break;
+      }
+  }
+  per = std::min(per, T);
   Span call(c, phe::kKCall, s);
   char* scratch = nullptr;
   cudaError_t e = phe::ctx_malloc_async(c, &scratch, (size_t)per * tok_bytes + 256, s);
@@ -674,8 +734,9 @@ cudaError_t matmul_packed_device(phe_ctx* c, const phe_weights::Dir& D, const ph
       e = phe::launch_lwedot_packin2(c, jt, k->rcK, k->rkK, gemm, s);
     }
     if (e == cudaSuccess)
-      e = pack_device(c, k, tn, D.rows, atil, true, rawb, static_cast<char*>(oa) + (size_t)t0 * G * N * osz,
-                      static_cast<char*>(ob) + (size_t)t0 * G * N * osz, mode, s);
+      e = pack_device(c, k, tn, D.rows, dense, atil, true, rawb,
+                      static_cast<char*>(oa) + (size_t)units_before(pg, t0) * N * osz,
+                      static_cast<char*>(ob) + (size_t)units_before(pg, t0) * N * osz, mode, s);
   }
   cudaError_t f = cudaFreeAsync(scratch, s);
   return e != cudaSuccess ? e : f;
@@ -804,23 +865,33 @@ void phe_ksk_free(phe_ksk* k) {
 
 uint64_t phe_ksk_device_bytes(const phe_ksk* k) { return k ? k->bytes : 0; }
 
+phe_status phe_pack_layout(uint32_t N, uint32_t rows, uint32_t T, uint32_t flags, uint64_t* units,
+                           uint32_t* tokens_per_unit) {
+  if (N == 0 || (N & (N - 1)) || rows == 0) return fail(PHE_EINVAL, "phe_pack_layout: N=%u rows=%u", N, rows);
+  if (flags & ~kPackFlags) return fail(PHE_EINVAL, "phe_pack_layout: flags=%u", flags);
+  const phe::PackGeom pg = pack_geom(N, rows, T, flags & PHE_PACK_DENSE);
+  if (units) *units = pack_units(pg, T);
+  if (tokens_per_unit) *tokens_per_unit = pg.tpu;
+  return PHE_OK;
+}
+
 phe_status phe_pack(phe_ctx* c, const phe_ksk* k, uint32_t T, uint32_t rows, const uint64_t* d_lwe_mask,
                     const uint64_t* d_lwe_body, void* d_out_a, void* d_out_b, uint32_t flags, void* stream) {
   phe_status st = check_ksk(c, k, "phe_pack");
   if (st != PHE_OK) return st;
-  if (flags != PHE_OUT_SWITCHED && flags != PHE_OUT_RAW) return fail(PHE_EINVAL, "phe_pack: flags=%u", flags);
+  if (flags & ~kPackFlags) return fail(PHE_EINVAL, "phe_pack: flags=%u", flags);
   if (T == 0 || rows == 0) return PHE_OK;
   if (!d_lwe_mask || !d_lwe_body || !d_out_a || !d_out_b) return fail(PHE_EINVAL, "phe_pack: null buffer");
   if (reinterpret_cast<uintptr_t>(d_lwe_mask) % 16)
     return fail(PHE_EINVAL, "phe_pack: d_lwe_mask must be 16-byte aligned (the masks are read two words at a time)");
-  const u32 G = (rows + c->prm.N - 1) / c->prm.N;
-  if ((u64)T * G > (1u << 24)) return fail(PHE_EINVAL, "phe_pack: T*ceil(rows/N)=%llu exceeds 2^24",
-                                           (unsigned long long)((u64)T * G));
+  const bool dense = flags & PHE_PACK_DENSE;
+  const u64 units = pack_units(pack_geom(c->prm.N, rows, T, dense), T);
+  if (units > (1u << 24)) return fail(PHE_EINVAL, "phe_pack: %llu output RLWEs exceed 2^24", (unsigned long long)units);
   DeviceGuard g(c->device);
   if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
-  cudaError_t e = pack_device(c, k, T, rows, d_lwe_mask, false, reinterpret_cast<const u64*>(d_lwe_body), d_out_a,
-                              d_out_b,
-                              flags == PHE_OUT_RAW ? phe::kOutRaw : phe::kOutSwitched, (cudaStream_t)stream);
+  cudaError_t e = pack_device(c, k, T, rows, dense, d_lwe_mask, false, reinterpret_cast<const u64*>(d_lwe_body),
+                              d_out_a, d_out_b, (flags & PHE_OUT_RAW) ? phe::kOutRaw : phe::kOutSwitched,
+                              (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "phe_pack");
   return PHE_OK;
 }
@@ -833,15 +904,15 @@ phe_status phe_matmul_packed(phe_ctx* c, const phe_weights* w, const phe_ksk* k,
   uint32_t rows = 0, cols = 0, L = 0;
   if (!w || w->ctx != c) return fail(PHE_EINVAL, "phe_matmul_packed: weights missing or of another context");
   if ((st = phe_weights_shape(w, dir, &rows, &cols, &L)) != PHE_OK) return st;
-  if (flags != PHE_OUT_SWITCHED && flags != PHE_OUT_RAW)
-    return fail(PHE_EINVAL, "phe_matmul_packed: flags=%u", flags);
+  if (flags & ~kPackFlags) return fail(PHE_EINVAL, "phe_matmul_packed: flags=%u", flags);
   if (T == 0) return PHE_OK;
   if (!d_in_mask || !d_in_body || !d_out_a || !d_out_b) return fail(PHE_EINVAL, "phe_matmul_packed: null buffer");
   DeviceGuard g(c->device);
   if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
   cudaError_t e = matmul_packed_device(c, w->dir[dir], k, T, reinterpret_cast<const u64*>(d_in_mask), nullptr,
                                        reinterpret_cast<const u64*>(d_in_body), d_out_a, d_out_b,
-                                       flags == PHE_OUT_RAW ? phe::kOutRaw : phe::kOutSwitched, (cudaStream_t)stream);
+                                       (flags & PHE_OUT_RAW) ? phe::kOutRaw : phe::kOutSwitched,
+                                       flags & PHE_PACK_DENSE, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "phe_matmul_packed");
   return PHE_OK;
 }
@@ -854,8 +925,7 @@ phe_status phe_matmul_packed_seeded(phe_ctx* c, const phe_weights* w, const phe_
   uint32_t rows = 0, cols = 0, L = 0;
   if (!w || w->ctx != c) return fail(PHE_EINVAL, "phe_matmul_packed_seeded: weights missing or of another context");
   if ((st = phe_weights_shape(w, dir, &rows, &cols, &L)) != PHE_OK) return st;
-  if (flags != PHE_OUT_SWITCHED && flags != PHE_OUT_RAW)
-    return fail(PHE_EINVAL, "phe_matmul_packed_seeded: flags=%u", flags);
+  if (flags & ~kPackFlags) return fail(PHE_EINVAL, "phe_matmul_packed_seeded: flags=%u", flags);
   if (T == 0) return PHE_OK;
   if (!d_in_seeds || !d_in_body || !d_out_a || !d_out_b)
     return fail(PHE_EINVAL, "phe_matmul_packed_seeded: null buffer");
@@ -863,7 +933,8 @@ phe_status phe_matmul_packed_seeded(phe_ctx* c, const phe_weights* w, const phe_
   if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
   cudaError_t e = matmul_packed_device(c, w->dir[dir], k, T, nullptr, reinterpret_cast<const u64*>(d_in_seeds),
                                        reinterpret_cast<const u64*>(d_in_body), d_out_a, d_out_b,
-                                       flags == PHE_OUT_RAW ? phe::kOutRaw : phe::kOutSwitched, (cudaStream_t)stream);
+                                       (flags & PHE_OUT_RAW) ? phe::kOutRaw : phe::kOutSwitched,
+                                       flags & PHE_PACK_DENSE, (cudaStream_t)stream);
   if (e != cudaSuccess) return cuda_fail(e, "phe_matmul_packed_seeded");
   return PHE_OK;
 }
@@ -876,16 +947,17 @@ phe_status phe_matmul_packed_host(phe_ctx* c, const phe_weights* w, const phe_ks
   uint32_t rows = 0, cols = 0, L = 0;
   if (!w || w->ctx != c) return fail(PHE_EINVAL, "phe_matmul_packed_host: weights missing or of another context");
   if ((st = phe_weights_shape(w, dir, &rows, &cols, &L)) != PHE_OK) return st;
-  if (flags != PHE_OUT_SWITCHED && flags != PHE_OUT_RAW)
-    return fail(PHE_EINVAL, "phe_matmul_packed_host: flags=%u", flags);
+  if (flags & ~kPackFlags) return fail(PHE_EINVAL, "phe_matmul_packed_host: flags=%u", flags);
   if (T == 0) return PHE_OK;
   if (!h_in_mask || !h_in_body || !h_out_a || !h_out_b) return fail(PHE_EINVAL, "phe_matmul_packed_host: null buffer");
   DeviceGuard g(c->device);
   if (g.err != cudaSuccess) return cuda_fail(g.err, "cudaSetDevice");
-  const u32 N = c->prm.N, G = (rows + N - 1) / N;
-  const size_t osz = flags == PHE_OUT_RAW ? sizeof(u64) : sizeof(u32);
-  const size_t in_tok = (size_t)L * N * sizeof(u64), out_tok = (size_t)G * N * osz;
-  const u32 tc = std::max(1u, std::min(tok_chunk ? tok_chunk : 8u, T));
+  const u32 N = c->prm.N;
+  const phe::PackGeom pg = pack_geom(N, rows, T, flags & PHE_PACK_DENSE);
+  const size_t osz = (flags & PHE_OUT_RAW) ? sizeof(u64) : sizeof(u32);
+  const size_t in_tok = (size_t)L * N * sizeof(u64), out_unit = (size_t)N * osz;
+  u32 tc = std::max(1u, std::min(tok_chunk ? tok_chunk : 8u, T));
+  if (tc < T) tc = std::min(T, std::max(pg.tpu, tc / pg.tpu * pg.tpu));  // whole units per chunk
   cudaStream_t caller = (cudaStream_t)stream;
   cudaError_t e = cudaSuccess;
   for (int i = 0; i < 2 && e == cudaSuccess; ++i)
@@ -903,8 +975,8 @@ phe_status phe_matmul_packed_host(phe_ctx* c, const phe_weights* w, const phe_ks
     cudaStream_t s = c->side[i];
     if ((e = phe::ctx_malloc_async(c, &buf[i].a, tc * in_tok, s)) != cudaSuccess) break;
     if ((e = phe::ctx_malloc_async(c, &buf[i].b, tc * in_tok, s)) != cudaSuccess) break;
-    if ((e = phe::ctx_malloc_async(c, &buf[i].oa, tc * out_tok, s)) != cudaSuccess) break;
-    e = phe::ctx_malloc_async(c, &buf[i].ob, tc * out_tok, s);
+    if ((e = phe::ctx_malloc_async(c, &buf[i].oa, pack_units(pg, tc) * out_unit, s)) != cudaSuccess) break;
+    e = phe::ctx_malloc_async(c, &buf[i].ob, pack_units(pg, tc) * out_unit, s);
   }
   for (u32 n = 0; n < nchunks && e == cudaSuccess && st == PHE_OK; ++n) {
     const u32 t0 = n * tc, tn = std::min(tc, T - t0);
@@ -917,9 +989,10 @@ phe_status phe_matmul_packed_host(phe_ctx* c, const phe_weights* w, const phe_ks
     st = phe_matmul_packed(c, w, k, dir, tn, reinterpret_cast<const uint64_t*>(B.a),
                            reinterpret_cast<const uint64_t*>(B.b), B.oa, B.ob, flags, s);
     if (st != PHE_OK) break;
-    if ((e = cudaMemcpyAsync(static_cast<char*>(h_out_a) + t0 * out_tok, B.oa, tn * out_tok, cudaMemcpyDeviceToHost,
-                             s)) != cudaSuccess) break;
-    e = cudaMemcpyAsync(static_cast<char*>(h_out_b) + t0 * out_tok, B.ob, tn * out_tok, cudaMemcpyDeviceToHost, s);
+    const size_t o0 = units_before(pg, t0) * out_unit, on = pack_units(pg, tn) * out_unit;
+    if ((e = cudaMemcpyAsync(static_cast<char*>(h_out_a) + o0, B.oa, on, cudaMemcpyDeviceToHost, s)) != cudaSuccess)
+      break;
+    e = cudaMemcpyAsync(static_cast<char*>(h_out_b) + o0, B.ob, on, cudaMemcpyDeviceToHost, s);
   }
   for (int i = 0; i < 2; ++i) {
     cudaStream_t s = c->side[i];

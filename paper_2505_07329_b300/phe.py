@@ -21,6 +21,7 @@ PHE_OK, PHE_EINVAL, PHE_ENOMEM, PHE_EBUSY, PHE_ETIMEOUT, PHE_ECUDA, PHE_EUNSUPPO
 PHE_FWD, PHE_BWD = 0, 1
 PHE_DIR_FWD_BIT, PHE_DIR_BWD_BIT = 1, 2
 PHE_OUT_SWITCHED, PHE_OUT_RAW = 0, 1
+PHE_PACK_DENSE = 2   # packing calls: several tokens per output RLWE
 
 
 class PheError(RuntimeError):
@@ -127,6 +128,7 @@ SIGNATURES = {
     "phe_matmul_packed_seeded": (_i32, [_vp, _vp, _vp, _i32, _u32, _vp, _vp, _vp, _vp, _u32, _vp]),
     "phe_matmul_packed_host": (_i32, [_vp, _vp, _vp, _i32, _u32, _vp, _vp, _vp, _vp, _u32, _u32, _vp]),
     "phe_wire_sizes": (_i32, [_vp, ctypes.POINTER(_u64), ctypes.POINTER(_u64), ctypes.POINTER(_u64)]),
+    "phe_pack_layout": (_i32, [_u32, _u32, _u32, _u32, ctypes.POINTER(_u64), ctypes.POINTER(_u32)]),
     "phe_wire_pack": (_i32, [_vp, _vp, _u32, _vp, _u32, _u64, _vp, _vp]),
     "phe_wire_unpack_inputs": (_i32, [_vp, _vp, _u64, _vp, _vp, _vp]),
     "phe_matmul_wire": (_i32, [_vp, _vp, _vp, _i32, _u32, _vp, _vp, _vp]),
@@ -487,6 +489,13 @@ def phe_matmul_packed_host(ctx, w, k, direction: int, T: int, h_in_mask, h_in_bo
                            flags: int = PHE_OUT_SWITCHED, tok_chunk: int = 8, stream=None) -> None:
     _check(lib().phe_matmul_packed_host(ctx, w, k, direction, T, _hptr(h_in_mask), _hptr(h_in_body),
                                         _hptr(h_out_a), _hptr(h_out_b), flags, tok_chunk, _stream(stream)))
+
+
+def phe_pack_layout(N: int, rows: int, T: int, flags: int = PHE_OUT_SWITCHED) -> tuple:
+    """(output RLWEs, tokens per RLWE) of a packing call."""
+    u, t = _u64(), _u32()
+    _check(lib().phe_pack_layout(N, rows, T, flags, ctypes.byref(u), ctypes.byref(t)))
+    return u.value, t.value
 
 
 def phe_wire_sizes(ctx) -> dict:

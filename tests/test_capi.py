@@ -138,3 +138,25 @@ def test_power_of_two_modulus_is_validated(L, N, q, k, rns, flags, msg):
         phe.phe_ctx_create(N, q, k, 0, rns=rns, flags=flags)
     assert ei.value.status == phe.PHE_EINVAL
     assert msg in str(ei.value)
+
+
+@pytest.mark.parametrize("N,rows,T,flags,want", [
+    (4096, 2048, 16, 0, (16, 1)),                   # one token per RLWE (Eq. (pack_rotate) per token)
+    (4096, 8192, 3, 0, (6, 1)),                     # two RLWEs per token
+    (4096, 2048, 16, phe.PHE_PACK_DENSE, (8, 2)),   # dense: 2 tokens fill the ring
+    (4096, 512, 17, phe.PHE_PACK_DENSE, (3, 8)),    # 8 per RLWE, the last holds 1
+    (4096, 700, 12, phe.PHE_PACK_DENSE, (3, 5)),    # 5 x 700 = 3500 of 4096 coefficients
+    (4096, 2049, 5, phe.PHE_PACK_DENSE, (5, 1)),    # above N/2: unchanged
+    (4096, 8192, 3, phe.PHE_PACK_DENSE | phe.PHE_OUT_RAW, (6, 1)),
+    (256, 1, 300, phe.PHE_PACK_DENSE, (2, 256)),
+    (4096, 512, 0, phe.PHE_PACK_DENSE, (0, 8)),
+])
+def test_pack_layout(L, N, rows, T, flags, want):
+    assert phe.phe_pack_layout(N, rows, T, flags) == want
+
+
+@pytest.mark.parametrize("N,rows,flags", [(4096, 0, 0), (3000, 10, 0), (4096, 10, 4), (0, 10, 0)])
+def test_pack_layout_rejects_bad_arguments(L, N, rows, flags):
+    with pytest.raises(phe.PheError) as ei:
+        phe.phe_pack_layout(N, rows, 4, flags)
+    assert ei.value.status == phe.PHE_EINVAL

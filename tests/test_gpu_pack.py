@@ -205,10 +205,11 @@ def test_matmul_packed_end_to_end(orc, ctxs, modulus, direction):
 
 
 def test_matmul_packed_token_chunks_agree(ctxs):
-    # 8192 raw rows x (N + 1) words x 8 B = 268 MB per token: the 2 GiB
-    # scratch holds 8 tokens, so 11 tokens run as two chunks.
+    # 8192 switched mask rows x N words x 4 B = 134 MB per token: the 2 GiB
+    # scratch holds 15 tokens, cut to 12 (24 RLWEs, whole blocks of the
+    # key contraction), so 19 tokens run as two chunks.
     import torch
-    N, T = 4096, 11
+    N, T = 4096, 19
     ctx = ctxs(N, "rns")
     q = synth.Q_RNS
     W = synth.weights(8192, 2048, seed=31)
@@ -353,3 +354,167 @@ def test_pack_rejects_unaligned_masks(ctxs):
         assert ei.value.status == phe.PHE_EINVAL and "aligned" in str(ei.value)
     finally:
         phe.phe_ksk_free(k)
+
+
+def _gpu_pack_dense(ctx, k, masks, bodies, N, flags):
+    """phe_pack with PHE_PACK_DENSE: outputs [units][N]."""
+    import torch
+    T, rows = bodies.shape
+    units, tpu = phe.phe_pack_layout(N, rows, T, flags | phe.PHE_PACK_DENSE)
+    odt = torch.int64 if flags == phe.PHE_OUT_RAW else torch.int32
+    oa = torch.empty((units, N), dtype=odt, device="cuda")
+    ob = torch.empty((units, N), dtype=odt, device="cuda")
+    phe.phe_pack(ctx, k, T, rows, to_dev_u64(masks), to_dev_u64(bodies), oa, ob, flags | phe.PHE_PACK_DENSE)
+    torch.cuda.synchronize()
+    if flags == phe.PHE_OUT_RAW:
+        return tpu, oa.cpu().numpy().view(np.uint64), ob.cpu().numpy().view(np.uint64)
+    return (tpu, oa.cpu().numpy().view(np.uint32).astype(np.uint64),
+            ob.cpu().numpy().view(np.uint32).astype(np.uint64))
+
+
+@pytest.mark.parametrize("modulus,base_log,ell", [("rns", 26, 1), ("prime", 13, 2), ("pow2", 26, 1)])
+@pytest.mark.parametrize("rows,T", [(60, 7), (128, 3), (1, 300)])
+def test_dense_pack_matches_oracle(orc, ctxs, modulus, base_log, ell, rows, T):
+    """Dense packing: the LWE outputs of floor(N/rows) consecutive tokens form
+    one list of Eq. (pack_rotate), token t's row r at coefficient
+    (t mod tpu)*rows + r; the last RLWE holds the remaining tokens and zeros.
+    rows = 60 at N = 256: 4 tokens (240 coefficients) per RLWE, 7 tokens ->
+    2 RLWEs; rows = N/2: 2 per RLWE; rows = 1: 256 per RLWE, 300 tokens ->
+    2 RLWEs, the second with 44 coefficients."""
+    N = 256
+    q = MODULI[modulus][0]
+    ctx = ctxs(N, modulus)
+    g = _rng(200 + rows + ell)
+    KA = g.integers(0, q, (N, ell, N), dtype=np.uint64)
+    KB = g.integers(0, q, (N, ell, N), dtype=np.uint64)
+    masks = g.integers(0, q, (T, rows, N), dtype=np.uint64)
+    bodies = g.integers(0, q, (T, rows), dtype=np.uint64)
+    k = phe.phe_ksk_upload(ctx, KA, KB, base_log, ell)
+    try:
+        tpu, raw_a, raw_b = _gpu_pack_dense(ctx, k, masks, bodies, N, phe.PHE_OUT_RAW)
+        _, sw_a, sw_b = _gpu_pack_dense(ctx, k, masks, bodies, N, phe.PHE_OUT_SWITCHED)
+    finally:
+        phe.phe_ksk_free(k)
+    assert tpu == N // rows
+    units = -(-T // tpu)
+    assert raw_a.shape == (units, N)
+    flat_a = masks.reshape(T * rows, N)
+    flat_b = bodies.reshape(T * rows)
+    for u in range(units):
+        f0, f1 = u * tpu * rows, min((u + 1) * tpu * rows, T * rows)
+        ea, eb = orc.pack_coeffs(flat_a[f0:f1], flat_b[f0:f1], KA, KB, q, base_log, ell, np.arange(N))
+        assert np.array_equal(raw_a[u], ea) and np.array_equal(raw_b[u], eb), u
+        assert np.array_equal(sw_a[u], orc.modswitch(ea, q, 32)), u
+        assert np.array_equal(sw_b[u], orc.modswitch(eb, q, 32)), u
+
+
+def test_dense_flag_changes_nothing_above_half_ring(ctxs):
+    # rows > N/2 (here 129 and 300 at N = 256): one token per RLWE either way
+    import torch
+    N, T = 256, 3
+    ctx = ctxs(N, "rns")
+    q = synth.Q_RNS
+    g = _rng(211)
+    KA = g.integers(0, q, (N, 1, N), dtype=np.uint64)
+    KB = g.integers(0, q, (N, 1, N), dtype=np.uint64)
+    k = phe.phe_ksk_upload(ctx, KA, KB, 26, 1)
+    try:
+        for rows in (129, 300):
+            masks = g.integers(0, q, (T, rows, N), dtype=np.uint64)
+            bodies = g.integers(0, q, (T, rows), dtype=np.uint64)
+            assert phe.phe_pack_layout(N, rows, T, phe.PHE_PACK_DENSE) == (T * -(-rows // N), 1)
+            ref = _gpu_pack(ctx, k, masks, bodies, N, phe.PHE_OUT_SWITCHED)
+            _, da, db = _gpu_pack_dense(ctx, k, masks, bodies, N, phe.PHE_OUT_SWITCHED)
+            assert np.array_equal(da, ref[0].reshape(-1, N)) and np.array_equal(db, ref[1].reshape(-1, N))
+    finally:
+        phe.phe_ksk_free(k)
+
+
+@pytest.mark.parametrize("modulus", ["rns", "prime"])
+def test_matmul_packed_dense_end_to_end(orc, ctxs, modulus):
+    """Eq. (LWEdot) then dense packing on real encryptions: 100 output rows at
+    N = 256 put 2 tokens in each RLWE (5 tokens -> 3 RLWEs); word for word
+    against the oracle composition, and every coefficient decrypts to its
+    token's (W x)_r mod t (zeros past the last token)."""
+    import torch
+    N, T, t = 256, 5, synth.T_PLAIN
+    q = MODULI[modulus][0]
+    ctx = ctxs(N, modulus)
+    W = synth.weights(100, 290, seed=221)
+    rows, cols = W.shape
+    S, A, B, X = _encrypted_inputs(orc, N, T, cols, q, 222)
+    g = _rng(223)
+    KA = g.integers(0, q, (N, 1, N), dtype=np.uint64)
+    E = np.rint(g.normal(0, synth.SIGMA, (N, 1, N))).astype(np.int64)
+    KB = orc.ksk_encrypt(KA, E, S, S, q, 26, 1)
+    w = phe.phe_weights_upload(ctx, W, phe.PHE_DIR_FWD_BIT)
+    k = phe.phe_ksk_upload(ctx, KA, KB, 26, 1)
+    units, tpu = phe.phe_pack_layout(N, rows, T, phe.PHE_PACK_DENSE)
+    assert (units, tpu) == (3, 2)
+    try:
+        oa = torch.empty((units, N), dtype=torch.int32, device="cuda")
+        ob = torch.empty((units, N), dtype=torch.int32, device="cuda")
+        phe.phe_matmul_packed(ctx, w, k, phe.PHE_FWD, T, to_dev_u64(A), to_dev_u64(B), oa, ob,
+                              phe.PHE_PACK_DENSE)
+        torch.cuda.synchronize()
+    finally:
+        phe.phe_ksk_free(k)
+        phe.phe_weights_free(w)
+    ga = oa.cpu().numpy().view(np.uint32).astype(np.uint64)
+    gb = ob.cpu().numpy().view(np.uint32).astype(np.uint64)
+    la, lb = orc.lwedot_all(W, A, B, q)
+    fa, fb = la.reshape(T * rows, N), lb.reshape(T * rows)
+    y = (X.astype(np.int64) @ W.astype(np.int64).T).reshape(T * rows)
+    Sq = np.array([s % (1 << 32) for s in S.tolist()], dtype=np.uint64)
+    for u in range(units):
+        f0, f1 = u * tpu * rows, min((u + 1) * tpu * rows, T * rows)
+        ea, eb = orc.pack_coeffs(fa[f0:f1], fb[f0:f1], KA, KB, q, 26, 1, np.arange(N))
+        assert np.array_equal(ga[u], orc.modswitch(ea, q, 32)), u
+        assert np.array_equal(gb[u], orc.modswitch(eb, q, 32)), u
+        AS = orc.negacyclic_mul(ga[u], Sq, 1 << 32)
+        got = [orc.decode((int(bv) - int(av)) % (1 << 32), 1 << 32, t) for bv, av in zip(gb[u], AS)]
+        want = [((int(v) + t // 2) % t) - t // 2 for v in y[f0:f1]] + [0] * (N - (f1 - f0))
+        assert got == want, u
+
+
+def test_matmul_packed_dense_chunks_and_host_buffers_agree(ctxs):
+    """2048 rows at N = 4096: 2 tokens per RLWE.  67 tokens need two token
+    chunks of the 2 GiB scratch (about 33.6 MB a token; the first cut to 48
+    tokens: whole RLWEs, whole blocks of the key contraction); the result equals
+    phe_matmul (raw) then phe_pack, both dense, and the host-buffer call with
+    3-token chunks (rounded to 2)."""
+    import torch
+    N, T, rows = 4096, 67, 2048
+    ctx = ctxs(N, "rns")
+    q = synth.Q_RNS
+    W = synth.weights(rows, 2048, seed=231)
+    g = _rng(232)
+    KA = g.integers(0, q, (N, 1, N), dtype=np.uint64)
+    KB = g.integers(0, q, (N, 1, N), dtype=np.uint64)
+    A = torch.tensor(g.integers(0, q, (T, 1, N), dtype=np.uint64).view(np.int64), device="cuda")
+    B = torch.tensor(g.integers(0, q, (T, 1, N), dtype=np.uint64).view(np.int64), device="cuda")
+    w = phe.phe_weights_upload(ctx, W, phe.PHE_DIR_FWD_BIT)
+    k = phe.phe_ksk_upload(ctx, KA, KB, 26, 1)
+    units, tpu = phe.phe_pack_layout(N, rows, T, phe.PHE_PACK_DENSE)
+    assert (units, tpu) == (34, 2)
+    try:
+        oa = torch.empty((units, N), dtype=torch.int32, device="cuda")
+        ob = torch.empty_like(oa)
+        phe.phe_matmul_packed(ctx, w, k, phe.PHE_FWD, T, A, B, oa, ob, phe.PHE_PACK_DENSE)
+        raw_m = torch.empty((T, rows, N), dtype=torch.int64, device="cuda")
+        raw_b = torch.empty((T, rows), dtype=torch.int64, device="cuda")
+        phe.phe_matmul(ctx, w, phe.PHE_FWD, T, A, B, raw_m, raw_b, phe.PHE_OUT_RAW)
+        ra = torch.empty_like(oa)
+        rb = torch.empty_like(oa)
+        phe.phe_pack(ctx, k, T, rows, raw_m, raw_b, ra, rb, phe.PHE_PACK_DENSE)
+        torch.cuda.synchronize()
+        del raw_m, raw_b
+        ha = torch.empty((units, N), dtype=torch.int32).pin_memory()
+        hb = torch.empty_like(ha).pin_memory()
+        phe.phe_matmul_packed_host(ctx, w, k, phe.PHE_FWD, T, A.cpu().pin_memory(), B.cpu().pin_memory(), ha, hb,
+                                   phe.PHE_PACK_DENSE, tok_chunk=3)
+    finally:
+        phe.phe_ksk_free(k)
+        phe.phe_weights_free(w)
+    assert torch.equal(oa, ra) and torch.equal(ob, rb)
+    assert torch.equal(ha, oa.cpu()) and torch.equal(hb, ob.cpu())
