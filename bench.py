@@ -45,8 +45,8 @@ METRIC = "encrypted W·[x] tokens/s per Llama-1B layer; p50/p99 latency; % of ro
 # whatever its tokens (the encoded weights), b what each token adds (its
 # transformed masks and its outputs).  Valid only for the kernel sources the
 # counters were taken on (kernel_source_hash) and those tunings.
-TRAFFIC_KERNEL_HASH = "448bd42d009c5ec2"
-TRAFFIC_FITS = {(16, 0): (3274.74e6, 736.938e6), (16, 3): (3262.17e6, 741.483e6)}
+TRAFFIC_KERNEL_HASH = "209d6dd5f79cba69"
+TRAFFIC_FITS = {(16, 0): (3281.46e6, 753.454e6), (16, 3): (3281.26e6, 749.330e6)}
 
 
 def lwedot_alg_bytes(wl, T: int) -> float:

@@ -443,7 +443,8 @@ typedef struct phe_ksk phe_ksk;
  *   h_ka, h_kb  host [n][ell][N] uint64: KSK_{i,l} = (h_ka[i][l], h_kb[i][l]),
  *               words mod q (larger words are reduced); caller keeps them.
  *   n           LWE dimension; must equal N.
- *   base_log, ell  1 <= ell <= 4, 1 <= base_log <= 30, base_log*ell <= 32.
+ *   base_log, ell  1 <= ell <= 4, 1 <= base_log <= 30, base_log*ell <= 32;
+ *               with an RNS modulus also 2^(base_log-1) < min(p1, p2).
  * With q = 2^K (computed through p1 p2) the contraction has no NTT mod q, so
  * it runs exactly over the integers through p1 p2.  The centred key is split
  * into S balanced slices of b bits, KSK = sum_s 2^(b s) KSK_s, with b the

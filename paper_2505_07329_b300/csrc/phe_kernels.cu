@@ -84,12 +84,14 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB)
   }
   W x[16];
   if (job.digits) {
-    // small signed integers (|d| < 2^31): d, or the modulus plus d
+    // small signed integers: in the RNS form (gadget digits, |d| <= 2^29 <
+    // p_i) each residue is p_i + d, in (0, 2 p_i) as the first butterflies
+    // take it; in the 64-bit form (|d| < 2^31) d or q + d
     const int32_t* src = job.digits + (size_t)(active ? b : 0) * S::N;
 #pragma unroll
     for (int e = 0; e < 16; ++e) {
       const int d = active ? src[pass_pos<LOGN, NP - 1>(p, e)] : 0;
-      if constexpr (RNS) x[e] = make_uint2(d < 0 ? rk.p1 + d : (u32)d, d < 0 ? rk.p2 + d : (u32)d);
+      if constexpr (RNS) x[e] = make_uint2(rk.p1 + d, rk.p2 + d);
       else x[e] = d < 0 ? rc.q - (u64)(-(long long)d) : (u64)d;
     }
   } else {
@@ -383,21 +385,36 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, lwedot_min_blocks<Shape<LOGN
       }
       if (active) {
         const u64* at = J.ahat + (size_t)t * J.L * N;
-        for (u32 i = 0; i < J.L; ++i) {
-          const Tw* wp = wrow + (size_t)i * N;
-          if constexpr (RNS) {
+        if constexpr (RNS) {
+          // Block i's products; the first block's (each in [0, 2p)) are the
+          // accumulator as they stand, later ones are added and reduced.
+          auto block = [&](u32 i, auto first) {
+            const Tw* wp = wrow + (size_t)i * N;
             const uint4* ap = reinterpret_cast<const uint4*>(at + (size_t)i * N);
 #pragma unroll
             for (int r = 0; r < 16; r += 2) {
               const uint4 av = __ldg(&ap[(r >> 1) * P + p]);  // (a1_r, a2_r, a1_r+1, a2_r+1)
               const uint4 w0 = __ldg(&wp[what_idx<LOGN>(p, r)]);
               const uint4 w1 = __ldg(&wp[what_idx<LOGN>(p, r + 1)]);
-              x[r].x = sub_if32(x[r].x + mul_shoup32(av.x, w0.x, w0.y, rk.p1), 2 * rk.p1);
-              x[r].y = sub_if32(x[r].y + mul_shoup32(av.y, w0.z, w0.w, rk.p2), 2 * rk.p2);
-              x[r + 1].x = sub_if32(x[r + 1].x + mul_shoup32(av.z, w1.x, w1.y, rk.p1), 2 * rk.p1);
-              x[r + 1].y = sub_if32(x[r + 1].y + mul_shoup32(av.w, w1.z, w1.w, rk.p2), 2 * rk.p2);
+              const u32 m0 = mul_shoup32(av.x, w0.x, w0.y, rk.p1), m1 = mul_shoup32(av.y, w0.z, w0.w, rk.p2);
+              const u32 m2 = mul_shoup32(av.z, w1.x, w1.y, rk.p1), m3 = mul_shoup32(av.w, w1.z, w1.w, rk.p2);
+              if constexpr (decltype(first)::value) {
+                x[r] = make_uint2(m0, m1);
+                x[r + 1] = make_uint2(m2, m3);
+              } else {
+                x[r].x = sub_if32(x[r].x + m0, 2 * rk.p1);
+                x[r].y = sub_if32(x[r].y + m1, 2 * rk.p2);
+                x[r + 1].x = sub_if32(x[r + 1].x + m2, 2 * rk.p1);
+                x[r + 1].y = sub_if32(x[r + 1].y + m3, 2 * rk.p2);
+              }
             }
-          } else {
+          };
+          block(0u, std::true_type{});
+          for (u32 i = 1; i < J.L; ++i) block(i, std::false_type{});
+        }
+        for (u32 i = 0; i < (RNS ? 0u : J.L); ++i) {
+          const Tw* wp = wrow + (size_t)i * N;
+          if constexpr (!RNS) {
             const ulonglong2* ap = reinterpret_cast<const ulonglong2*>(at + (size_t)i * N);
 #pragma unroll
             for (int r = 0; r < 16; r += 2) {

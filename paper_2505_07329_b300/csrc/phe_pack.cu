@@ -761,6 +761,10 @@ phe_status phe_ksk_upload(phe_ctx* c, const uint64_t* h_ka, const uint64_t* h_kb
   if (ell < 1 || ell > 4 || base_log < 1 || base_log > 30 || base_log * ell > 32)
     return fail(PHE_EINVAL, "phe_ksk_upload: base_log=%u ell=%u (need 1<=ell<=4, 1<=base_log<=30, product<=32)",
                 base_log, ell);
+  // the digit transform takes each residue of a digit d as p_i + d: |d| <= B/2 < p_i
+  if (c->rns && (1ull << (base_log - 1)) >= std::min(c->rk.p1, c->rk.p2))
+    return fail(PHE_EINVAL, "phe_ksk_upload: base_log=%u: digits of magnitude 2^%u reach the RNS prime %u", base_log,
+                base_log - 1, std::min(c->rk.p1, c->rk.p2));
   const size_t nr = (size_t)n * ell, words = nr * 2 * N;
   // q = 2^K: slices of b bits with n ell N (B/2) 2^(b-1) below (p1 p2)/2
   u32 slices = 1, bits = 0;

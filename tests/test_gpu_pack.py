@@ -518,3 +518,31 @@ def test_matmul_packed_dense_chunks_and_host_buffers_agree(ctxs):
         phe.phe_weights_free(w)
     assert torch.equal(oa, ra) and torch.equal(ob, rb)
     assert torch.equal(ha, oa.cpu()) and torch.equal(hb, ob.cpu())
+
+
+def test_dense_pack_full_size_sampled(orc, ctxs):
+    """Dense packing at N = 4096: 512 rows put 8 tokens in each RLWE, so 9
+    tokens make 2 RLWEs, the second holding one token and zeros.  Sampled
+    coefficients on both sides of each token boundary, against the oracle's
+    coefficient-by-coefficient evaluation of the concatenated LWE list."""
+    N, T, rows = 4096, 9, 512
+    q = synth.Q_RNS
+    ctx = ctxs(N, "rns")
+    g = _rng(241)
+    KA = g.integers(0, q, (N, 1, N), dtype=np.uint64)
+    KB = g.integers(0, q, (N, 1, N), dtype=np.uint64)
+    masks = g.integers(0, q, (T, rows, N), dtype=np.uint64)
+    bodies = g.integers(0, q, (T, rows), dtype=np.uint64)
+    k = phe.phe_ksk_upload(ctx, KA, KB, 26, 1)
+    try:
+        tpu, ga, gb = _gpu_pack_dense(ctx, k, masks, bodies, N, phe.PHE_OUT_SWITCHED)
+    finally:
+        phe.phe_ksk_free(k)
+    assert tpu == 8 and ga.shape == (2, N)
+    flat_a, flat_b = masks.reshape(T * rows, N), bodies.reshape(T * rows)
+    for u, rs in ((0, [0, 1, 511, 512, 1023, 1024, 3583, 3584, 4095]), (1, [0, 255, 511, 512, 2048, 4095])):
+        f0, f1 = u * tpu * rows, min((u + 1) * tpu * rows, T * rows)
+        rs = np.array(rs)
+        ea, eb = orc.pack_coeffs(flat_a[f0:f1], flat_b[f0:f1], KA, KB, q, 26, 1, rs)
+        assert np.array_equal(ga[u, rs], orc.modswitch(ea, q, 32)), u
+        assert np.array_equal(gb[u, rs], orc.modswitch(eb, q, 32)), u
