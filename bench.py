@@ -40,13 +40,15 @@ METRIC = "encrypted W·[x] tokens/s per Llama-1B layer; p50/p99 latency; % of ro
 # DRAM bytes (read + write) of one lwedot_kernel launch of the batched form
 # (all 14 products of the layer workload, RNS modulus) as a function of the
 # launch's tokens T: a + b T, from ncu captures of the same launch at T = 2
-# and T = 4 (dram__bytes_read.sum + dram__bytes_write.sum), one fit per
-# tuning (tokens per tile, blocks per SM).  a is what a launch reads once
-# whatever its tokens (the encoded weights), b what each token adds (its
-# transformed masks and its outputs).  Valid only for the kernel sources the
-# counters were taken on (kernel_source_hash) and those tunings.
+# and T = 4 (dram__bytes_read.sum + dram__bytes_write.sum), one fit per grid
+# policy (blocks per SM: 0 = one CTA per tile, 3 = the persistent grid).  a is
+# what a launch reads once whatever its tokens (the encoded weights), b what
+# each token adds (its transformed masks and its outputs).  In the captured
+# launches every tile holds all of a row's T <= 4 tokens, which is the launch
+# of any tokens-per-tile of at least 4, so a fit serves all of those.  Valid
+# only for the kernel sources the counters were taken on (kernel_source_hash).
 TRAFFIC_KERNEL_HASH = "209d6dd5f79cba69"
-TRAFFIC_FITS = {(16, 0): (3281.46e6, 753.454e6), (16, 3): (3281.26e6, 749.330e6)}
+TRAFFIC_FITS = {0: (3281.46e6, 753.454e6), 3: (3281.26e6, 749.330e6)}
 
 
 def lwedot_alg_bytes(wl, T: int) -> float:
@@ -686,7 +688,7 @@ def main():
     achieved = modmuls / (kernel_ms / 1e3) / 1e9 if kernel_ms else None
     peak = alu["gmodmul"]
     unit_bound = unit_bound_gmodmul(clk.get("sm_max_mhz") or 2032.0) if args.modulus == "rns" else None
-    fit = TRAFFIC_FITS.get(tuple(tuning)) if tuning is not None else None
+    fit = TRAFFIC_FITS.get(tuning[1]) if tuning is not None and tuning[0] >= 4 else None
     traffic_ok = (kernel_source_hash() == TRAFFIC_KERNEL_HASH and wl.name == "layer"
                   and args.form == "batched" and args.modulus == "rns" and T % bchunk == 0 and fit is not None)
     roof = {"bound": "alu", "unit": "Gmodmul/s", "achieved": achieved, "peak": peak,
