@@ -708,7 +708,9 @@ def main():
             "kernel_ms_per_launch": kernel_ms / launches if launches else None,
             "launches": launches,
             "share_of_step": kernel_ms / elapsed_ms if elapsed_ms else None,
-            "out_write_GBps": out_bytes_per_token(wl) * T * args.steps / (kernel_ms / 1e3) / 1e9 if kernel_ms else None}
+            "out_write_GBps": out_bytes_per_token(wl) * T * args.steps / (kernel_ms / 1e3) / 1e9 if kernel_ms else None,
+            "out_write_frac_of_hbm": (out_bytes_per_token(wl) * T * args.steps / (kernel_ms / 1e3) / 1e9 / HBM_GBPS
+                                      if kernel_ms else None)}
     bg = trace.get("body_gemm_kernel", {})
     roof_body = None
     if bg.get("total_ms"):
