@@ -385,11 +385,14 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, lwedot_min_blocks<Shape<LOGN
       }
       if (active) {
         const u64* at = J.ahat + (size_t)t * J.L * N;
-        if constexpr (RNS) {
-          // Block i's products; the first block's (each in [0, 2p)) are the
-          // accumulator as they stand, later ones are added and reduced.
-          auto block = [&](u32 i, auto first) {
-            const Tw* wp = wrow + (size_t)i * N;
+        // Block i's products; the first block's (each below 2p in the RNS
+        // form, below 4q in the 64-bit form: the inverse transform's input
+        // bound) are the accumulator as they stand, later ones are added and
+        // reduced.
+        auto block = [&](u32 i, auto first) {
+          constexpr bool FIRST = decltype(first)::value;
+          const Tw* wp = wrow + (size_t)i * N;
+          if constexpr (RNS) {
             const uint4* ap = reinterpret_cast<const uint4*>(at + (size_t)i * N);
 #pragma unroll
             for (int r = 0; r < 16; r += 2) {
@@ -398,7 +401,7 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, lwedot_min_blocks<Shape<LOGN
               const uint4 w1 = __ldg(&wp[what_idx<LOGN>(p, r + 1)]);
               const u32 m0 = mul_shoup32(av.x, w0.x, w0.y, rk.p1), m1 = mul_shoup32(av.y, w0.z, w0.w, rk.p2);
               const u32 m2 = mul_shoup32(av.z, w1.x, w1.y, rk.p1), m3 = mul_shoup32(av.w, w1.z, w1.w, rk.p2);
-              if constexpr (decltype(first)::value) {
+              if constexpr (FIRST) {
                 x[r] = make_uint2(m0, m1);
                 x[r + 1] = make_uint2(m2, m3);
               } else {
@@ -408,26 +411,27 @@ __global__ void __launch_bounds__(Shape<LOGN>::TPB, lwedot_min_blocks<Shape<LOGN
                 x[r + 1].y = sub_if32(x[r + 1].y + m3, 2 * rk.p2);
               }
             }
-          };
-          block(0u, std::true_type{});
-          for (u32 i = 1; i < J.L; ++i) block(i, std::false_type{});
-        }
-        for (u32 i = 0; i < (RNS ? 0u : J.L); ++i) {
-          const Tw* wp = wrow + (size_t)i * N;
-          if constexpr (!RNS) {
+          } else {
             const ulonglong2* ap = reinterpret_cast<const ulonglong2*>(at + (size_t)i * N);
 #pragma unroll
             for (int r = 0; r < 16; r += 2) {
               const ulonglong2 av = __ldg(&ap[(r >> 1) * P + p]);
               const ulonglong2 w0 = __ldg(&wp[what_idx<LOGN>(p, r)]);
               const ulonglong2 w1 = __ldg(&wp[what_idx<LOGN>(p, r + 1)]);
-              const u64 s0 = x[r] + mul_shoup_lazy(av.x, w0.x, w0.y, q);
-              const u64 s1 = x[r + 1] + mul_shoup_lazy(av.y, w1.x, w1.y, q);
-              x[r] = (s0 >= q4) ? s0 - q4 : s0;
-              x[r + 1] = (s1 >= q4) ? s1 - q4 : s1;
+              const u64 m0 = mul_shoup_lazy(av.x, w0.x, w0.y, q), m1 = mul_shoup_lazy(av.y, w1.x, w1.y, q);
+              if constexpr (FIRST) {
+                x[r] = m0;
+                x[r + 1] = m1;
+              } else {
+                const u64 s0 = x[r] + m0, s1 = x[r + 1] + m1;  // each term < 4q, sum < 8q
+                x[r] = (s0 >= q4) ? s0 - q4 : s0;
+                x[r + 1] = (s1 >= q4) ? s1 - q4 : s1;
+              }
             }
           }
-        }
+        };
+        block(0u, std::true_type{});
+        for (u32 i = 1; i < J.L; ++i) block(i, std::false_type{});
       }
       intt_regs<LOGN>(x, p, buf, tw0, twc, ring);  // barriers inside also order red[]
       if (active) {
