@@ -628,7 +628,7 @@ def main():
 
     # sanity: outputs of the last chunk's first product decrypt to W x mod t
     last_chunk = chunk if args.form == "plain" else bchunk
-    check = sanity_decrypt(wl, mm, inputs, keys, outs, S, T, last_chunk)
+    check, noise = sanity_decrypt(wl, mm, inputs, keys, outs, S, T, last_chunk)
 
     clocks = ClockSampler(local)
     if dist:
@@ -839,7 +839,7 @@ def main():
                 "roofline": roof, "roofline_body": roof_body, "cpu_baseline": cpu, "e2e": e2e,
                 "e2e_unpacked": e2e_unpacked, "e2e_packed_dense": e2e_dense, "gpu_launches": gpu_launches,
                 "kernels": {k: {"launches": v["launches"], "total_ms": v["total_ms"]} for k, v in trace.items()},
-                "clocks": clk, "sanity_decrypt": check}
+                "clocks": clk, "sanity_decrypt": check, "noise": noise}
         print(json.dumps(line))
     for pl in plans:
         phe.phe_plan_destroy(pl)
@@ -936,7 +936,9 @@ def body_flops_per_token(wl) -> int:
 
 def sanity_decrypt(wl, mm, inputs, keys, outs, S, T, chunk):
     """Decrypt a few outputs of the last chunk of the first product with the
-    client's key and compare with W x mod t (plain integer arithmetic)."""
+    client's key and compare with W x mod t (plain integer arithmetic).  Also
+    the noise of those outputs after the switch: e = phase - (q'/t) (W x mod
+    t), centred; decryption is exact while |e| < q'/(2t)."""
     N = wl.ring.N
     pi, name, d, rows, cols, L = mm[0]
     A, B, X = inputs[keys[(pi, d)][0]]
@@ -948,17 +950,26 @@ def sanity_decrypt(wl, mm, inputs, keys, outs, S, T, chunk):
     s = S.cpu().numpy().astype(np.int64)
     ok = 0
     tot = 0
+    e_max = 0
+    k = wl.ring.log2_qout
+    t_plain = synth.T_PLAIN
     for t in range(min(tn, 2)):
         x = X[t0 + t].cpu().numpy().astype(np.int64)
-        for j in (0, rows // 2, rows - 1):
+        for j in sorted({0, rows // 2, rows - 1} | set(range(1, rows, max(1, rows // 16)))):
             a = om[t, j].cpu().numpy().view(np.uint32).astype(np.int64)
             b = int(ob[t, j].item()) & 0xffffffff
-            v = (b - int(np.dot(a, s))) % (1 << 32)
+            v = (b - int(np.dot(a, s))) % (1 << k)
             y = int(np.dot(Wd[j].astype(np.int64), x))
-            dec = ((v * synth.T_PLAIN + (1 << 31)) >> 32) % synth.T_PLAIN
-            ok += int((dec - y) % synth.T_PLAIN == 0)
+            dec = ((v * t_plain + (1 << (k - 1))) >> k) % t_plain
+            ok += int((dec - y) % t_plain == 0)
+            e = (v - (y % t_plain) * ((1 << k) // t_plain)) % (1 << k)
+            e_max = max(e_max, abs(e - (1 << k) if e >= (1 << (k - 1)) else e))
             tot += 1
-    return f"{ok}/{tot}"
+    noise = {"outputs": tot, "max_abs": e_max, "log2_max_abs": math.log2(e_max) if e_max else None,
+             "log2_budget": math.log2((1 << k) / (2 * t_plain)),
+             "note": "after the switch to 2^k: e = phase - (2^k/t)(W x mod t), centred; exact decryption needs "
+                     "|e| < 2^k/(2t)"}
+    return f"{ok}/{tot}", noise
 
 
 def measure_serving(phe, ctx, weights, wl, inputs, keys, n_requests, rate, T_avail, tok_chunk=8, blocks_per_sm=0):
